@@ -1,0 +1,388 @@
+"""Benchmark of the GB300 stereo ray tracer.
+
+One step = one full stereo pair through the whole hot path (primary rays of
+both eyes, shadow rays, mirror rays to the scene's depth, shading, resolve)
+via ``rt_render_stereo`` on an already-built scene resident in HBM.
+
+Workload (the plain method at scale): 200 seeded displaced icosphere blobs
+(256,000 triangles) + 1,000 spheres in a 100^3 box, 4 point lights, 30 %
+mirrors (reflectivity 0.7), 1920x1080 per eye, reflection depth 5.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Timing: W untimed warm-up steps, then K steps, each bracketed by CUDA events
+on the render stream; L2 is flushed (256 MiB write) before every timed step,
+outside the events; barrier + synchronize around the timed loop; max over
+ranks. ``e2e`` repeats the measurement through ``rt_render_stereo_host``
+(camera in, both images copied to pinned host memory, synchronised).
+``--impl reference`` times the FP64 CPU oracle on a bounded pixel sample of
+the same workload on this machine's cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mrays/s & stereo pairs/s at 1080p/eye: learned reprojection vs full trace"
+UNIT = "Mrays/s"
+WORKLOAD = "blobs-256000tri-1000sph-4lights-1920x1080x2-depth5"
+
+# algorithmic FP32-pipe instruction cost per unit of work (FMA = 1)
+COST = dict(node=40, sphere=16, tri=41, raygen=30, shade_hit=30, shade_light=15, reflect=12,
+            shadow_setup=10)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--seed", type=int, default=2)
+    ap.add_argument("--W", type=int, default=1920)
+    ap.add_argument("--H", type=int, default=1080)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=24000,
+                    help="pixels of the workload the CPU oracle traces for cpu_baseline")
+    return ap.parse_args()
+
+
+def workload(args):
+    from paper_1702_01530_gb300 import scenegen as sg
+    return sg.config_blobs(args.seed, W=args.W, H=args.H)
+
+
+def dist_setup(args):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        import shutil
+        import tempfile
+        if shutil.which("nvidia-smi"):
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                stderr=subprocess.DEVNULL)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if not self.path:
+            return None
+        rows = []
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                rows.append(p)
+            except ValueError:
+                pass
+        os.unlink(self.path)
+        if not rows:
+            return None
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4)
+                          if r[5 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ---------------------------------------------------------------- helpers
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        return json.load(open(p)), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def alu_peak_tops(n_sms: int, mhz: float) -> float:
+    """FP32-pipe issue peak: SMs x 128 lanes x clock, in T instructions/s."""
+    return n_sms * 128 * mhz * 1e6 / 1e12
+
+
+def cpu_baseline(scene, n_pixels: int, seed: int = 7):
+    """Time the FP64 oracle on a seeded pixel sample of the workload."""
+    import oracle
+    osc = oracle.OracleScene(scene)
+    osc.lbvh()                                   # one-time scene preparation
+    rng = np.random.default_rng(seed)
+    pix = rng.choice(2 * scene.W * scene.H, size=n_pixels, replace=False)
+    cores = oracle.default_threads()
+    t0 = time.perf_counter()
+    r = osc.render(pixels=pix, n_threads=cores)
+    dt = time.perf_counter() - t0
+    rays = int(r["rays"].sum())
+    return {"seconds": dt, "rays": rays, "pixels": n_pixels, "cores": cores,
+            "mrays_per_s": rays / dt / 1e6,
+            "pairs_per_s_est": (n_pixels / (2 * scene.W * scene.H)) / dt}
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(args, rank, world, local):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1702_01530_gb300 import build as rtbuild
+    from paper_1702_01530_gb300 import capi
+
+    rtbuild.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    s = workload(args)
+    stream = torch.cuda.current_stream()
+
+    t0 = time.perf_counter()
+    g = capi.GpuScene(s)
+    build_s = time.perf_counter() - t0
+    n_sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    img = torch.empty((2, s.H, s.W, 3), dtype=torch.float32, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    # counting pass (untimed): rays by kind, BVH work, primary hits
+    aux = g.render(count_work=True)
+    capi.rt_sync_status(g.handle)
+    rays = aux["rays"].cpu().numpy().astype(np.int64)
+    work = aux["work"].cpu().numpy().reshape(3, 3).astype(np.int64)
+    hits = int((aux["hit_id"] != -1).sum().item())
+    total_rays = int(rays.sum())
+
+    def step():
+        capi.rt_render_stereo(g.handle, s.camera, s.eye_sep, s.convergence, s.W, s.H,
+                              s.max_depth, img[0], img[1], stream)
+
+    for _ in range(args.warmup):
+        step()
+    capi.rt_profile_enable(g.handle, True)
+    stage_ms = {k: [] for k in capi.STAGES}
+    step_ms = []
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step()
+            e1.record(stream)
+            e1.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+            st = capi.rt_profile_read(g.handle)
+            for k, v in st.items():
+                stage_ms[k].append(v)
+        torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if world > 1:
+        dist.barrier()
+    capi.rt_profile_enable(g.handle, False)
+    capi.rt_sync_status(g.handle)
+    clocks = clk.summary()
+
+    ms = float(np.mean(step_ms))
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    mrays = world * total_rays / (ms * 1e-3) / 1e6
+    pairs = world / (ms * 1e-3)
+
+    # e2e: camera in, both images out to pinned host memory, through the C-ABI
+    hl = torch.empty((s.H, s.W, 3), dtype=torch.float32).pin_memory()
+    hr = torch.empty((s.H, s.W, 3), dtype=torch.float32).pin_memory()
+    for _ in range(max(1, args.warmup // 2)):
+        capi.rt_render_stereo_host(g.handle, s.camera, s.eye_sep, s.convergence, s.W, s.H,
+                                   s.max_depth, hl, hr, stream)
+    e2e_ms = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        capi.rt_render_stereo_host(g.handle, s.camera, s.eye_sep, s.convergence, s.W, s.H,
+                                   s.max_depth, hl, hr, stream)
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e = float(np.mean(e2e_ms))
+    if world > 1:
+        t = torch.tensor([e2e], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e = float(t.item())
+
+    # roofline of the dominant kernel (FP32 issue bound). Kernels: the
+    # primary-ray kernel (1 launch), the shadow any-hit kernel (D+1 launches)
+    # and the mirror-ray kernel (D launches); achieved = algorithmic ops of
+    # all its launches / their summed event time.
+    stages = {k: float(np.mean(v)) for k, v in stage_ms.items()}
+    L = len(s.lights)
+    kern_ms = {"primary": stages["primary"], "shadow": stages["shadow0"] + stages["shadowN"],
+               "reflect": stages["reflect"]}
+    ops = {
+        "primary": (rays[0] * COST["raygen"] + work[0, 0] * COST["node"]
+                    + work[0, 1] * COST["sphere"] + work[0, 2] * COST["tri"]
+                    + hits * (COST["shade_hit"] + COST["shade_light"] * L)),
+        "shadow": (rays[1] * COST["shadow_setup"] + work[1, 0] * COST["node"]
+                   + work[1, 1] * COST["sphere"] + work[1, 2] * COST["tri"]),
+        "reflect": (rays[2] * COST["reflect"] + work[2, 0] * COST["node"]
+                    + work[2, 1] * COST["sphere"] + work[2, 2] * COST["tri"]),
+    }
+    dom = max(kern_ms, key=lambda k: kern_ms[k])
+    pk, pk_kind = peaks()
+    sm_max = float(pk.get("sm_max_mhz", 2070.0))
+    peak = alu_peak_tops(n_sms, sm_max)
+    achieved = ops[dom] / (kern_ms[dom] * 1e-3) / 1e12 if kern_ms[dom] > 0 else 0.0
+    kernel_names = {"primary": "k_trace<primary>", "shadow": "k_shadow",
+                    "reflect": "k_trace<reflect>"}
+    prof = {}
+    pfile = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(pfile):
+        prof = json.load(open(pfile))
+
+    line = {
+        "metric": METRIC, "value": round(mrays, 2), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded scene generator; no dataset)",
+        "config": {"workload": WORKLOAD, "seed": args.seed, "W": s.W, "H": s.H,
+                   "max_depth": s.max_depth, "lights": L, "triangles": len(s.triangles),
+                   "spheres": len(s.spheres), "parallelism": f"replicas{world}",
+                   "l2": "flushed before every timed step (256 MiB write), per-step CUDA events"},
+        "stereo_pairs_per_s": round(pairs, 2),
+        "rays_per_pair": {"primary": int(rays[0]), "shadow": int(rays[1]),
+                          "reflection": int(rays[2])},
+        "stage_ms": {k: round(v, 4) for k, v in stages.items()},
+        "work_per_pair": {"inner_node_visits": work[:, 0].tolist(),
+                          "sphere_tests": work[:, 1].tolist(), "tri_tests": work[:, 2].tolist(),
+                          "kinds": ["primary", "shadow", "reflection"]},
+        "scene_build_ms": round(build_s * 1e3, 2),
+        "e2e": {"value": round(world * total_rays / (e2e * 1e-3) / 1e6, 2), "unit": UNIT,
+                "stereo_pairs_per_s": round(world / (e2e * 1e-3), 2), "ms_per_step": round(e2e, 3),
+                "h2d_bytes_per_step": int(s.camera.nbytes),
+                "d2h_bytes_per_step": int(2 * s.W * s.H * 3 * 4),
+                "call": "rt_render_stereo_host"},
+        "roofline": {"bound": "alu", "kernel": kernel_names[dom],
+                     "algorithmic_ops_per_step": int(ops[dom]),
+                     "kernel_ms_per_step": round(kern_ms[dom], 4),
+                     "achieved": round(achieved, 3),
+                     "peak": round(peak, 2), "unit": "TFLOP/s",
+                     "peak_note": f"FP32-pipe issue: {n_sms} SMs x 128 lanes x {sm_max:.0f} MHz "
+                                  f"(FMA = 1 op); SM clock max from MEASURED_PEAKS ({pk_kind})",
+                     "frac": round(achieved / peak, 4) if peak else None,
+                     "traffic": prof.get(dom)},
+        "gpu_launches": int(args.steps * (2 * (s.max_depth + 1) + 1)),
+        "clocks": clocks,
+    }
+    if clocks and clocks.get("sm_mhz"):
+        line["roofline"]["frac_at_sampled_clock"] = round(
+            achieved / alu_peak_tops(n_sms, clocks["sm_mhz"]), 4)
+    if rank == 0 and not args.no_cpu_baseline:
+        cb = cpu_baseline(s, args.cpu_sample)
+        line["cpu_baseline"] = {"value": round(cb["mrays_per_s"], 4), "unit": UNIT,
+                                "cores": cb["cores"], "kind": "oracle",
+                                "sample": f"{cb['pixels']} seeded random pixels of the workload "
+                                          f"({cb['rays']} rays, {cb['seconds']:.1f} s, FP64)",
+                                "stereo_pairs_per_s_est": round(cb["pairs_per_s_est"], 6)}
+    g.close()
+    if world > 1:
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line))
+
+
+# --------------------------------------------------------- reference arm
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import oracle
+    s = workload(args)
+    osc = oracle.OracleScene(s)
+    osc.lbvh()
+    cores = oracle.default_threads()
+    per_step = max(256, args.cpu_sample // max(1, args.steps + args.warmup))
+    rng = np.random.default_rng(11)
+    for _ in range(args.warmup):
+        osc.render(pixels=rng.choice(2 * s.W * s.H, size=per_step, replace=False), n_threads=cores)
+    rays = 0
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        r = osc.render(pixels=rng.choice(2 * s.W * s.H, size=per_step, replace=False),
+                       n_threads=cores)
+        rays += int(r["rays"].sum())
+    dt = time.perf_counter() - t0
+    v = rays / dt / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(dt / args.steps * 1e3, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded scene generator; no dataset)",
+            "config": {"workload": WORKLOAD, "seed": args.seed, "W": s.W, "H": s.H,
+                       "max_depth": s.max_depth, "parallelism": "cpu-threads"},
+            "cpu_baseline": {"value": round(v, 4), "unit": UNIT, "cores": cores,
+                             "kind": "oracle",
+                             "sample": f"{per_step} seeded random pixels per step"},
+            "e2e": {"value": round(v, 4), "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

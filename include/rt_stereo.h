@@ -1,0 +1,230 @@
+/*
+ * rt_stereo.h -- C-ABI of the GB300 stereo ray tracer.
+ *
+ * The library computes a stereo pair: two images of one scene seen from two
+ * cameras at the observer's eyes (paper Sec. 2: stereoscopic synthesis is
+ * the computation of two projections of the scene from two cameras; Sec. 3:
+ * the left and right channel are independent -- "parallel level 1" -- and
+ * each channel's pixels are traced in parallel -- "parallel level 2").
+ * Each pixel is ray traced (Sec. 3, Table 1: reverse/"classical" ray tracing
+ * over a BVH): a primary ray, one shadow ray per light facing the surface,
+ * and mirror reflection rays up to a fixed depth, shaded to RGB.
+ *
+ * Conventions shared by every entry point
+ *  - Return value: RT_OK (0) or a negative RT_ERR_* code. No C++ exception
+ *    crosses this boundary. rt_last_error() gives a message for the calling
+ *    thread's last failure.
+ *  - "host" pointers are ordinary CPU memory (pageable or pinned); "device"
+ *    pointers are CUDA global memory of the current device (for example the
+ *    data pointer of a CUDA torch tensor).
+ *  - cuda_stream is a cudaStream_t (NULL = legacy default stream). Work is
+ *    enqueued on it and the call returns before the GPU finishes, except
+ *    where a call says it synchronises. Errors found on the host (bad
+ *    arguments, allocation failure) are returned at once; a device-side
+ *    check that trips (a traversal or queue bound) is reported by the next
+ *    rt_sync_status() on the scene.
+ *  - A scene is used by one stream at a time: renders of one scene must not
+ *    overlap (they share the scene's scratch buffers).
+ *
+ * Geometry conventions (the paper fixes none of these; they are readings):
+ *  - Right-handed world space. Spheres are (centre, radius); triangles are
+ *    (v0, v1, v2) and two-sided. Primitive ids: spheres 0..n_spheres-1, then
+ *    triangles n_spheres..n_spheres+n_tris-1; no hit = 0xFFFFFFFF.
+ *  - Closest hit = smallest t > 0; equal t resolves to the lower id.
+ *  - Camera: off-axis stereo. fwd = normalize(forward), right =
+ *    normalize(forward x up), up' = right x fwd. Pixel (i, j) (row 0 = top)
+ *    aims at Q = eye + convergence * (fwd + nx right + ny up') with
+ *    nx = (2(i+0.5)/W - 1) tan(vfov/2) W/H and ny = (1 - 2(j+0.5)/H) tan(vfov/2).
+ *    The left eye sits at eye - (eye_sep/2) right, the right eye at
+ *    eye + (eye_sep/2) right; both aim at the same Q, so a point at view
+ *    depth z appears f_px * eye_sep * (1/z - 1/convergence) pixels further
+ *    right in the left image, f_px = (H/2)/tan(vfov/2).
+ *  - Shading (Whitted): at a hit p with normal n facing the ray,
+ *    local = albedo * (0.1 + sum over lights with n.l > 0 and an unblocked
+ *    shadow ray of intensity * n.l); colour = (1 - r) local + r colour of the
+ *    mirror ray while depth < max_depth (the reflected term is 0 at
+ *    max_depth); a miss returns the background (0.2, 0.3, 0.5). Secondary
+ *    rays start at p + n * 1e-4 * max(1, |p|_inf); a shadow ray towards a
+ *    light at distance L is blocked by a hit with t < L - that offset.
+ *    Output = colour clamped to [0, 1].
+ */
+#ifndef RT_STEREO_H
+#define RT_STEREO_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RT_OK 0
+#define RT_ERR_INVALID_ARG (-1)   /* an argument failed validation            */
+#define RT_ERR_CUDA (-2)          /* a CUDA runtime call failed                */
+#define RT_ERR_OOM (-3)           /* device or host allocation failed          */
+#define RT_ERR_TIMEOUT (-4)       /* a device loop hit its iteration bound     */
+#define RT_ERR_DEVICE_CHECK (-5)  /* a device-side bound or index check failed */
+
+#define RT_MAX_DEPTH 16
+#define RT_MISS_ID 0xFFFFFFFFu
+
+/* Scene records: little-endian, no padding (20, 40, 16, 16, 40 bytes). */
+typedef struct { float center[3]; float radius; uint32_t material; } rt_sphere;
+typedef struct { float v0[3]; float v1[3]; float v2[3]; uint32_t material; } rt_triangle;
+/* albedo in [0,1]^3, reflectivity r in [0,1] */
+typedef struct { float albedo[3]; float reflectivity; } rt_material;
+/* white point light, no distance falloff */
+typedef struct { float position[3]; float intensity; } rt_light;
+/* the centre ("cyclopean") eye; vfov_deg is the vertical field of view */
+typedef struct { float eye[3]; float forward[3]; float up[3]; float vfov_deg; } rt_camera;
+
+typedef struct rt_scene rt_scene;  /* opaque */
+
+/*
+ * rt_scene_create -- upload a scene and build its BVH on the GPU.
+ * Paper: Sec. 4 (the host prepares the scene -- objects, polygons, lights --
+ * and copies it to GPU memory) and Table 1 (BVH trees as the acceleration
+ * structure). The BVH is a linear BVH: FP64 centroid bounds and 10-bit per
+ * axis Morton codes, 64-bit keys (morton << 32 | primitive id) sorted on
+ * the GPU, a binary radix tree over the keys, FP32 boxes refitted bottom-up
+ * (sphere boxes rounded outward).
+ *   spheres/tris/mats/lights: host arrays of n_* records; copied, the caller
+ *     keeps ownership. n_spheres + n_tris >= 1 and < 2^31; n_mats >= 1;
+ *     n_lights >= 1. Every material index < n_mats; radii > 0; all values
+ *     finite; reflectivity and albedo in [0, 1]; intensity >= 0.
+ *   cuda_stream: stream for the upload and build; the call synchronises it
+ *     before returning.
+ *   out_scene: receives the new scene; owned by the caller, released with
+ *     rt_scene_destroy.
+ * Errors: RT_ERR_INVALID_ARG (validation), RT_ERR_OOM, RT_ERR_CUDA.
+ */
+int rt_scene_create(const rt_sphere* spheres, uint32_t n_spheres,
+                    const rt_triangle* tris, uint32_t n_tris,
+                    const rt_material* mats, uint32_t n_mats,
+                    const rt_light* lights, uint32_t n_lights,
+                    void* cuda_stream, rt_scene** out_scene);
+
+/* Release a scene and all device memory it owns. NULL is ignored. The
+ * caller must make sure no work using the scene is still in flight. */
+void rt_scene_destroy(rt_scene* scene);
+
+/*
+ * rt_render_stereo -- trace both eyes of one stereo pair.
+ * Paper: Sec. 2-3 (two projections from two eye cameras; left and right
+ * channel computed in parallel; per-pixel ray tracing within a channel).
+ *   cam: host pointer; forward x up must not vanish; 0 < vfov_deg < 180.
+ *   eye_sep >= 0: distance between the eyes. convergence > 0: distance of the
+ *     shared image window (zero-disparity plane) along forward.
+ *   W, H >= 1 pixels per eye, 2*W*H <= 2^31; max_depth <= RT_MAX_DEPTH
+ *     reflection bounces after the primary hit.
+ *   out_L, out_R: device buffers of H*W*3 float32 each, row-major, row 0 at
+ *     the top, RGB interleaved; owned by the caller; fully overwritten.
+ *   cuda_stream: the stream the render is enqueued on (asynchronous).
+ * The first render at a new size may allocate scene-owned scratch (which is
+ * then reused); it does not synchronise.
+ * Errors: RT_ERR_INVALID_ARG, RT_ERR_OOM, RT_ERR_CUDA on the host;
+ * device-side bounds are reported by rt_sync_status.
+ */
+int rt_render_stereo(const rt_scene* scene, const rt_camera* cam,
+                     float eye_sep, float convergence,
+                     uint32_t W, uint32_t H, uint32_t max_depth,
+                     float* out_L, float* out_R, void* cuda_stream);
+
+/*
+ * rt_render_stereo_aux -- rt_render_stereo plus per-pixel and per-ray-kind
+ * diagnostics, for tests and measurement. Any of the extra pointers may be
+ * NULL. All are device pointers owned by the caller:
+ *   hit_id_L/R: H*W uint32, primary-ray hit primitive id (RT_MISS_ID on miss)
+ *   depth_L/R:  H*W float32, view depth of the primary hit (t * d.fwd),
+ *               +infinity on a miss
+ *   ray_counts: 3 uint64: rays traced by kind (primary, shadow, reflection)
+ *   work:       9 uint64: per kind (primary, shadow, reflection) the internal
+ *               BVH nodes visited, ray-sphere tests, ray-triangle tests. When
+ *               non-NULL the instrumented traversal variant runs (slower).
+ */
+int rt_render_stereo_aux(const rt_scene* scene, const rt_camera* cam,
+                         float eye_sep, float convergence,
+                         uint32_t W, uint32_t H, uint32_t max_depth,
+                         float* out_L, float* out_R,
+                         uint32_t* hit_id_L, uint32_t* hit_id_R,
+                         float* depth_L, float* depth_R,
+                         uint64_t* ray_counts, uint64_t* work,
+                         void* cuda_stream);
+
+/*
+ * rt_render_stereo_host -- end-to-end render into HOST buffers.
+ * Paper: Sec. 4-5 (the synthesis time splits into GPU computation and the
+ * copies between CPU and GPU memory). Renders like rt_render_stereo into
+ * scene-owned device buffers, copies both images to host_L/host_R (H*W*3
+ * float32 each, same layout; pinned memory gives full copy speed) and
+ * synchronises the stream before returning.
+ */
+int rt_render_stereo_host(const rt_scene* scene, const rt_camera* cam,
+                          float eye_sep, float convergence,
+                          uint32_t W, uint32_t H, uint32_t max_depth,
+                          float* host_L, float* host_R, void* cuda_stream);
+
+/*
+ * rt_sync_status -- synchronise cuda_stream and report device-side checks
+ * raised by earlier work on the scene (then clear them).
+ * Returns RT_OK, RT_ERR_TIMEOUT (a traversal or queue loop reached its
+ * iteration bound), RT_ERR_DEVICE_CHECK (a stack, queue or index bound was
+ * exceeded) or RT_ERR_CUDA.
+ */
+int rt_sync_status(const rt_scene* scene, void* cuda_stream);
+
+/*
+ * rt_scene_get_bvh -- copy the scene's LBVH to HOST arrays (test hook;
+ * synchronises). n = number of primitives. Any pointer may be NULL.
+ *   keys[n]:        sorted 64-bit keys (morton30 << 32 | primitive id)
+ *   left[n-1], right[n-1]: children of internal node i (binary radix tree
+ *                   numbering, root 0): >= 0 internal node, < 0 leaf ~k
+ *                   (leaf k holds the primitive of keys[k])
+ *   parent[2n-1]:   parent of internal node i at [i], of leaf k at [n-1+k];
+ *                   -1 for the root
+ *   inner_box[(n-1)*6], leaf_box[n*6]: FP32 boxes, lo xyz then hi xyz
+ */
+int rt_scene_get_bvh(const rt_scene* scene, uint64_t* keys, int32_t* left, int32_t* right,
+                     int32_t* parent, float* inner_box, float* leaf_box);
+
+/*
+ * rt_debug_set_node -- TEST HOOK; the paper has no counterpart. Overwrites
+ * the children of internal node `node` with (left, right) (>= 0 internal
+ * node < n-1, < 0 leaf ~k with k < n; out-of-range values are rejected with
+ * RT_ERR_INVALID_ARG) and, when empty_right != 0, gives the right child an
+ * empty box. It lets a test build a cycle in the BVH (for example node 0 as
+ * its own left child with an empty right child) to check that traversal
+ * stops at its iteration bound and rt_sync_status reports RT_ERR_TIMEOUT;
+ * every index stays in range, so no memory outside the scene is touched.
+ * Synchronises the device.
+ */
+int rt_debug_set_node(rt_scene* scene, uint32_t node, int32_t left, int32_t right,
+                      int empty_right);
+
+/*
+ * rt_profile_enable / rt_profile_read -- per-stage GPU time of the last
+ * render of a scene (paper Sec. 4, Figure 7: time spent on the basic
+ * procedures of the synthesis). While enabled, every render records a CUDA
+ * event on its stream after each stage. rt_profile_read waits for the last
+ * render's events and writes RT_NUM_STAGES floats (milliseconds) to the
+ * HOST array ms: [0] clears, [1] primary rays (generation, closest hit,
+ * shading, enqueue), [2] shadow rays of primary hits, [3] mirror rays (all
+ * depths), [4] shadow rays of mirror hits, [5] resolve to float RGB.
+ * Returns RT_ERR_INVALID_ARG if profiling was off during the last render.
+ */
+#define RT_NUM_STAGES 6
+int rt_profile_enable(rt_scene* scene, int on);
+int rt_profile_read(const rt_scene* scene, float* ms);
+
+/* Number of primitives of the scene (0 for NULL). */
+uint32_t rt_scene_num_prims(const rt_scene* scene);
+
+/* Message of the calling thread's last failure ("" if none). */
+const char* rt_last_error(void);
+
+/* Library version string. */
+const char* rt_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RT_STEREO_H */

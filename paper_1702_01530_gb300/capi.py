@@ -1,0 +1,265 @@
+"""Python binding of the C-ABI in ``include/rt_stereo.h`` (ctypes).
+
+Argument marshalling only: every step of BVH construction and rendering
+runs in the CUDA library ``_build/librtstereo.so``. Functions keep the C
+names. Device buffers are passed as CUDA torch tensors (or raw integer
+device addresses); streams as ``torch.cuda.Stream``, raw handles, or None
+(= torch's current stream). There is no CPU fallback: if the library is
+missing, loading it raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+from . import scenegen
+from .build import INCLUDE, LIB
+
+RT_OK = 0
+RT_ERR_INVALID_ARG = -1
+RT_ERR_CUDA = -2
+RT_ERR_OOM = -3
+RT_ERR_TIMEOUT = -4
+RT_ERR_DEVICE_CHECK = -5
+RT_MISS_ID = 0xFFFFFFFF
+HEADER = os.path.join(INCLUDE, "rt_stereo.h")
+
+_lib = None
+_vp = ctypes.c_void_p
+_u32 = ctypes.c_uint32
+_f32 = ctypes.c_float
+
+
+class RtError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"rt error {code}: {msg}")
+        self.code = code
+
+
+_SIGS = {
+    "rt_scene_create": (ctypes.c_int, [_vp, _u32, _vp, _u32, _vp, _u32, _vp, _u32, _vp,
+                                       ctypes.POINTER(_vp)]),
+    "rt_scene_destroy": (None, [_vp]),
+    "rt_render_stereo": (ctypes.c_int, [_vp, _vp, _f32, _f32, _u32, _u32, _u32, _vp, _vp, _vp]),
+    "rt_render_stereo_aux": (ctypes.c_int, [_vp, _vp, _f32, _f32, _u32, _u32, _u32, _vp, _vp,
+                                            _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "rt_render_stereo_host": (ctypes.c_int, [_vp, _vp, _f32, _f32, _u32, _u32, _u32, _vp, _vp,
+                                             _vp]),
+    "rt_sync_status": (ctypes.c_int, [_vp, _vp]),
+    "rt_scene_get_bvh": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "rt_scene_num_prims": (_u32, [_vp]),
+    "rt_debug_set_node": (ctypes.c_int, [_vp, _u32, ctypes.c_int32, ctypes.c_int32,
+                                         ctypes.c_int]),
+    "rt_profile_enable": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "rt_profile_read": (ctypes.c_int, [_vp, _vp]),
+    "rt_last_error": (ctypes.c_char_p, []),
+    "rt_version": (ctypes.c_char_p, []),
+}
+
+
+def library_path() -> str:
+    return LIB
+
+
+def lib():
+    """Load librtstereo.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB):
+            raise ImportError(f"{LIB} is missing: build it with "
+                              "`python -m paper_1702_01530_gb300.build` (needs nvcc)")
+        L = ctypes.CDLL(LIB)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def header_functions() -> list[str]:
+    """Names of the functions declared in include/rt_stereo.h."""
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(rt_[a-z0-9_]+)\s*\(", src)))
+
+
+def rt_last_error() -> str:
+    return lib().rt_last_error().decode()
+
+
+def rt_version() -> str:
+    return lib().rt_version().decode()
+
+
+def _check(rc: int):
+    if rc != RT_OK:
+        raise RtError(rc, rt_last_error())
+
+
+def _dptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if not x.is_cuda or not x.is_contiguous():
+        raise ValueError("device buffers must be contiguous CUDA tensors")
+    return x.data_ptr()
+
+
+def _stream(s):
+    if s is None:
+        try:
+            import torch
+            return torch.cuda.current_stream().cuda_stream if torch.cuda.is_available() else None
+        except ImportError:
+            return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def _np(a, dt):
+    a = np.ascontiguousarray(a, dtype=dt)
+    return a, (a.ctypes.data if a.size else None)
+
+
+def rt_scene_create(spheres, triangles, materials, lights, stream=None) -> int:
+    sp, psp = _np(spheres, scenegen.SPHERE_DT)
+    tr, ptr = _np(triangles, scenegen.TRIANGLE_DT)
+    mt, pmt = _np(materials, scenegen.MATERIAL_DT)
+    li, pli = _np(lights, scenegen.LIGHT_DT)
+    h = _vp()
+    _check(lib().rt_scene_create(psp, len(sp), ptr, len(tr), pmt, len(mt), pli, len(li),
+                                 _stream(stream), ctypes.byref(h)))
+    return h.value
+
+
+def rt_scene_destroy(scene: int):
+    lib().rt_scene_destroy(scene)
+
+
+def _cam(camera):
+    c = np.ascontiguousarray(np.asarray(camera, dtype=scenegen.CAMERA_DT).reshape(()))
+    return c, c.ctypes.data
+
+
+def rt_render_stereo(scene, camera, eye_sep, convergence, W, H, max_depth, out_L, out_R,
+                     stream=None):
+    c, pc = _cam(camera)
+    _check(lib().rt_render_stereo(scene, pc, eye_sep, convergence, W, H, max_depth, _dptr(out_L),
+                                  _dptr(out_R), _stream(stream)))
+
+
+def rt_render_stereo_aux(scene, camera, eye_sep, convergence, W, H, max_depth, out_L, out_R,
+                         hit_id_L=None, hit_id_R=None, depth_L=None, depth_R=None,
+                         ray_counts=None, work=None, stream=None):
+    c, pc = _cam(camera)
+    _check(lib().rt_render_stereo_aux(scene, pc, eye_sep, convergence, W, H, max_depth,
+                                      _dptr(out_L), _dptr(out_R), _dptr(hit_id_L),
+                                      _dptr(hit_id_R), _dptr(depth_L), _dptr(depth_R),
+                                      _dptr(ray_counts), _dptr(work), _stream(stream)))
+
+
+def _hptr(x):
+    if isinstance(x, np.ndarray):
+        if not x.flags.c_contiguous or x.dtype != np.float32:
+            raise ValueError("host buffers must be contiguous float32")
+        return x.ctypes.data
+    if x.is_cuda or not x.is_contiguous():
+        raise ValueError("host buffers must be contiguous CPU tensors")
+    return x.data_ptr()
+
+
+def rt_render_stereo_host(scene, camera, eye_sep, convergence, W, H, max_depth, host_L, host_R,
+                          stream=None):
+    c, pc = _cam(camera)
+    _check(lib().rt_render_stereo_host(scene, pc, eye_sep, convergence, W, H, max_depth,
+                                       _hptr(host_L), _hptr(host_R), _stream(stream)))
+
+
+def rt_sync_status(scene, stream=None):
+    _check(lib().rt_sync_status(scene, _stream(stream)))
+
+
+def rt_debug_set_node(scene, node, left, right, empty_right=False):
+    _check(lib().rt_debug_set_node(scene, node, left, right, int(bool(empty_right))))
+
+
+STAGES = ("clear", "primary", "shadow0", "reflect", "shadowN", "resolve")
+
+
+def rt_profile_enable(scene, on=True):
+    _check(lib().rt_profile_enable(scene, int(bool(on))))
+
+
+def rt_profile_read(scene) -> dict:
+    ms = np.zeros(len(STAGES), np.float32)
+    _check(lib().rt_profile_read(scene, ms.ctypes.data))
+    return dict(zip(STAGES, ms.astype(float).tolist()))
+
+
+def rt_scene_num_prims(scene) -> int:
+    return lib().rt_scene_num_prims(scene)
+
+
+def rt_scene_get_bvh(scene) -> dict:
+    n = rt_scene_num_prims(scene)
+    keys = np.zeros(n, np.uint64)
+    left = np.zeros(max(n - 1, 0), np.int32)
+    right = np.zeros(max(n - 1, 0), np.int32)
+    parent = np.zeros(2 * n - 1, np.int32)
+    ibox = np.zeros((max(n - 1, 0), 6), np.float32)
+    lbox = np.zeros((n, 6), np.float32)
+    p = lambda a: a.ctypes.data if a.size else None  # noqa: E731
+    _check(lib().rt_scene_get_bvh(scene, p(keys), p(left), p(right), p(parent), p(ibox),
+                                  p(lbox)))
+    return dict(keys=keys, left=left, right=right, parent=parent, inner_box=ibox, leaf_box=lbox)
+
+
+class GpuScene:
+    """Owns one rt_scene built from a ``scenegen.Scene``."""
+
+    def __init__(self, scene: scenegen.Scene, stream=None):
+        self.scene = scene
+        self.handle = rt_scene_create(scene.spheres, scene.triangles, scene.materials,
+                                      scene.lights, stream)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            rt_scene_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def render(self, W=None, H=None, max_depth=None, eye_sep=None, convergence=None, aux=False,
+               count_work=False, stream=None, out=None):
+        """Render both eyes into (2, H, W, 3) float32 CUDA tensors (left, right)."""
+        import torch
+        s = self.scene
+        W = s.W if W is None else W
+        H = s.H if H is None else H
+        D = s.max_depth if max_depth is None else max_depth
+        es = s.eye_sep if eye_sep is None else eye_sep
+        cv = s.convergence if convergence is None else convergence
+        dev = torch.device("cuda")
+        img = out if out is not None else torch.empty((2, H, W, 3), dtype=torch.float32, device=dev)
+        res = {"rgb": img}
+        if aux or count_work:
+            hit = torch.empty((2, H, W), dtype=torch.int32, device=dev)
+            dep = torch.empty((2, H, W), dtype=torch.float32, device=dev)
+            rays = torch.zeros(3, dtype=torch.int64, device=dev)
+            work = torch.zeros(9, dtype=torch.int64, device=dev) if count_work else None
+            rt_render_stereo_aux(self.handle, s.camera, es, cv, W, H, D, img[0], img[1],
+                                 hit[0], hit[1], dep[0], dep[1], rays, work, stream)
+            res.update(hit_id=hit, depth=dep, rays=rays, work=work)
+        else:
+            rt_render_stereo(self.handle, s.camera, es, cv, W, H, D, img[0], img[1], stream)
+        return res

@@ -1,0 +1,121 @@
+// Internal declarations of the GB300 stereo ray tracer (CUDA, sm_103a).
+//
+// Data layout in HBM (all 16-byte aligned, read with 16-byte vector loads):
+//   nodes  : (n-1) BVH2 nodes of 64 B = 4 x float4, binary radix tree
+//            numbering (root 0). Both children's boxes live in the parent:
+//              [0] = (c0.lo.x, c0.hi.x, c0.lo.y, c0.hi.y)
+//              [1] = (c1.lo.x, c1.hi.x, c1.lo.y, c1.hi.y)
+//              [2] = (c0.lo.z, c0.hi.z, c1.lo.z, c1.hi.z)
+//              [3] = (left, right, -, -) as int bits; >= 0 internal, < 0 leaf ~k
+//   prims  : n leaf records of 48 B = 3 x float4 in leaf (sorted key) order:
+//            triangle: (v0.xyz, id) (e1.xyz, material) (e2.xyz, 0)
+//            sphere  : (c.xyz, id)  (r, 0, 0, material)  (0, 0, 0, 0)
+//            (id and material stored as uint bits; id < n_spheres = sphere)
+//   mats   : float4 (albedo rgb, reflectivity)
+//   lights : float4 (position xyz, intensity)
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/rt_stereo.h"
+
+namespace rt {
+
+// device error word bits
+enum : uint32_t {
+  ERR_STACK = 1u,      // traversal stack bound exceeded
+  ERR_ITER = 2u,       // traversal iteration bound reached
+  ERR_QUEUE = 4u,      // a wavefront queue would overflow
+  ERR_INDEX = 8u,      // an index read from memory is out of range
+  ERR_BUILD = 16u,     // BVH refit did not reach the root
+};
+
+constexpr int kStackSize = 64;   // radix-tree depth over unique 64-bit keys <= 64
+constexpr float kAmbient = 0.1f;
+constexpr float kBgR = 0.2f, kBgG = 0.3f, kBgB = 0.5f;
+
+struct DeviceScene {
+  const float4* nodes;
+  const float4* prims;
+  const float4* mats;
+  const float4* lights;
+  uint32_t n_prims, n_spheres, n_mats, n_lights;
+};
+
+// host-computed camera basis (double -> float)
+struct CameraParams {
+  float eye[3], right[3], up[3], fwd[3];
+  float tan_x, tan_y, zc, half_sep;
+  uint32_t W, H;
+  uint32_t tiles_x, tiles_y;  // 8x4-pixel tiles per eye
+};
+
+// scratch of one render (scene-owned, grown on demand)
+struct Workspace {
+  size_t bytes = 0;
+  void* base = nullptr;
+  uint32_t* accum = nullptr;     // 2*P*3 fixed-point colour sums
+  float4* queue[2] = {nullptr, nullptr};  // reflection rays, 3 float4 each
+  float4* shadow = nullptr;      // shadow rays, 3 float4 each
+  uint32_t* counters = nullptr;  // see Counter enum
+  uint64_t cap_rays = 0;         // entries per reflection queue (2*P)
+  uint64_t cap_shadow = 0;       // shadow entries (2*P*L)
+  float4* frame = nullptr;       // frame buffers for rt_render_stereo_host
+  size_t frame_bytes = 0;
+  uint32_t W = 0, H = 0, L = 0;
+  // stage timing (CUDA events on the render stream), see Stage
+  bool profile = false;
+  cudaEvent_t ev[2 * RT_MAX_DEPTH + 8] = {};
+  int ev_stage[2 * RT_MAX_DEPTH + 8] = {};   // stage that ends at event k
+  int n_ev = 0;
+};
+
+// stages of one render, in launch order
+enum Stage : int {
+  ST_CLEAR = 0,     // counter and accumulator clears
+  ST_PRIMARY = 1,   // primary rays: generate, closest hit, shade, enqueue
+  ST_SHADOW0 = 2,   // any-hit of the primary hits' shadow rays
+  ST_REFLECT = 3,   // closest hit + shade of mirror rays, all depths
+  ST_SHADOWN = 4,   // any-hit of the mirror hits' shadow rays, all depths
+  ST_RESOLVE = 5,   // fixed-point sums to float RGB
+  ST_COUNT = 6
+};
+
+// counters block layout (uint32 each)
+enum Counter : int {
+  C_WORK = 0,                     // [0, 2*(RT_MAX_DEPTH+1)): persistent work counters
+  C_QLEN = 2 * (RT_MAX_DEPTH + 1),  // [.., +RT_MAX_DEPTH+2): reflection queue length per depth
+  C_SLEN = C_QLEN + RT_MAX_DEPTH + 2,  // [.., +RT_MAX_DEPTH+1): shadow queue length per depth
+  C_TOTAL = C_SLEN + RT_MAX_DEPTH + 1
+};
+
+struct RenderArgs {
+  DeviceScene sc;
+  CameraParams cam;
+  uint32_t max_depth;
+  float color_scale;       // fixed-point scale of the colour accumulators
+  float* out_L;
+  float* out_R;
+  uint32_t* hit_L;
+  uint32_t* hit_R;
+  float* depth_L;
+  float* depth_R;
+  uint64_t* ray_counts;
+  uint64_t* work;          // non-null => instrumented traversal
+  uint32_t* err;           // device error word
+};
+
+// entry points implemented in the .cu files
+cudaError_t build_lbvh(const float4* d_sph_in, const float* d_tri_in, uint32_t ns, uint32_t nt,
+                       float4* d_nodes, float4* d_prims, uint64_t* d_keys, int32_t* d_parent,
+                       void* d_tmp, size_t tmp_bytes, uint32_t* d_err, cudaStream_t st);
+size_t lbvh_tmp_bytes(uint32_t n);
+cudaError_t render(const RenderArgs& a, Workspace& ws, cudaStream_t st);
+int num_sms();
+
+}  // namespace rt
+
+// error message plumbing (rt_api.cu)
+void rt_set_error(const std::string& msg);

@@ -1,0 +1,222 @@
+"""GPU path vs the FP64 oracle, element by element, through the C-ABI.
+
+Pass criteria (tolerances of the FP32 GPU path against the FP64 oracle):
+  * primary hit id equal on every pixel whose primary ray the oracle does
+    not flag as a near tie (flags bit 0);
+  * per-channel |RGB error| <= 2e-3 on at least 99.9 % of all pixels;
+  * max |RGB error| <= 2e-2 over pixels with no flagged ray (flags == 0);
+  * ray counts by kind equal up to the rays of flagged pixels;
+  * LBVH keys, topology and FP32 boxes bit-exact.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1702_01530_gb300 import capi, scenegen as sg
+from tests.scenes_util import quad, scene
+
+pytestmark = pytest.mark.gpu
+
+TOL, FRAC, MAXERR = 2e-3, 0.999, 2e-2
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    from paper_1702_01530_gb300 import build
+    build.build()
+    oracle.build()
+    torch.cuda.init()
+
+
+def gpu_render(s, **kw):
+    g = capi.GpuScene(s)
+    try:
+        r = g.render(aux=True, **kw)
+        capi.rt_sync_status(g.handle)
+        out = {"rgb": r["rgb"].cpu().numpy(),
+               "hit_id": r["hit_id"].cpu().numpy().view(np.uint32),
+               "depth": r["depth"].cpu().numpy(),
+               "rays": r["rays"].cpu().numpy()}
+        if r.get("work") is not None:
+            out["work"] = r["work"].cpu().numpy().reshape(3, 3)
+        return out
+    finally:
+        g.close()
+
+
+def check_parity(gpu, ref, n_lights, max_depth, check_rays=True):
+    err = np.abs(gpu["rgb"] - ref["rgb"])
+    flags = ref["flags"]
+    within = (err <= TOL).all(axis=-1).mean()
+    assert within >= FRAC, f"only {within:.5f} of pixels within {TOL}"
+    unfl = flags == 0
+    assert unfl.mean() > 0.9
+    assert err[unfl].max() <= MAXERR, f"max err on unflagged pixels {err[unfl].max()}"
+    prim = (flags & 1) == 0
+    bad = gpu["hit_id"][prim] != ref["hit_id"][prim]
+    assert not bad.any(), f"{bad.sum()} unflagged primary hit ids differ"
+    if check_rays:
+        budget = int((flags != 0).sum()) * (n_lights * (max_depth + 1) + max_depth)
+        assert gpu["rays"][0] == ref["rays"][0]
+        assert abs(int(gpu["rays"][1]) - int(ref["rays"][1])) <= budget
+        assert abs(int(gpu["rays"][2]) - int(ref["rays"][2])) <= budget
+    return err
+
+
+# ---------------------------------------------------------------- LBVH
+def _lbvh_scenes():
+    one = scene(spheres=[((0.1, 0.2, -3.0), 0.7, 0)])
+    two = scene(spheres=[((0, 0, -3), 1.0, 0)], tris=[((0, 0, -5), (1, 0, -5), (0, 1, -5), 0)])
+    same = scene(spheres=[((5.0, 5.0, 5.0), 0.1 + 0.01 * k, 0) for k in range(8)])
+    return {
+        "one": one, "two": two, "coincident": same,
+        "small": sg.config_small(1),
+        "polyhedra": sg.config_polyhedra(5, ground=True),
+        "blobs": sg.config_blobs(3, n_blobs=20, n_spheres=100),
+        "blobs_full": sg.config_blobs(2),
+    }
+
+
+@pytest.mark.parametrize("name", list(_lbvh_scenes()))
+def test_lbvh_bit_exact(name):
+    s = _lbvh_scenes()[name]
+    g = capi.GpuScene(s)
+    try:
+        got = capi.rt_scene_get_bvh(g.handle)
+    finally:
+        g.close()
+    ref = oracle.OracleScene(s).lbvh()
+    for k in ("keys", "left", "right", "parent", "leaf_box", "inner_box"):
+        assert np.array_equal(got[k], ref[k]), k
+
+
+# -------------------------------------------------------------- render
+@pytest.mark.parametrize("seed,W,H,D", [(1, 320, 240, 3), (2, 37, 23, 5), (3, 64, 48, 0),
+                                        (4, 1, 1, 3), (5, 129, 67, 16)])
+def test_small_scene_parity(seed, W, H, D):
+    s = sg.config_small(seed, W=W, H=H, max_depth=D)
+    gpu = gpu_render(s)
+    ref = oracle.render(s)
+    check_parity(gpu, ref, 1, D)
+
+
+def test_zero_separation_is_bitwise_identical():
+    s = sg.config_small(1).with_view(eye_sep=0.0)
+    gpu = gpu_render(s)
+    assert np.array_equal(gpu["rgb"][0], gpu["rgb"][1])
+    assert np.array_equal(gpu["hit_id"][0], gpu["hit_id"][1])
+
+
+def test_polyhedra_scene_parity():
+    s = sg.config_polyhedra(5, n_lights=3, ground=True, W=200, H=150)
+    check_parity(gpu_render(s), oracle.render(s), 3, s.max_depth)
+
+
+@pytest.mark.parametrize("nb,ns,W,H", [(20, 100, 160, 90), (60, 300, 96, 64)])
+def test_blob_scene_parity(nb, ns, W, H):
+    s = sg.config_blobs(2, n_blobs=nb, n_spheres=ns, W=W, H=H)
+    ref = oracle.render(s)
+    assert (ref["hit_id"] != capi.RT_MISS_ID).mean() > 0.05
+    check_parity(gpu_render(s), ref, 4, 5)
+
+
+def test_mirror_pair_deep_recursion():
+    a = (0.2, 0.4, 0.8)
+    tris = quad(-10, 10, -10, 10, -5.0, 0) + quad(-10, 10, -10, 10, 5.0, 0)
+    s = scene(tris=tris, mats=[(*a, 0.5)], lights=[((0, 0, 0), 0.3)], W=9, H=9, max_depth=16)
+    gpu = gpu_render(s)
+    ref = oracle.render(s)
+    check_parity(gpu, ref, 1, 16)
+    assert int(gpu["rays"][2]) == 2 * 81 * 16
+
+
+def test_single_primitive_scene():
+    s = scene(spheres=[((0, 0, -5), 1.0, 0)], W=31, H=17)
+    check_parity(gpu_render(s), oracle.render(s), 1, 3)
+
+
+def test_work_counts_match_oracle_bvh_traversal():
+    s = sg.config_blobs(5, n_blobs=10, n_spheres=50, W=96, H=64)
+    gpu = gpu_render(s, count_work=True)
+    ref = oracle.OracleScene(s).render(mode=oracle.OracleScene.MODE_BVH)
+    g, r = gpu["work"].astype(np.float64), ref["work"].astype(np.float64)
+    assert r[0, 0] > 1000
+    rel = np.abs(g - r) / np.maximum(r, 1.0)
+    assert rel.max() < 0.02, (g, r)
+
+
+def test_host_render_matches_device_render():
+    import torch
+    s = sg.config_small(2, W=80, H=60)
+    g = capi.GpuScene(s)
+    try:
+        dev = g.render()["rgb"].cpu().numpy()
+        hl = torch.empty((60, 80, 3), dtype=torch.float32).pin_memory()
+        hr = torch.empty((60, 80, 3), dtype=torch.float32).pin_memory()
+        capi.rt_render_stereo_host(g.handle, s.camera, s.eye_sep, s.convergence, 80, 60,
+                                   s.max_depth, hl, hr)
+        assert np.array_equal(dev[0], hl.numpy()) and np.array_equal(dev[1], hr.numpy())
+    finally:
+        g.close()
+
+
+def test_repeated_renders_are_identical():
+    s = sg.config_blobs(4, n_blobs=10, n_spheres=40, W=64, H=48)
+    g = capi.GpuScene(s)
+    try:
+        a = g.render()["rgb"].cpu().numpy()
+        g.render(W=32, H=16)
+        b = g.render()["rgb"].cpu().numpy()
+        assert np.array_equal(a, b)
+    finally:
+        g.close()
+
+
+# ---------------------------------------------- full size, sampled pixels
+def test_full_size_blob_scene_sampled_parity():
+    """256,000 triangles + 1,000 spheres at 1920x1080 per eye, depth 5, 4
+    lights, rendered exactly as the benchmark renders it; the oracle traces
+    a seeded sample of pixels one by one."""
+    import torch
+    s = sg.config_blobs(2)
+    g = capi.GpuScene(s)
+    try:
+        img = g.render()["rgb"]                      # the timed call
+        aux = g.render(aux=True)                     # same image + hit ids
+        capi.rt_sync_status(g.handle)
+        assert torch.equal(img, aux["rgb"])
+        rgb = aux["rgb"].cpu().numpy().reshape(-1, 3)
+        hit = aux["hit_id"].cpu().numpy().view(np.uint32).reshape(-1)
+    finally:
+        g.close()
+    rng = np.random.default_rng(2024)
+    pix = rng.choice(2 * s.W * s.H, size=3000, replace=False)
+    ref = oracle.OracleScene(s).render(pixels=pix)
+    err = np.abs(rgb[pix] - ref["rgb"])
+    assert (err <= TOL).all(axis=-1).mean() >= FRAC
+    unfl = ref["flags"] == 0
+    assert err[unfl].max() <= MAXERR
+    prim = (ref["flags"] & 1) == 0
+    assert np.array_equal(hit[pix][prim], ref["hit_id"][prim])
+    assert (ref["hit_id"] != capi.RT_MISS_ID).mean() > 0.05
+
+
+# ------------------------------------------------------------ watchdog
+def test_bvh_cycle_stops_at_iteration_bound():
+    s = sg.config_blobs(6, n_blobs=2, n_spheres=20, W=32, H=24, max_depth=1)
+    g = capi.GpuScene(s)
+    try:
+        bvh = capi.rt_scene_get_bvh(g.handle)
+        # node 0 becomes its own left child; its right child gets an empty
+        # box: every ray entering the root loops until the iteration bound
+        capi.rt_debug_set_node(g.handle, 0, 0, int(bvh["right"][0]), empty_right=True)
+        g.render()
+        with pytest.raises(capi.RtError) as e:
+            capi.rt_sync_status(g.handle)
+        assert e.value.code == capi.RT_ERR_TIMEOUT
+        capi.rt_sync_status(g.handle)                # cleared after reporting
+    finally:
+        g.close()
+    gpu = gpu_render(sg.config_small(1, W=32, H=24))  # the context is still usable
+    assert gpu["rgb"].shape == (2, 24, 32, 3)
