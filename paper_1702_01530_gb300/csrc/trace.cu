@@ -86,7 +86,11 @@ __device__ __forceinline__ bool hit_sphere(float4 p0, float r, V3 o, V3 d, float
   return disc >= 0.f && t > 0.f;
 }
 
-// Moller-Trumbore, two-sided, edges inclusive (branch-free acceptance).
+// Moller-Trumbore, two-sided, edges inclusive (branch-free acceptance). The
+// barycentric bounds are widened by kEdge so that a ray through the shared
+// edge of two triangles cannot slip between them when FP32 rounding puts it
+// just outside both (the band lies far inside the oracle's near-tie margin).
+constexpr float kEdge = 1e-6f;
 __device__ __forceinline__ bool hit_tri(float4 p0, float4 p1, float4 p2, V3 o, V3 d, float& t) {
   V3 e1 = xyz(p1), e2 = xyz(p2);
   V3 pv = cross(d, e2);
@@ -97,7 +101,7 @@ __device__ __forceinline__ bool hit_tri(float4 p0, float4 p1, float4 p2, V3 o, V
   V3 qv = cross(tv, e1);
   float v = dot(d, qv) * inv;
   t = dot(e2, qv) * inv;
-  return det != 0.f && u >= 0.f && v >= 0.f && u + v <= 1.f && t > 0.f;
+  return det != 0.f && u >= -kEdge && v >= -kEdge && u + v <= 1.f + kEdge && t > 0.f;
 }
 
 // BVH traversal. ANY = any-hit with t < tmax (returns true if blocked);

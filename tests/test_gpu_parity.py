@@ -45,13 +45,13 @@ def gpu_render(s, **kw):
         g.close()
 
 
-def check_parity(gpu, ref, n_lights, max_depth, check_rays=True):
+def check_parity(gpu, ref, n_lights, max_depth, check_rays=True, min_unflagged=0.9):
     err = np.abs(gpu["rgb"] - ref["rgb"])
     flags = ref["flags"]
     within = (err <= TOL).all(axis=-1).mean()
     assert within >= FRAC, f"only {within:.5f} of pixels within {TOL}"
     unfl = flags == 0
-    assert unfl.mean() > 0.9
+    assert unfl.mean() > min_unflagged
     assert err[unfl].max() <= MAXERR, f"max err on unflagged pixels {err[unfl].max()}"
     prim = (flags & 1) == 0
     bad = gpu["hit_id"][prim] != ref["hit_id"][prim]
@@ -115,7 +115,8 @@ def test_polyhedra_scene_parity():
 
 @pytest.mark.parametrize("nb,ns,W,H", [(20, 100, 160, 90), (60, 300, 96, 64)])
 def test_blob_scene_parity(nb, ns, W, H):
-    s = sg.config_blobs(2, n_blobs=nb, n_spheres=ns, W=W, H=H)
+    # the box shrinks with the blob count so the density matches the full scene
+    s = sg.config_blobs(2, n_blobs=nb, n_spheres=ns, W=W, H=H, box=50.0 * (nb / 200) ** (1 / 3))
     ref = oracle.render(s)
     assert (ref["hit_id"] != capi.RT_MISS_ID).mean() > 0.05
     check_parity(gpu_render(s), ref, 4, 5)
@@ -127,8 +128,11 @@ def test_mirror_pair_deep_recursion():
     s = scene(tris=tris, mats=[(*a, 0.5)], lights=[((0, 0, 0), 0.3)], W=9, H=9, max_depth=16)
     gpu = gpu_render(s)
     ref = oracle.render(s)
-    check_parity(gpu, ref, 1, 16)
-    assert int(gpu["rays"][2]) == 2 * 81 * 16
+    # the quads' shared diagonals run through the 9 diagonal pixels of each
+    # eye: those exact edge hits are near ties by construction
+    check_parity(gpu, ref, 1, 16, min_unflagged=0.85)
+    # off-centre rays drift off the mirrors; the centre pixel bounces 16 times
+    assert np.array_equal(gpu["rays"], ref["rays"]) and int(gpu["rays"][2]) >= 2 * 16
 
 
 def test_single_primitive_scene():
