@@ -215,6 +215,39 @@ int rt_debug_set_node(rt_scene* scene, uint32_t node, int32_t left, int32_t righ
 int rt_profile_enable(rt_scene* scene, int on);
 int rt_profile_read(const rt_scene* scene, float* ms);
 
+/*
+ * rt_build_lbvh_noalloc -- the LBVH build of rt_scene_create, for callers
+ * that cannot allocate device memory. The paper has no counterpart: this
+ * entry point exists for code that must not call cudaMalloc, such as a
+ * plugin whose host application hands out all GPU memory from its own pool,
+ * or a real-time loop that cannot afford cudaMalloc's implicit device
+ * synchronisation. It runs the same kernels as rt_scene_create but writes
+ * into the caller's buffers and keeps its scratch in a static device array
+ * of 13 MiB that every GPU loading this library holds until the process
+ * exits; nothing is allocated.
+ *   d_spheres / d_tris: DEVICE arrays of n_spheres rt_sphere and n_tris
+ *     rt_triangle records (not validated: the caller vouches for finite
+ *     values and material indices).
+ *   1 <= n_spheres + n_tris <= 1,048,576 (2^20); larger builds are
+ *     rejected with RT_ERR_INVALID_ARG.
+ *   Outputs (DEVICE, caller-owned, d_nodes and d_prims 16-byte aligned):
+ *     d_nodes:  max(n-1,1) nodes of 16 floats (64 B): child boxes and child
+ *               indices in the layout the renderer reads;
+ *     d_prims:  n leaf records of 12 floats (48 B);
+ *     d_keys:   n sorted keys; d_parent: 2n-1 parent indices (as in
+ *               rt_scene_get_bvh).
+ *   The call synchronises cuda_stream and returns RT_ERR_DEVICE_CHECK if the
+ *   device-side refit check trips. Every call uses the same scratch array:
+ *   calls whose GPU work overlaps (other streams or host threads) race and
+ *   must be serialised by the caller. The first call on a device looks up
+ *   the array's device address; make that first call before any stream
+ *   capture begins.
+ */
+int rt_build_lbvh_noalloc(const rt_sphere* d_spheres, uint32_t n_spheres,
+                          const rt_triangle* d_tris, uint32_t n_tris,
+                          float* d_nodes, float* d_prims, uint64_t* d_keys, int32_t* d_parent,
+                          void* cuda_stream);
+
 /* Number of primitives of the scene (0 for NULL). */
 uint32_t rt_scene_num_prims(const rt_scene* scene);
 

@@ -55,6 +55,7 @@ _SIGS = {
                                          ctypes.c_int]),
     "rt_profile_enable": (ctypes.c_int, [_vp, ctypes.c_int]),
     "rt_profile_read": (ctypes.c_int, [_vp, _vp]),
+    "rt_build_lbvh_noalloc": (ctypes.c_int, [_vp, _u32, _vp, _u32, _vp, _vp, _vp, _vp, _vp]),
     "rt_last_error": (ctypes.c_char_p, []),
     "rt_version": (ctypes.c_char_p, []),
 }
@@ -218,6 +219,15 @@ def rt_scene_get_bvh(scene) -> dict:
     _check(lib().rt_scene_get_bvh(scene, p(keys), p(left), p(right), p(parent), p(ibox),
                                   p(lbox)))
     return dict(keys=keys, left=left, right=right, parent=parent, inner_box=ibox, leaf_box=lbox)
+
+
+def rt_build_lbvh_noalloc(d_spheres, n_spheres, d_tris, n_tris, d_nodes, d_prims, d_keys,
+                          d_parent, stream=None):
+    """LBVH build into caller-owned device buffers with no device allocation
+    (for callers that may not call cudaMalloc); see include/rt_stereo.h."""
+    _check(lib().rt_build_lbvh_noalloc(_dptr(d_spheres), n_spheres, _dptr(d_tris), n_tris,
+                                       _dptr(d_nodes), _dptr(d_prims), _dptr(d_keys),
+                                       _dptr(d_parent), _stream(stream)))
 
 
 class GpuScene:
