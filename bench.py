@@ -275,30 +275,21 @@ def run_ours(args, rank, world, local):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e = float(t.item())
 
-    # roofline of the dominant kernel (FP32 issue bound). Kernels: the
-    # primary-ray kernel (1 launch), the shadow any-hit kernel (D+1 launches)
-    # and the mirror-ray kernel (D launches); achieved = algorithmic ops of
-    # all its launches / their summed event time.
+    # roofline of the dominant kernel (FP32 issue bound): the persistent
+    # render kernel traces every ray of the pair; achieved = its algorithmic
+    # ops / its event time (recorded inside the library on the same stream).
     stages = {k: float(np.mean(v)) for k, v in stage_ms.items()}
     L = len(s.lights)
-    kern_ms = {"primary": stages["primary"], "shadow": stages["shadow0"] + stages["shadowN"],
-               "reflect": stages["reflect"]}
-    ops = {
-        "primary": (rays[0] * COST["raygen"] + work[0, 0] * COST["node"]
-                    + work[0, 1] * COST["sphere"] + work[0, 2] * COST["tri"]
-                    + hits * (COST["shade_hit"] + COST["shade_light"] * L)),
-        "shadow": (rays[1] * COST["shadow_setup"] + work[1, 0] * COST["node"]
-                   + work[1, 1] * COST["sphere"] + work[1, 2] * COST["tri"]),
-        "reflect": (rays[2] * COST["reflect"] + work[2, 0] * COST["node"]
-                    + work[2, 1] * COST["sphere"] + work[2, 2] * COST["tri"]),
-    }
-    dom = max(kern_ms, key=lambda k: kern_ms[k])
+    ops_all = (rays[0] * COST["raygen"] + hits * (COST["shade_hit"] + COST["shade_light"] * L)
+               + rays[1] * COST["shadow_setup"] + rays[2] * COST["reflect"]
+               + int(work[:, 0].sum()) * COST["node"] + int(work[:, 1].sum()) * COST["sphere"]
+               + int(work[:, 2].sum()) * COST["tri"])
+    kern = "k_render"
+    kern_ms = stages["trace"]
     pk, pk_kind = peaks()
     sm_max = float(pk.get("sm_max_mhz", 2070.0))
     peak = alu_peak_tops(n_sms, sm_max)
-    achieved = ops[dom] / (kern_ms[dom] * 1e-3) / 1e12 if kern_ms[dom] > 0 else 0.0
-    kernel_names = {"primary": "k_trace<primary>", "shadow": "k_shadow",
-                    "reflect": "k_trace<reflect>"}
+    achieved = ops_all / (kern_ms * 1e-3) / 1e12 if kern_ms > 0 else 0.0
     prof = {}
     pfile = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(pfile):
@@ -327,16 +318,16 @@ def run_ours(args, rank, world, local):
                 "h2d_bytes_per_step": int(s.camera.nbytes),
                 "d2h_bytes_per_step": int(2 * s.W * s.H * 3 * 4),
                 "call": "rt_render_stereo_host"},
-        "roofline": {"bound": "alu", "kernel": kernel_names[dom],
-                     "algorithmic_ops_per_step": int(ops[dom]),
-                     "kernel_ms_per_step": round(kern_ms[dom], 4),
+        "roofline": {"bound": "alu", "kernel": kern,
+                     "algorithmic_ops_per_step": int(ops_all),
+                     "kernel_ms_per_step": round(kern_ms, 4),
                      "achieved": round(achieved, 3),
                      "peak": round(peak, 2), "unit": "TFLOP/s",
                      "peak_note": f"FP32-pipe issue: {n_sms} SMs x 128 lanes x {sm_max:.0f} MHz "
                                   f"(FMA = 1 op); SM clock max from MEASURED_PEAKS ({pk_kind})",
                      "frac": round(achieved / peak, 4) if peak else None,
-                     "traffic": prof.get(dom)},
-        "gpu_launches": int(args.steps * (2 * (s.max_depth + 1) + 1)),
+                     "traffic": prof.get(kern)},
+        "gpu_launches": int(args.steps * 2),
         "clocks": clocks,
     }
     if clocks and clocks.get("sm_mhz"):

@@ -206,12 +206,11 @@ int rt_debug_set_node(rt_scene* scene, uint32_t node, int32_t left, int32_t righ
  * procedures of the synthesis). While enabled, every render records a CUDA
  * event on its stream after each stage. rt_profile_read waits for the last
  * render's events and writes RT_NUM_STAGES floats (milliseconds) to the
- * HOST array ms: [0] clears, [1] primary rays (generation, closest hit,
- * shading, enqueue), [2] shadow rays of primary hits, [3] mirror rays (all
- * depths), [4] shadow rays of mirror hits, [5] resolve to float RGB.
+ * HOST array ms: [0] clears, [1] ray tracing (primary, shadow and mirror
+ * rays of both eyes, one persistent kernel), [2] resolve to float RGB.
  * Returns RT_ERR_INVALID_ARG if profiling was off during the last render.
  */
-#define RT_NUM_STAGES 6
+#define RT_NUM_STAGES 3
 int rt_profile_enable(rt_scene* scene, int on);
 int rt_profile_read(const rt_scene* scene, float* ms);
 

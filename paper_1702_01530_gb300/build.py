@@ -48,13 +48,17 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(p) <= t for p in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
-    if not force and not extra_flags and up_to_date():
+def build(force: bool = False, verbose: bool = False, extra_flags=(), out_dir: str | None = None) -> str:
+    """Compile and link; ``extra_flags`` (e.g. tuning macros) and ``out_dir``
+    build a variant library elsewhere without touching the default one."""
+    if not force and not extra_flags and out_dir is None and up_to_date():
         return LIB
-    os.makedirs(OUT_DIR, exist_ok=True)
+    odir = out_dir or OUT_DIR
+    lib_path = os.path.join(odir, "librtstereo.so")
+    os.makedirs(odir, exist_ok=True)
     cc = nvcc()
     srcs = _sources()
-    objs = [os.path.join(OUT_DIR, os.path.basename(s)[:-3] + ".o") for s in srcs]
+    objs = [os.path.join(odir, os.path.basename(s)[:-3] + ".o") for s in srcs]
 
     def compile_one(src_obj):
         src, obj = src_obj
@@ -71,13 +75,13 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     if verbose:
         for lg in logs:
             sys.stderr.write(lg)
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib_path + f".tmp{os.getpid()}"
     r = subprocess.run([cc, *ARCH, "-shared", "-Xcompiler", "-fPIC", *objs, "-o", tmp],
                        capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":

@@ -190,7 +190,7 @@ def rt_debug_set_node(scene, node, left, right, empty_right=False):
     _check(lib().rt_debug_set_node(scene, node, left, right, int(bool(empty_right))))
 
 
-STAGES = ("clear", "primary", "shadow0", "reflect", "shadowN", "resolve")
+STAGES = ("clear", "trace", "resolve")
 
 
 def rt_profile_enable(scene, on=True):

@@ -59,35 +59,37 @@ void free_workspace(rt::Workspace& ws) {
   ws = rt::Workspace();
 }
 
-// grow the scene's scratch to hold a W x H stereo pair with L lights
+// grow the scene's scratch to hold a W x H stereo pair with L lights:
+// fixed-point accumulators for both eyes and, per resident warp of the
+// render kernel, a shadow queue of 32 L + 32 and a mirror queue of 64
+// entries (48 B each)
 int ensure_workspace(const rt_scene* sc_c, uint32_t W, uint32_t H) {
   rt_scene* sc = const_cast<rt_scene*>(sc_c);
   rt::Workspace& ws = sc->ws;
-  const uint64_t P = (uint64_t)W * H;
-  const uint64_t rays = 2 * P;
-  if (ws.base && ws.cap_rays >= rays && ws.L >= sc->nl) return RT_OK;
-  const uint64_t cap_rays = rays, cap_shadow = rays * sc->nl;
-  size_t b_acc = align256(rays * 3 * sizeof(uint32_t));
-  size_t b_q = align256(cap_rays * 3 * sizeof(float4));
-  size_t b_s = align256(cap_shadow * 3 * sizeof(float4));
+  const uint64_t pixels = 2ull * W * H;
+  const uint64_t n_warps = (uint64_t)rt::render_grid() * (rt::render_threads() / 32);
+  const uint32_t cap_s = 32u * sc->nl + 32u, cap_r = 64u;
+  if (ws.base && ws.cap_pixels >= pixels && ws.L == sc->nl && ws.n_warps >= n_warps) return RT_OK;
+  const uint64_t cap_pixels = ws.cap_pixels > pixels ? ws.cap_pixels : pixels;
+  size_t b_acc = align256(cap_pixels * 3 * sizeof(uint32_t));
+  size_t b_q = align256(n_warps * (cap_s + cap_r) * 3 * sizeof(float4));
   size_t b_c = align256(rt::C_TOTAL * sizeof(uint32_t));
-  size_t total = b_acc + 2 * b_q + b_s + b_c;
+  size_t total = b_acc + b_q + b_c;
   void* base = nullptr;
   cudaError_t e = cudaMalloc(&base, total);
   if (e != cudaSuccess) { cudaGetLastError(); return cuda_fail(e, "workspace allocation"); }
   if (ws.base) cudaFree(ws.base);
-  ws.base = nullptr;
   char* p = static_cast<char*>(base);
   ws.base = base;
   ws.bytes = total;
   ws.accum = reinterpret_cast<uint32_t*>(p); p += b_acc;
-  ws.queue[0] = reinterpret_cast<float4*>(p); p += b_q;
-  ws.queue[1] = reinterpret_cast<float4*>(p); p += b_q;
-  ws.shadow = reinterpret_cast<float4*>(p); p += b_s;
+  ws.wq = reinterpret_cast<float4*>(p); p += b_q;
   ws.counters = reinterpret_cast<uint32_t*>(p);
-  ws.cap_rays = cap_rays;
-  ws.cap_shadow = cap_shadow;
-  ws.W = W; ws.H = H; ws.L = sc->nl;
+  ws.cap_s = cap_s;
+  ws.cap_r = cap_r;
+  ws.n_warps = n_warps;
+  ws.cap_pixels = cap_pixels;
+  ws.L = sc->nl;
   return RT_OK;
 }
 

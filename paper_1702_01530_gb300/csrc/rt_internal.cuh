@@ -57,38 +57,35 @@ struct Workspace {
   size_t bytes = 0;
   void* base = nullptr;
   uint32_t* accum = nullptr;     // 2*P*3 fixed-point colour sums
-  float4* queue[2] = {nullptr, nullptr};  // reflection rays, 3 float4 each
-  float4* shadow = nullptr;      // shadow rays, 3 float4 each
+  float4* wq = nullptr;          // warp queues: n_warps x (cap_s + cap_r) x 3 float4
   uint32_t* counters = nullptr;  // see Counter enum
-  uint64_t cap_rays = 0;         // entries per reflection queue (2*P)
-  uint64_t cap_shadow = 0;       // shadow entries (2*P*L)
+  uint32_t cap_s = 0, cap_r = 0; // shadow / mirror entries per warp
+  uint64_t n_warps = 0;          // warps the queues are sized for
+  uint64_t cap_pixels = 0;       // 2*P the accumulators are sized for
   float4* frame = nullptr;       // frame buffers for rt_render_stereo_host
   size_t frame_bytes = 0;
-  uint32_t W = 0, H = 0, L = 0;
+  uint32_t L = 0;
   // stage timing (CUDA events on the render stream), see Stage
   bool profile = false;
-  cudaEvent_t ev[2 * RT_MAX_DEPTH + 8] = {};
-  int ev_stage[2 * RT_MAX_DEPTH + 8] = {};   // stage that ends at event k
+  cudaEvent_t ev[8] = {};
+  int ev_stage[8] = {};          // stage that ends at event k
   int n_ev = 0;
 };
 
 // stages of one render, in launch order
 enum Stage : int {
   ST_CLEAR = 0,     // counter and accumulator clears
-  ST_PRIMARY = 1,   // primary rays: generate, closest hit, shade, enqueue
-  ST_SHADOW0 = 2,   // any-hit of the primary hits' shadow rays
-  ST_REFLECT = 3,   // closest hit + shade of mirror rays, all depths
-  ST_SHADOWN = 4,   // any-hit of the mirror hits' shadow rays, all depths
-  ST_RESOLVE = 5,   // fixed-point sums to float RGB
-  ST_COUNT = 6
+  ST_TRACE = 1,     // all rays: primary, shadow and mirror (one persistent kernel)
+  ST_RESOLVE = 2,   // fixed-point sums to float RGB
+  ST_COUNT = 3
 };
 
 // counters block layout (uint32 each)
 enum Counter : int {
-  C_WORK = 0,                     // [0, 2*(RT_MAX_DEPTH+1)): persistent work counters
-  C_QLEN = 2 * (RT_MAX_DEPTH + 1),  // [.., +RT_MAX_DEPTH+2): reflection queue length per depth
-  C_SLEN = C_QLEN + RT_MAX_DEPTH + 2,  // [.., +RT_MAX_DEPTH+1): shadow queue length per depth
-  C_TOTAL = C_SLEN + RT_MAX_DEPTH + 1
+  C_TILE = 0,       // next primary tile
+  C_SHADOW = 1,     // shadow rays enqueued (all warps)
+  C_REFL = 2,       // mirror rays enqueued (all warps)
+  C_TOTAL = 4
 };
 
 struct RenderArgs {
@@ -114,6 +111,8 @@ cudaError_t build_lbvh(const float4* d_sph_in, const float* d_tri_in, uint32_t n
 size_t lbvh_tmp_bytes(uint32_t n);
 cudaError_t render(const RenderArgs& a, Workspace& ws, cudaStream_t st);
 int num_sms();
+int render_grid();      // persistent blocks of the render kernel
+int render_threads();   // threads per block of the render kernel
 
 }  // namespace rt
 

@@ -3,18 +3,21 @@
 // Paper Sec. 3: the left and right channel are independent ("parallel level
 // 1") and the pixels of a channel are traced in parallel ("parallel level 2");
 // the image is split into parts processed by parallel workers (Figure 1).
-// Here both eyes share one launch: persistent warps pull 32-ray batches from
-// a global counter, and the primary batches are 8x4-pixel tiles that
-// alternate left / right eye, so the two eyes' nearly identical rays touch
-// the same BVH nodes close together in time.
+// Here both eyes share one persistent launch: warps pull 8x4-pixel tiles from
+// a global counter, tiles alternating left / right eye, so the two eyes'
+// nearly identical rays touch the same BVH nodes close together in time.
 //
-// Per stereo pair (D = max_depth):
-//   k_trace<PRIMARY>    primary rays of both eyes: generate, closest hit,
-//                       shade; push shadow rays (queue S) and mirror rays
-//                       (queue Q1)
-//   k_shadow            any-hit over S; unblocked contributions accumulate
-//   for d = 1..D: k_trace<REFLECT> over Q_d (push S, Q_{d+1}), k_shadow
-//   k_resolve           fixed-point sums -> float RGB, clamp to [0,1]
+// Per stereo pair:
+//   k_render   one persistent kernel. Every warp owns two small wavefront
+//              queues in global memory (L2-resident): shadow rays and mirror
+//              rays produced by its own shading. Each round the warp picks,
+//              warp-uniformly, 32 queued shadow rays (any-hit), else 32
+//              queued mirror rays (closest hit + shade), else a new primary
+//              tile (generate + closest hit + shade); when the tiles are gone
+//              it drains its queues. Rounds are full warps except the final
+//              drain, no ray waits for a later launch, and there is one
+//              launch tail per frame instead of one per bounce depth.
+//   k_resolve  fixed-point sums -> float RGB, clamp to [0,1]
 //
 // Colour sums are fixed-point uint32 per channel (atomic adds of
 // round(value * 2^k)): integer addition is associative, so the image does
@@ -35,6 +38,20 @@
 namespace rt {
 namespace {
 
+// Tuning knobs (compile-time): RT_MIN_BLOCKS = minimum resident blocks per
+// SM requested from the register allocator (0 = no request; 10 measured
+// best on GB300: 48 registers, 40 warps per SM); RT_WHILE_WHILE = 1
+// postpones the first leaf a ray meets and keeps descending until every
+// active lane of the warp holds a leaf, so the leaf tests of a warp run
+// together instead of interleaving with node visits (the "while-while" loop
+// of Aila & Laine, HPG 2009) -- 20 % slower here with one primitive per leaf,
+// hence off by default.
+#ifndef RT_MIN_BLOCKS
+#define RT_MIN_BLOCKS 10
+#endif
+#ifndef RT_WHILE_WHILE
+#define RT_WHILE_WHILE 0
+#endif
 constexpr int kThreads = 128;
 constexpr float kRobust = 1.00000036f;   // 1 + 2*gamma_3 (Ize 2013): conservative slab exit
 
@@ -179,19 +196,112 @@ __device__ __forceinline__ bool traverse(const DeviceScene& sc, V3 o, V3 d, floa
   return any;
 }
 
-__device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31; }
 
-// warp-aggregated reservation of one slot per thread with pred set
-__device__ __forceinline__ uint32_t reserve(uint32_t* ctr, bool pred, uint32_t& slot) {
-  const uint32_t mask = __ballot_sync(__activemask(), pred);
-  if (!pred) return 0;
-  const uint32_t leader = __ffs(mask) - 1;
-  uint32_t base = 0;
-  if (lane_id() == leader) base = atomicAdd(ctr, (uint32_t)__popc(mask));
-  base = __shfl_sync(mask, base, leader);
-  slot = base + __popc(mask & ((1u << lane_id()) - 1u));
-  return 1;
+#if RT_WHILE_WHILE
+// Same traversal with postponed leaves. Internal nodes are visited until
+// every active lane of the warp holds one pending leaf (or has finished);
+// then the pending leaves (and any leaves that follow directly) are tested.
+template <bool ANY, bool COUNT>
+__device__ __forceinline__ bool traverse_ww(const DeviceScene& sc, V3 o, V3 d, float tmax,
+                                            float& t_best, uint32_t& id_best, uint32_t& k_best,
+                                            WorkCount& wc, uint32_t* err) {
+  constexpr int32_t kDone = 0x7FFFFFFF;   // larger than any internal node index
+  const V3 idir = v3(safe_rcp(d.x), safe_rcp(d.y), safe_rcp(d.z));
+  const V3 ood = v3(o.x * idir.x, o.y * idir.y, o.z * idir.z);
+  int32_t stack[kStackSize];
+  int sp = 0;
+  const uint32_t n = sc.n_prims;
+  int32_t node = n == 1 ? ~0 : 0;
+  int32_t leaf = 0;
+  const uint32_t it_max = 2u * n + 64u;
+  uint32_t it = 0;
+  float tcur = ANY ? tmax : t_best;
+  bool any = false;
+  if (node < 0) { leaf = node; node = kDone; }
+  while (node != kDone || leaf != 0) {
+    while ((uint32_t)node < (uint32_t)kDone) {   // node >= 0 and not done
+      if (++it > it_max) { atomicOr(err, ERR_ITER); node = kDone; leaf = 0; break; }
+      if ((uint32_t)node >= n - 1) { atomicOr(err, ERR_INDEX); node = kDone; leaf = 0; break; }
+      const float4* np = sc.nodes + 4 * (size_t)node;
+      const float4 a = __ldg(np), b = __ldg(np + 1), c = __ldg(np + 2), e = __ldg(np + 3);
+      if (COUNT) wc.inner++;
+      const float l0x = fmaf(a.x, idir.x, -ood.x), h0x = fmaf(a.y, idir.x, -ood.x);
+      const float l0y = fmaf(a.z, idir.y, -ood.y), h0y = fmaf(a.w, idir.y, -ood.y);
+      const float l0z = fmaf(c.x, idir.z, -ood.z), h0z = fmaf(c.y, idir.z, -ood.z);
+      const float l1x = fmaf(b.x, idir.x, -ood.x), h1x = fmaf(b.y, idir.x, -ood.x);
+      const float l1y = fmaf(b.z, idir.y, -ood.y), h1y = fmaf(b.w, idir.y, -ood.y);
+      const float l1z = fmaf(c.z, idir.z, -ood.z), h1z = fmaf(c.w, idir.z, -ood.z);
+      const float in0 = fmax3(fminf(l0x, h0x), fminf(l0y, h0y), fmaxf(fminf(l0z, h0z), 0.f));
+      const float out0 = fmin3(fmaxf(l0x, h0x), fmaxf(l0y, h0y), fminf(fmaxf(l0z, h0z), tcur));
+      const float in1 = fmax3(fminf(l1x, h1x), fminf(l1y, h1y), fmaxf(fminf(l1z, h1z), 0.f));
+      const float out1 = fmin3(fmaxf(l1x, h1x), fmaxf(l1y, h1y), fminf(fmaxf(l1z, h1z), tcur));
+      const bool hit0 = in0 <= out0 * kRobust;
+      const bool hit1 = in1 <= out1 * kRobust;
+      const int32_t cl = __float_as_int(e.x), cr = __float_as_int(e.y);
+      if (hit0 && hit1) {
+        const bool swap = in1 < in0;
+        if (sp >= kStackSize) { atomicOr(err, ERR_STACK); node = kDone; leaf = 0; break; }
+        stack[sp++] = swap ? cl : cr;
+        node = swap ? cr : cl;
+      } else if (hit0 | hit1) {
+        node = hit0 ? cl : cr;
+      } else {
+        node = sp ? stack[--sp] : kDone;
+      }
+      if (node < 0 && leaf == 0) {           // postpone this leaf, keep descending
+        leaf = node;
+        node = sp ? stack[--sp] : kDone;
+      }
+      if (!__any_sync(__activemask(), leaf == 0)) break;
+    }
+    while (leaf < 0) {
+      if (++it > it_max) { atomicOr(err, ERR_ITER); node = kDone; leaf = 0; break; }
+      const uint32_t k = (uint32_t)~leaf;
+      if (k >= n) { atomicOr(err, ERR_INDEX); node = kDone; leaf = 0; break; }
+      const float4* pp = sc.prims + 3 * (size_t)k;
+      const float4 p0 = __ldg(pp), p1 = __ldg(pp + 1);
+      const uint32_t id = __float_as_uint(p0.w);
+      float t;
+      bool h;
+      if (id < sc.n_spheres) {
+        if (COUNT) wc.sphere++;
+        h = hit_sphere(p0, p1.x, o, d, t);
+      } else {
+        if (COUNT) wc.tri++;
+        h = hit_tri(p0, p1, __ldg(pp + 2), o, d, t);
+      }
+      if (ANY) {
+        if (h && t < tmax) { any = true; node = kDone; leaf = 0; break; }
+      } else if (h && (t < tcur || (t == tcur && id < id_best))) {
+        tcur = t;
+        id_best = id;
+        k_best = k;
+        any = true;
+      }
+      leaf = 0;
+      if (node < 0) {                         // the next node is a leaf too
+        leaf = node;
+        node = sp ? stack[--sp] : kDone;
+      }
+    }
+  }
+  if (!ANY) t_best = tcur;
+  return any;
 }
+#endif
+
+template <bool ANY, bool COUNT>
+__device__ __forceinline__ bool trace_ray(const DeviceScene& sc, V3 o, V3 d, float tmax,
+                                          float& t_best, uint32_t& id_best, uint32_t& k_best,
+                                          WorkCount& wc, uint32_t* err) {
+#if RT_WHILE_WHILE
+  return traverse_ww<ANY, COUNT>(sc, o, d, tmax, t_best, id_best, k_best, wc, err);
+#else
+  return traverse<ANY, COUNT>(sc, o, d, tmax, t_best, id_best, k_best, wc, err);
+#endif
+}
+
+__device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31; }
 
 __device__ __forceinline__ void accumulate(uint32_t* acc, uint32_t pix, float r, float g, float b,
                                            float scale) {
@@ -204,12 +314,10 @@ __device__ __forceinline__ void accumulate(uint32_t* acc, uint32_t pix, float r,
 struct KParams {
   RenderArgs a;
   uint32_t* accum;
-  const float4* qin;
-  float4* qout;
-  float4* shadow;
+  float4* wq;          // warp queues: per warp cap_s shadow then cap_r mirror entries
   uint32_t* counters;
-  uint64_t cap_rays, cap_shadow;
-  uint32_t depth;
+  uint32_t cap_s, cap_r;
+  uint32_t n_tiles;    // 2 * tiles_x * tiles_y
 };
 
 __device__ __forceinline__ void flush_work(const WorkCount& wc, uint64_t* work, int kind) {
@@ -226,93 +334,138 @@ __device__ __forceinline__ void flush_work(const WorkCount& wc, uint64_t* work, 
   }
 }
 
-// Closest-hit + shading kernel. PRIMARY: rays come from the camera, one
-// 8x4-pixel tile per 32 slots, tiles alternating eyes. Otherwise the rays
-// are read from the reflection queue of this depth.
-template <bool PRIMARY, bool COUNT>
-__global__ void __launch_bounds__(kThreads) k_trace(KParams kp) {
+enum Mode : int { M_SHADOW = 0, M_PRIMARY = 1, M_MIRROR = 2 };
+
+// Shadow queue entry: (origin | pixel) (direction | t_max) (contribution | 0)
+// Mirror queue entry: (origin | pixel) (direction | depth) (weight | 0)
+template <bool COUNT>
+__global__ void
+#if RT_MIN_BLOCKS > 0
+__launch_bounds__(kThreads, RT_MIN_BLOCKS)
+#else
+__launch_bounds__(kThreads)
+#endif
+k_render(KParams kp) {
   const RenderArgs& a = kp.a;
   const CameraParams& cam = a.cam;
   const uint32_t P = cam.W * cam.H;
-  // queue lengths are clamped to the capacity: entries past it were never written
-  const uint32_t n = PRIMARY ? 2u * cam.tiles_x * cam.tiles_y * 32u
-                             : (uint32_t)min((uint64_t)*(volatile uint32_t*)&kp.counters[C_QLEN + kp.depth],
-                                             kp.cap_rays);
-  uint32_t* work_ctr = &kp.counters[C_WORK + 2 * kp.depth];
-  WorkCount wc = {0, 0, 0};
-  for (;;) {
-    uint32_t base = 0;
-    if (lane_id() == 0) base = atomicAdd(work_ctr, 32u);
-    base = __shfl_sync(0xFFFFFFFFu, base, 0);
-    if (base >= n) break;
-    const uint32_t idx = base + lane_id();
-    bool active = idx < n;
+  const uint32_t lane = lane_id();
+  const uint32_t lt_mask = (1u << lane) - 1u;
+  const size_t gwarp = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  float4* const S = kp.wq + gwarp * 3 * (size_t)(kp.cap_s + kp.cap_r);
+  float4* const R = S + 3 * (size_t)kp.cap_s;
+  uint32_t nS = 0, nR = 0;          // warp-uniform queue fills
+  uint32_t made_s = 0, made_r = 0;  // rays this warp enqueued
+  bool tiles_left = true;
+  WorkCount wc_p = {0, 0, 0}, wc_s = {0, 0, 0}, wc_r = {0, 0, 0};
+  const uint32_t L = a.sc.n_lights;
+
+  for (uint32_t round = 0;; ++round) {
+    if (round > (1u << 30)) { if (lane == 0) atomicOr(a.err, ERR_ITER); break; }
+    // ---------------------------------------------- warp-uniform schedule
+    int mode;
+    uint32_t take = 0, base = 0, tile = 0;
+    if (nS >= 32) { mode = M_SHADOW; take = 32; nS -= 32; base = nS; }
+    else if (nR >= 32) { mode = M_MIRROR; take = 32; nR -= 32; base = nR; }
+    else if (tiles_left) {
+      uint32_t t = 0;
+      if (lane == 0) t = atomicAdd(&kp.counters[C_TILE], 1u);
+      t = __shfl_sync(0xFFFFFFFFu, t, 0);
+      if (t >= kp.n_tiles) { tiles_left = false; continue; }
+      mode = M_PRIMARY; tile = t;
+    }
+    else if (nS > 0) { mode = M_SHADOW; take = nS; base = 0; nS = 0; }
+    else if (nR > 0) { mode = M_MIRROR; take = nR; base = 0; nR = 0; }
+    else break;
+
+    if (mode == M_SHADOW) {
+      // ------------------------------------------------ any-hit round
+      if (lane < take) {
+        const float4* e = S + 3 * (size_t)(base + lane);
+        const float4 s0 = e[0], s1 = e[1];
+        float tb = 0.f;
+        uint32_t id = 0, k = 0;
+        const bool blocked = trace_ray<true, COUNT>(a.sc, xyz(s0), xyz(s1), s1.w, tb, id, k, wc_s, a.err);
+        if (!blocked) {
+          const float4 s2 = e[2];
+          accumulate(kp.accum, __float_as_uint(s0.w), s2.x, s2.y, s2.z, a.color_scale);
+        }
+      }
+      __syncwarp();
+      continue;
+    }
+
+    // ------------------------------------------- closest hit + shading
+    bool active;
     V3 o, d, w = v3(1.f, 1.f, 1.f);
-    uint32_t pix = 0;
-    if (PRIMARY) {
-      const uint32_t tile = idx >> 5, ln = idx & 31u;
+    uint32_t pix = 0, depth = 0;
+    if (mode == M_PRIMARY) {
       const uint32_t eye = tile & 1u, tt = tile >> 1;
-      const uint32_t px = (tt % cam.tiles_x) * 8u + (ln & 7u);
-      const uint32_t py = (tt / cam.tiles_x) * 4u + (ln >> 3);
-      active = active && px < cam.W && py < cam.H;
+      const uint32_t px = (tt % cam.tiles_x) * 8u + (lane & 7u);
+      const uint32_t py = (tt / cam.tiles_x) * 4u + (lane >> 3);
+      active = px < cam.W && py < cam.H;
       pix = eye * P + py * cam.W + px;
       const float nx = (2.f * ((float)px + 0.5f) / (float)cam.W - 1.f) * cam.tan_x;
       const float ny = (1.f - 2.f * ((float)py + 0.5f) / (float)cam.H) * cam.tan_y;
       const V3 E = v3(cam.eye[0], cam.eye[1], cam.eye[2]);
-      const V3 R = v3(cam.right[0], cam.right[1], cam.right[2]);
+      const V3 Rt = v3(cam.right[0], cam.right[1], cam.right[2]);
       const V3 U = v3(cam.up[0], cam.up[1], cam.up[2]);
       const V3 F = v3(cam.fwd[0], cam.fwd[1], cam.fwd[2]);
-      const V3 Q = E + (F + R * nx + U * ny) * cam.zc;
-      o = E + R * (eye ? cam.half_sep : -cam.half_sep);
+      const V3 Q = E + (F + Rt * nx + U * ny) * cam.zc;
+      o = E + Rt * (eye ? cam.half_sep : -cam.half_sep);
       d = normalize(Q - o);
-    } else if (active) {
-      const float4 q0 = kp.qin[3 * (size_t)idx], q1 = kp.qin[3 * (size_t)idx + 1],
-                   q2 = kp.qin[3 * (size_t)idx + 2];
-      o = xyz(q0);
-      pix = __float_as_uint(q0.w);
-      d = xyz(q1);
-      w = xyz(q2);
+    } else {
+      active = lane < take;
+      if (active) {
+        const float4* e = R + 3 * (size_t)(base + lane);
+        const float4 q0 = e[0], q1 = e[1], q2 = e[2];
+        o = xyz(q0);
+        pix = __float_as_uint(q0.w);
+        d = xyz(q1);
+        depth = __float_as_uint(q1.w);
+        w = xyz(q2);
+      }
+      __syncwarp();  // every lane has read its entry before the slots are refilled
     }
     float t = INFINITY;
     uint32_t id = RT_MISS_ID, k = 0;
     bool hit = false;
-    if (active) hit = traverse<false, COUNT>(a.sc, o, d, INFINITY, t, id, k, wc, a.err);
+    if (active)
+      hit = trace_ray<false, COUNT>(a.sc, o, d, INFINITY, t, id, k,
+                                   mode == M_PRIMARY ? wc_p : wc_r, a.err);
+    __syncwarp();
 
-    // ------------------------------------------------------------ shading
-    float amb_r = 0.f, amb_g = 0.f, amb_b = 0.f;
-    V3 p = v3(0.f, 0.f, 0.f), nrm = v3(0.f, 0.f, 1.f), o2;
+    V3 p = v3(0.f, 0.f, 0.f), nrm = v3(0.f, 0.f, 1.f);
     float4 mat = make_float4(0.f, 0.f, 0.f, 0.f);
     float eps = 0.f;
     if (active) {
+      float ar, ag, ab;
       if (!hit) {
-        amb_r = w.x * kBgR; amb_g = w.y * kBgG; amb_b = w.z * kBgB;
+        ar = w.x * kBgR; ag = w.y * kBgG; ab = w.z * kBgB;
       } else {
         const float4* pp = a.sc.prims + 3 * (size_t)k;
         const float4 p0 = __ldg(pp), p1 = __ldg(pp + 1);
         p = o + d * t;
         uint32_t mid = __float_as_uint(p1.w);
-        if (id < a.sc.n_spheres) {
-          nrm = (p - xyz(p0)) * (1.f / p1.x);
-        } else {
-          nrm = normalize(cross(xyz(p1), xyz(__ldg(pp + 2))));
-        }
+        if (id < a.sc.n_spheres) nrm = (p - xyz(p0)) * (1.f / p1.x);
+        else nrm = normalize(cross(xyz(p1), xyz(__ldg(pp + 2))));
         if (dot(nrm, d) > 0.f) nrm = nrm * -1.f;
         if (mid >= a.sc.n_mats) { atomicOr(a.err, ERR_INDEX); mid = 0; }
         mat = __ldg(a.sc.mats + mid);
         const float kd = (1.f - mat.w) * kAmbient;
-        amb_r = w.x * kd * mat.x; amb_g = w.y * kd * mat.y; amb_b = w.z * kd * mat.z;
+        ar = w.x * kd * mat.x; ag = w.y * kd * mat.y; ab = w.z * kd * mat.z;
         eps = 1e-4f * fmaxf(1.f, fmax3(fabsf(p.x), fabsf(p.y), fabsf(p.z)));
       }
-      accumulate(kp.accum, pix, amb_r, amb_g, amb_b, a.color_scale);
+      accumulate(kp.accum, pix, ar, ag, ab, a.color_scale);
     }
-    o2 = p + nrm * eps;
-    // shadow rays: one per light facing the surface
-    const uint32_t L = a.sc.n_lights;
+    const bool lit = active && hit;
+    const V3 o2 = p + nrm * eps;
+    // shadow rays into this warp's queue, one per light facing the surface
     for (uint32_t l = 0; l < L; ++l) {
       bool emit = false;
       V3 lh = v3(0.f, 0.f, 1.f);
       float ld = 0.f, ndl = 0.f;
-      if (active && hit) {
+      if (lit) {
         const float4 lp = __ldg(a.sc.lights + l);
         const V3 lv = xyz(lp) - o2;
         const float inv = rsqrtf(dot(lv, lv));
@@ -322,33 +475,31 @@ __global__ void __launch_bounds__(kThreads) k_trace(KParams kp) {
         emit = ndl > 0.f;
         ndl *= lp.w * (1.f - mat.w);
       }
-      uint32_t slot;
-      if (reserve(&kp.counters[C_SLEN + kp.depth], emit, slot)) {
-        if (slot < kp.cap_shadow) {
-          float4* s = kp.shadow + 3 * (size_t)slot;
-          s[0] = make_float4(o2.x, o2.y, o2.z, __uint_as_float(pix));
-          s[1] = make_float4(lh.x, lh.y, lh.z, ld - eps);
-          s[2] = make_float4(w.x * ndl * mat.x, w.y * ndl * mat.y, w.z * ndl * mat.z, 0.f);
-        } else {
-          atomicOr(a.err, ERR_QUEUE);
-        }
+      const uint32_t m = __ballot_sync(0xFFFFFFFFu, emit);
+      const uint32_t slot = nS + __popc(m & lt_mask);
+      if (emit && slot < kp.cap_s) {
+        float4* e = S + 3 * (size_t)slot;
+        e[0] = make_float4(o2.x, o2.y, o2.z, __uint_as_float(pix));
+        e[1] = make_float4(lh.x, lh.y, lh.z, ld - eps);
+        e[2] = make_float4(w.x * ndl * mat.x, w.y * ndl * mat.y, w.z * ndl * mat.z, 0.f);
       }
+      nS += __popc(m);
+      made_s += __popc(m);
     }
-    // mirror ray
-    const bool refl = active && hit && mat.w > 0.f && kp.depth < a.max_depth;
-    uint32_t slot;
-    if (reserve(&kp.counters[C_QLEN + kp.depth + 1], refl, slot)) {
-      if (slot < kp.cap_rays) {
-        V3 rd = normalize(d - nrm * (2.f * dot(d, nrm)));
-        float4* q = kp.qout + 3 * (size_t)slot;
-        q[0] = make_float4(o2.x, o2.y, o2.z, __uint_as_float(pix));
-        q[1] = make_float4(rd.x, rd.y, rd.z, 0.f);
-        q[2] = make_float4(w.x * mat.w, w.y * mat.w, w.z * mat.w, 0.f);
-      } else {
-        atomicOr(a.err, ERR_QUEUE);
-      }
+    // mirror ray into this warp's queue
+    const bool refl = lit && mat.w > 0.f && depth < a.max_depth;
+    const uint32_t mr = __ballot_sync(0xFFFFFFFFu, refl);
+    const uint32_t rslot = nR + __popc(mr & lt_mask);
+    if (refl && rslot < kp.cap_r) {
+      const V3 rd = normalize(d - nrm * (2.f * dot(d, nrm)));
+      float4* e = R + 3 * (size_t)rslot;
+      e[0] = make_float4(o2.x, o2.y, o2.z, __uint_as_float(pix));
+      e[1] = make_float4(rd.x, rd.y, rd.z, __uint_as_float(depth + 1));
+      e[2] = make_float4(w.x * mat.w, w.y * mat.w, w.z * mat.w, 0.f);
     }
-    if (PRIMARY && active) {
+    nR += __popc(mr);
+    made_r += __popc(mr);
+    if (mode == M_PRIMARY && active) {
       const uint32_t eye = pix >= P;
       const uint32_t pi = pix - eye * P;
       uint32_t* hid = eye ? a.hit_R : a.hit_L;
@@ -356,37 +507,21 @@ __global__ void __launch_bounds__(kThreads) k_trace(KParams kp) {
       if (hid) hid[pi] = id;
       if (dep) dep[pi] = hit ? t * dot(d, v3(cam.fwd[0], cam.fwd[1], cam.fwd[2])) : INFINITY;
     }
-  }
-  if (COUNT) flush_work(wc, a.work, PRIMARY ? 0 : 2);
-}
-
-// Any-hit over the shadow queue of this depth; unblocked rays add their
-// precomputed contribution to the pixel.
-template <bool COUNT>
-__global__ void __launch_bounds__(kThreads) k_shadow(KParams kp) {
-  const RenderArgs& a = kp.a;
-  const uint32_t n = (uint32_t)min((uint64_t)*(volatile uint32_t*)&kp.counters[C_SLEN + kp.depth],
-                                   kp.cap_shadow);
-  uint32_t* work_ctr = &kp.counters[C_WORK + 2 * kp.depth + 1];
-  WorkCount wc = {0, 0, 0};
-  for (;;) {
-    uint32_t base = 0;
-    if (lane_id() == 0) base = atomicAdd(work_ctr, 32u);
-    base = __shfl_sync(0xFFFFFFFFu, base, 0);
-    if (base >= n) break;
-    const uint32_t idx = base + lane_id();
-    if (idx >= n) continue;
-    const float4* s = kp.shadow + 3 * (size_t)idx;
-    const float4 s0 = s[0], s1 = s[1];
-    float tb = 0.f;
-    uint32_t id = 0, k = 0;
-    const bool blocked = traverse<true, COUNT>(a.sc, xyz(s0), xyz(s1), s1.w, tb, id, k, wc, a.err);
-    if (!blocked) {
-      const float4 s2 = s[2];
-      accumulate(kp.accum, __float_as_uint(s0.w), s2.x, s2.y, s2.z, a.color_scale);
+    if (nS > kp.cap_s || nR > kp.cap_r) {  // cannot happen by construction; writes were skipped
+      if (lane == 0) atomicOr(a.err, ERR_QUEUE);
+      break;
     }
+    __syncwarp();
   }
-  if (COUNT) flush_work(wc, a.work, 1);
+  if (lane == 0) {
+    atomicAdd(&kp.counters[C_SHADOW], made_s);
+    atomicAdd(&kp.counters[C_REFL], made_r);
+  }
+  if (COUNT) {
+    flush_work(wc_p, a.work, 0);
+    flush_work(wc_s, a.work, 1);
+    flush_work(wc_r, a.work, 2);
+  }
 }
 
 __global__ void k_resolve(const uint32_t* __restrict__ acc, float* __restrict__ out_L,
@@ -397,24 +532,20 @@ __global__ void k_resolve(const uint32_t* __restrict__ acc, float* __restrict__ 
   }
 }
 
-__global__ void k_counts(const uint32_t* counters, uint32_t max_depth, uint64_t primary,
-                         uint64_t* out) {
+__global__ void k_counts(const uint32_t* counters, uint64_t primary, uint64_t* out) {
   if (threadIdx.x != 0) return;
-  uint64_t sh = 0, rf = 0;
-  for (uint32_t d = 0; d <= max_depth; ++d) sh += counters[C_SLEN + d];
-  for (uint32_t d = 1; d <= max_depth; ++d) rf += counters[C_QLEN + d];
   out[0] = primary;
-  out[1] = sh;
-  out[2] = rf;
+  out[1] = counters[C_SHADOW];
+  out[2] = counters[C_REFL];
 }
 
-template <typename K>
-int grid_for(K kernel) {
+template <bool COUNT>
+int blocks_per_sm() {
   static int cached = 0;
   if (!cached) {
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, 0);
-    cached = num_sms() * (per_sm > 0 ? per_sm : 1);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render<COUNT>, kThreads, 0);
+    cached = per_sm > 0 ? per_sm : 1;
   }
   return cached;
 }
@@ -425,10 +556,13 @@ cudaError_t render_impl(const RenderArgs& a, Workspace& ws, cudaStream_t st) {
   KParams kp;
   kp.a = a;
   kp.accum = ws.accum;
-  kp.shadow = ws.shadow;
+  kp.wq = ws.wq;
   kp.counters = ws.counters;
-  kp.cap_rays = ws.cap_rays;
-  kp.cap_shadow = ws.cap_shadow;
+  kp.cap_s = ws.cap_s;
+  kp.cap_r = ws.cap_r;
+  kp.n_tiles = 2u * a.cam.tiles_x * a.cam.tiles_y;
+  const int grid = render_grid();
+  if ((uint64_t)grid * (kThreads / 32) > ws.n_warps) return cudaErrorInvalidValue;
   ws.n_ev = 0;
   auto mark = [&](int stage) {  // stage timing: an event after each stage
     if (!ws.profile) return;
@@ -440,24 +574,12 @@ cudaError_t render_impl(const RenderArgs& a, Workspace& ws, cudaStream_t st) {
   cudaMemsetAsync(ws.accum, 0, 2 * P * 3 * sizeof(uint32_t), st);
   if (a.work) cudaMemsetAsync(a.work, 0, 9 * sizeof(uint64_t), st);
   mark(ST_CLEAR);
-  for (uint32_t d = 0; d <= a.max_depth; ++d) {
-    kp.depth = d;
-    kp.qin = ws.queue[d & 1];
-    kp.qout = ws.queue[(d + 1) & 1];
-    if (d == 0) {
-      k_trace<true, COUNT><<<grid_for(k_trace<true, COUNT>), kThreads, 0, st>>>(kp);
-      mark(ST_PRIMARY);
-    } else {
-      k_trace<false, COUNT><<<grid_for(k_trace<false, COUNT>), kThreads, 0, st>>>(kp);
-      mark(ST_REFLECT);
-    }
-    k_shadow<COUNT><<<grid_for(k_shadow<COUNT>), kThreads, 0, st>>>(kp);
-    mark(d == 0 ? ST_SHADOW0 : ST_SHADOWN);
-  }
+  k_render<COUNT><<<grid, kThreads, 0, st>>>(kp);
+  mark(ST_TRACE);
   const uint32_t n3 = (uint32_t)(P * 3);
   k_resolve<<<num_sms() * 8, 256, 0, st>>>(ws.accum, a.out_L, a.out_R, n3, 1.f / a.color_scale);
   mark(ST_RESOLVE);
-  if (a.ray_counts) k_counts<<<1, 32, 0, st>>>(ws.counters, a.max_depth, 2 * P, a.ray_counts);
+  if (a.ray_counts) k_counts<<<1, 32, 0, st>>>(ws.counters, 2 * P, a.ray_counts);
   return cudaGetLastError();
 }
 
@@ -473,6 +595,14 @@ int num_sms() {
   }
   return sms;
 }
+
+int render_grid() {
+  // the instrumented variant may fit fewer blocks; size for the larger grid
+  return num_sms() * (blocks_per_sm<false>() > blocks_per_sm<true>() ? blocks_per_sm<false>()
+                                                                      : blocks_per_sm<true>());
+}
+
+int render_threads() { return kThreads; }
 
 cudaError_t render(const RenderArgs& a, Workspace& ws, cudaStream_t st) {
   return a.work ? render_impl<true>(a, ws, st) : render_impl<false>(a, ws, st);
