@@ -247,6 +247,103 @@ int rt_build_lbvh_noalloc(const rt_sphere* d_spheres, uint32_t n_spheres,
                           float* d_nodes, float* d_prims, uint64_t* d_keys, int32_t* d_parent,
                           void* cuda_stream);
 
+/* ------------------------------------------------------------------------
+ * Learned right-eye reprojection. The paper computes the left and right
+ * channel independently (Sec. 3, "parallel level 1"); this extension traces
+ * the left channel, warps it to the right eye, and re-traces only the right
+ * pixels that a small network (or a disocclusion) marks. The full right-eye
+ * trace stays the reference it is judged against.
+ *
+ * Network: 3x3 convolutions 9 -> 32 -> 32 -> 32 -> 1, zero padding 1,
+ * ReLU, sigmoid; BF16 operands on the tensor cores, FP32 accumulation,
+ * FP32 master weights. Parameters (RT_NET_PARAMS floats) in this order:
+ * W1[32][9][3][3], b1[32], W2[32][32][3][3], b2[32], W3[32][32][3][3],
+ * b3[32], W4[1][32][3][3], b4[1].
+ * Features of a right pixel (BF16, 16 channels per pixel, channels 9-15
+ * zero; all zero on a hole): min(z/100, 1), the normal (3), hash(hit id) =
+ * (fmix32(id) >> 8) * 2^-24 (MurmurHash3 finaliser), the left RGB (3) and
+ * the disparity / 16, taken from the left pixel that the forward warp puts
+ * there: a left pixel (i, j) at view depth z lands on column
+ * floor(i - D + 0.5) of row j, D = f_px * eye_sep * (1/z - 1/convergence),
+ * f_px = (H/2)/tan(vfov/2); the nearest z wins, equal z the lower index.
+ * A left pixel whose ray missed is a source at infinity (z = +inf, zero
+ * normal, background colour), so only disocclusions and the uncovered
+ * border remain holes.
+ */
+#define RT_NET_PARAMS 21409
+typedef struct rt_net rt_net;  /* opaque */
+
+/* Upload RT_NET_PARAMS host floats (finite) into a new network; synchronises.
+ * Errors: RT_ERR_INVALID_ARG, RT_ERR_OOM, RT_ERR_CUDA. */
+int rt_net_create(const float* host_params, uint32_t n_params, rt_net** out);
+void rt_net_destroy(rt_net* net);
+/* Copy the current FP32 parameters to host memory (synchronises). */
+int rt_net_get_params(const rt_net* net, float* host_params);
+/* Synchronise the stream and report a tensor-core wait that reached its
+ * bound in earlier network work (RT_ERR_TIMEOUT), then clear it. */
+int rt_net_status(const rt_net* net, void* cuda_stream);
+
+/*
+ * rt_net_forward -- retrace probability of every pixel of a W x H feature map.
+ *   d_feat16: DEVICE, W*H*16 BF16 (as uint16 bits), row-major pixels.
+ *   d_prob:   DEVICE, W*H float32 output in (0, 1).
+ * Asynchronous on cuda_stream; the network's activation buffers are grown
+ * on demand (allocation on the first call at a size).
+ */
+int rt_net_forward(rt_net* net, const uint16_t* d_feat16, uint32_t W, uint32_t H, float* d_prob,
+                   void* cuda_stream);
+
+/*
+ * rt_net_train_step -- one step on the mean binary cross-entropy of the
+ * network's output against d_label (DEVICE, W*H floats in {0,1}): forward,
+ * backward (data gradients on the tensor cores, weight gradients in FP32),
+ * then Adam (beta 0.9 / 0.999, eps 1e-8, step size lr) when lr > 0.
+ *   host_loss: if non-NULL receives the loss before the update (synchronises).
+ *   d_grads:   if non-NULL, DEVICE RT_NET_PARAMS floats receive the gradient.
+ */
+int rt_net_train_step(rt_net* net, const uint16_t* d_feat16, const float* d_label, uint32_t W,
+                      uint32_t H, float lr, float* host_loss, float* d_grads, void* cuda_stream);
+
+/*
+ * rt_reproj_warp -- forward warp of a left G-buffer to the right eye.
+ *   inputs (DEVICE, W*H pixels each): d_depth_L view depth (+inf = the ray
+ *   missed: a source at infinity; <= 0 or NaN: skipped),
+ *   d_normal_L (3 floats), d_id_L (hit id), d_rgb_L (3 floats).
+ *   d_zbuf: DEVICE scratch of W*H uint64 (overwritten).
+ *   outputs (DEVICE, any may be NULL): d_feat16 (W*H*16 BF16 bits),
+ *   d_feat32 (W*H*9 floats, the same features before BF16 rounding),
+ *   d_hole (W*H bytes, 1 where no left pixel lands), d_warped (W*H*3 floats).
+ */
+int rt_reproj_warp(const float* d_depth_L, const float* d_normal_L, const uint32_t* d_id_L,
+                   const float* d_rgb_L, uint32_t W, uint32_t H, float f_px, float eye_sep,
+                   float convergence, uint64_t* d_zbuf, uint16_t* d_feat16, float* d_feat32,
+                   uint8_t* d_hole, float* d_warped, void* cuda_stream);
+
+/*
+ * rt_reproj_training_pair -- one training example: traces both eyes in full
+ * (d_out_L, d_out_R as in rt_render_stereo), warps the left eye, writes the
+ * right-eye features (d_feat16) and labels d_label = 1 where the pixel is a
+ * hole or some channel of the warped colour differs from the full trace by
+ * more than label_threshold (DEVICE buffers of W*H*16 BF16 / W*H floats).
+ */
+int rt_reproj_training_pair(const rt_scene* scene, const rt_camera* cam, float eye_sep,
+                            float convergence, uint32_t W, uint32_t H, uint32_t max_depth,
+                            float* d_out_L, float* d_out_R, uint16_t* d_feat16, float* d_label,
+                            float label_threshold, void* cuda_stream);
+
+/*
+ * rt_render_stereo_reproj -- a stereo pair with the right eye reprojected:
+ * traces the left eye (out_L exactly as rt_render_stereo), warps it to the
+ * right grid, runs the network (net may be NULL: retrace holes only), traces
+ * the right pixels with hole != 0 or p > threshold, and writes out_R = traced
+ * colour there, warped colour elsewhere. d_n_retraced (DEVICE uint32, may be
+ * NULL) receives the number of retraced right pixels. Asynchronous.
+ */
+int rt_render_stereo_reproj(const rt_scene* scene, const rt_camera* cam, float eye_sep,
+                            float convergence, uint32_t W, uint32_t H, uint32_t max_depth,
+                            rt_net* net, float threshold, float* d_out_L, float* d_out_R,
+                            uint32_t* d_n_retraced, void* cuda_stream);
+
 /* Number of primitives of the scene (0 for NULL). */
 uint32_t rt_scene_num_prims(const rt_scene* scene);
 

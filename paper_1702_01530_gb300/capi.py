@@ -56,6 +56,18 @@ _SIGS = {
     "rt_profile_enable": (ctypes.c_int, [_vp, ctypes.c_int]),
     "rt_profile_read": (ctypes.c_int, [_vp, _vp]),
     "rt_build_lbvh_noalloc": (ctypes.c_int, [_vp, _u32, _vp, _u32, _vp, _vp, _vp, _vp, _vp]),
+    "rt_net_create": (ctypes.c_int, [_vp, _u32, ctypes.POINTER(_vp)]),
+    "rt_net_destroy": (None, [_vp]),
+    "rt_net_get_params": (ctypes.c_int, [_vp, _vp]),
+    "rt_net_status": (ctypes.c_int, [_vp, _vp]),
+    "rt_net_forward": (ctypes.c_int, [_vp, _vp, _u32, _u32, _vp, _vp]),
+    "rt_net_train_step": (ctypes.c_int, [_vp, _vp, _vp, _u32, _u32, _f32, _vp, _vp, _vp]),
+    "rt_reproj_warp": (ctypes.c_int, [_vp, _vp, _vp, _vp, _u32, _u32, _f32, _f32, _f32, _vp, _vp,
+                                      _vp, _vp, _vp, _vp]),
+    "rt_reproj_training_pair": (ctypes.c_int, [_vp, _vp, _f32, _f32, _u32, _u32, _u32, _vp, _vp,
+                                               _vp, _vp, _f32, _vp]),
+    "rt_render_stereo_reproj": (ctypes.c_int, [_vp, _vp, _f32, _f32, _u32, _u32, _u32, _vp, _f32,
+                                               _vp, _vp, _vp, _vp]),
     "rt_last_error": (ctypes.c_char_p, []),
     "rt_version": (ctypes.c_char_p, []),
 }
@@ -228,6 +240,93 @@ def rt_build_lbvh_noalloc(d_spheres, n_spheres, d_tris, n_tris, d_nodes, d_prims
     _check(lib().rt_build_lbvh_noalloc(_dptr(d_spheres), n_spheres, _dptr(d_tris), n_tris,
                                        _dptr(d_nodes), _dptr(d_prims), _dptr(d_keys),
                                        _dptr(d_parent), _stream(stream)))
+
+
+RT_NET_PARAMS = 21409
+
+
+def rt_net_create(params) -> int:
+    p = np.ascontiguousarray(params, np.float32).reshape(-1)
+    h = _vp()
+    _check(lib().rt_net_create(p.ctypes.data, len(p), ctypes.byref(h)))
+    return h.value
+
+
+def rt_net_destroy(net):
+    lib().rt_net_destroy(net)
+
+
+def rt_net_get_params(net) -> np.ndarray:
+    out = np.zeros(RT_NET_PARAMS, np.float32)
+    _check(lib().rt_net_get_params(net, out.ctypes.data))
+    return out
+
+
+def rt_net_status(net, stream=None):
+    _check(lib().rt_net_status(net, _stream(stream)))
+
+
+def rt_net_forward(net, feat16, W, H, prob, stream=None):
+    _check(lib().rt_net_forward(net, _dptr(feat16), W, H, _dptr(prob), _stream(stream)))
+
+
+def rt_net_train_step(net, feat16, label, W, H, lr, want_loss=True, grads=None, stream=None):
+    loss = ctypes.c_float()
+    _check(lib().rt_net_train_step(net, _dptr(feat16), _dptr(label), W, H, lr,
+                                   ctypes.byref(loss) if want_loss else None, _dptr(grads),
+                                   _stream(stream)))
+    return loss.value if want_loss else None
+
+
+def rt_reproj_warp(depth_L, normal_L, id_L, rgb_L, W, H, f_px, eye_sep, convergence, zbuf,
+                   feat16=None, feat32=None, hole=None, warped=None, stream=None):
+    _check(lib().rt_reproj_warp(_dptr(depth_L), _dptr(normal_L), _dptr(id_L), _dptr(rgb_L), W, H,
+                                f_px, eye_sep, convergence, _dptr(zbuf), _dptr(feat16),
+                                _dptr(feat32), _dptr(hole), _dptr(warped), _stream(stream)))
+
+
+def rt_reproj_training_pair(scene, camera, eye_sep, convergence, W, H, max_depth, out_L, out_R,
+                            feat16, label, label_threshold=1e-2, stream=None):
+    c, pc = _cam(camera)
+    _check(lib().rt_reproj_training_pair(scene, pc, eye_sep, convergence, W, H, max_depth,
+                                         _dptr(out_L), _dptr(out_R), _dptr(feat16), _dptr(label),
+                                         label_threshold, _stream(stream)))
+
+
+def rt_render_stereo_reproj(scene, camera, eye_sep, convergence, W, H, max_depth, net, threshold,
+                            out_L, out_R, n_retraced=None, stream=None):
+    c, pc = _cam(camera)
+    _check(lib().rt_render_stereo_reproj(scene, pc, eye_sep, convergence, W, H, max_depth, net,
+                                         threshold, _dptr(out_L), _dptr(out_R), _dptr(n_retraced),
+                                         _stream(stream)))
+
+
+def focal_px(camera, H) -> float:
+    """f_px = (H/2)/tan(vfov/2), rounded to float32 as the library does."""
+    import math
+    v = float(np.asarray(camera, dtype=scenegen.CAMERA_DT)["vfov_deg"])
+    return float(np.float32(0.5 * H / math.tan(0.5 * v * math.pi / 180.0)))
+
+
+class Net:
+    """Owns one rt_net."""
+
+    def __init__(self, params):
+        self.handle = rt_net_create(params)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            rt_net_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def params(self) -> np.ndarray:
+        return rt_net_get_params(self.handle)
 
 
 class GpuScene:

@@ -1,0 +1,309 @@
+// C-ABI of the learned right-eye reprojection and its retrace network
+// (declared in include/rt_stereo.h). Host-side marshalling and buffer
+// ownership only; the work runs in reproj.cu, nn.cu and trace.cu.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "rt_internal.cuh"
+
+using rt::cuda_fail;
+using rt::fail;
+
+struct rt_net {
+  void* block = nullptr;        // params, grads, Adam m and v, packed weights, scalars
+  float* params = nullptr;
+  float* grads = nullptr;
+  float* m = nullptr;
+  float* v = nullptr;
+  __nv_bfloat16* wf[4] = {};
+  __nv_bfloat16* wb[4] = {};
+  float* loss = nullptr;
+  uint32_t* err = nullptr;
+  uint32_t step = 0;
+  // forward / training activations, grown on demand
+  void* tb = nullptr;
+  uint64_t tcap = 0;
+  __nv_bfloat16* act[3] = {};
+  float* prob = nullptr;
+  __nv_bfloat16* g16 = nullptr;
+  float* g32 = nullptr;
+  __nv_bfloat16* dz[2] = {};
+};
+
+namespace {
+
+size_t a256(size_t b) { return (b + 255) & ~size_t(255); }
+
+int net_buffers(rt_net* net, uint64_t P) {
+  if (net->tb && net->tcap >= P) return RT_OK;
+  const size_t b_act = a256(P * 32 * 2), b_prob = a256(P * 4), b_g16 = a256(P * 16 * 2),
+               b_g32 = a256(P * 4);
+  void* base = nullptr;
+  cudaError_t e = cudaMalloc(&base, 3 * b_act + b_prob + b_g16 + b_g32 + 2 * b_act);
+  if (e != cudaSuccess) { cudaGetLastError(); return cuda_fail(e, "network activations"); }
+  if (net->tb) cudaFree(net->tb);
+  net->tb = base;
+  net->tcap = P;
+  char* p = static_cast<char*>(base);
+  for (int i = 0; i < 3; ++i) { net->act[i] = reinterpret_cast<__nv_bfloat16*>(p); p += b_act; }
+  net->prob = reinterpret_cast<float*>(p); p += b_prob;
+  net->g16 = reinterpret_cast<__nv_bfloat16*>(p); p += b_g16;
+  net->g32 = reinterpret_cast<float*>(p); p += b_g32;
+  for (int i = 0; i < 2; ++i) { net->dz[i] = reinterpret_cast<__nv_bfloat16*>(p); p += b_act; }
+  return RT_OK;
+}
+
+int reproj_buffers(const rt_scene* sc_c, uint64_t P) {
+  rt_scene* sc = const_cast<rt_scene*>(sc_c);
+  rt::ReprojBuffers& rp = sc->ws.rp;
+  if (rp.base && rp.cap >= P) return RT_OK;
+  const size_t b4 = a256(P * 4), b12 = a256(P * 12), b8 = a256(P * 8), b1 = a256(P),
+               bf = a256(P * 16 * 2), bact = a256(P * 32 * 2);
+  const size_t total = b4 + b12 + b4 + b8 + bf + b1 + b12 + b1 + b4 + 256 + b4 + 3 * bact;
+  void* base = nullptr;
+  cudaError_t e = cudaMalloc(&base, total);
+  if (e != cudaSuccess) { cudaGetLastError(); return cuda_fail(e, "reprojection buffers"); }
+  if (rp.base) cudaFree(rp.base);
+  char* p = static_cast<char*>(base);
+  rp.base = base;
+  rp.cap = P;
+  rp.depth_L = reinterpret_cast<float*>(p); p += b4;
+  rp.normal_L = reinterpret_cast<float*>(p); p += b12;
+  rp.id_L = reinterpret_cast<uint32_t*>(p); p += b4;
+  rp.zbuf = reinterpret_cast<unsigned long long*>(p); p += b8;
+  rp.feat16 = reinterpret_cast<__nv_bfloat16*>(p); p += bf;
+  rp.hole = reinterpret_cast<uint8_t*>(p); p += b1;
+  rp.warped = reinterpret_cast<float*>(p); p += b12;
+  rp.mask = reinterpret_cast<uint8_t*>(p); p += b1;
+  rp.plist = reinterpret_cast<uint32_t*>(p); p += b4;
+  rp.count = reinterpret_cast<uint32_t*>(p); p += 256;
+  rp.prob = reinterpret_cast<float*>(p); p += b4;
+  for (int i = 0; i < 3; ++i) { rp.act[i] = reinterpret_cast<__nv_bfloat16*>(p); p += bact; }
+  return RT_OK;
+}
+
+float focal_px(const rt_camera* cam, uint32_t H) {
+  return (float)(0.5 * (double)H / std::tan(0.5 * (double)cam->vfov_deg * M_PI / 180.0));
+}
+
+}  // namespace
+
+extern "C" {
+
+int rt_net_create(const float* host_params, uint32_t n_params, rt_net** out) {
+  if (!out) return fail(RT_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!host_params || n_params != rt::nn::kParams)
+    return fail(RT_ERR_INVALID_ARG, "need RT_NET_PARAMS (" + std::to_string(rt::nn::kParams) + ") parameters");
+  for (uint32_t i = 0; i < n_params; ++i)
+    if (!std::isfinite(host_params[i])) return fail(RT_ERR_INVALID_ARG, "non-finite parameter " + std::to_string(i));
+  rt_net* net = new (std::nothrow) rt_net();
+  if (!net) return fail(RT_ERR_OOM, "host allocation failed");
+  const size_t bp = a256((size_t)rt::nn::kParams * 4);
+  size_t bw = 0;
+  for (int l = 0; l < 4; ++l) bw += a256(rt::nn::packed_fwd_elems(l) * 2) + a256(rt::nn::packed_bwd_elems(l) * 2);
+  cudaError_t e = cudaMalloc(&net->block, 4 * bp + bw + 512);
+  if (e != cudaSuccess) { cudaGetLastError(); delete net; return cuda_fail(e, "network allocation"); }
+  char* p = static_cast<char*>(net->block);
+  net->params = reinterpret_cast<float*>(p); p += bp;
+  net->grads = reinterpret_cast<float*>(p); p += bp;
+  net->m = reinterpret_cast<float*>(p); p += bp;
+  net->v = reinterpret_cast<float*>(p); p += bp;
+  for (int l = 0; l < 4; ++l) {
+    net->wf[l] = reinterpret_cast<__nv_bfloat16*>(p); p += a256(rt::nn::packed_fwd_elems(l) * 2);
+    net->wb[l] = reinterpret_cast<__nv_bfloat16*>(p); p += a256(rt::nn::packed_bwd_elems(l) * 2);
+  }
+  net->loss = reinterpret_cast<float*>(p); p += 256;
+  net->err = reinterpret_cast<uint32_t*>(p);
+  e = cudaMemcpy(net->params, host_params, (size_t)n_params * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(net->m, 0, (size_t)n_params * 4);
+  if (e == cudaSuccess) e = cudaMemset(net->v, 0, (size_t)n_params * 4);
+  if (e == cudaSuccess) e = cudaMemset(net->err, 0, 4);
+  if (e == cudaSuccess) e = rt::nn::pack_weights(net->params, net->wf, net->wb, 0);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) { cudaFree(net->block); delete net; return cuda_fail(e, "network upload"); }
+  *out = net;
+  return RT_OK;
+}
+
+void rt_net_destroy(rt_net* net) {
+  if (!net) return;
+  if (net->tb) cudaFree(net->tb);
+  if (net->block) cudaFree(net->block);
+  delete net;
+}
+
+int rt_net_get_params(const rt_net* net, float* host_params) {
+  if (!net || !host_params) return fail(RT_ERR_INVALID_ARG, "net or output is NULL");
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(host_params, net->params, (size_t)rt::nn::kParams * 4, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "parameter download");
+  return RT_OK;
+}
+
+int rt_net_status(const rt_net* net, void* cuda_stream) {
+  if (!net) return fail(RT_ERR_INVALID_ARG, "net is NULL");
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  uint32_t bits = 0;
+  cudaError_t e = cudaMemcpyAsync(&bits, net->err, 4, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "status read");
+  if (!bits) return RT_OK;
+  cudaMemsetAsync(net->err, 0, 4, st);
+  cudaStreamSynchronize(st);
+  return fail(RT_ERR_TIMEOUT, "a tensor-core wait reached its bound (bits " + std::to_string(bits) + ")");
+}
+
+int rt_net_forward(rt_net* net, const uint16_t* d_feat16, uint32_t W, uint32_t H, float* d_prob,
+                   void* cuda_stream) {
+  if (!net || !d_feat16 || !d_prob || W < 1 || H < 1) return fail(RT_ERR_INVALID_ARG, "bad argument");
+  if ((uint64_t)W * H > (1ull << 30)) return fail(RT_ERR_INVALID_ARG, "image too large");
+  int rc = net_buffers(net, (uint64_t)W * H);
+  if (rc) return rc;
+  cudaError_t e = rt::nn::forward(reinterpret_cast<const __nv_bfloat16*>(d_feat16), net->params,
+                                  net->wf, net->act[0], net->act[1], net->act[2], d_prob, W, H,
+                                  net->err, static_cast<cudaStream_t>(cuda_stream));
+  if (e != cudaSuccess) return cuda_fail(e, "network forward");
+  return RT_OK;
+}
+
+int rt_net_train_step(rt_net* net, const uint16_t* d_feat16, const float* d_label, uint32_t W,
+                      uint32_t H, float lr, float* host_loss, float* d_grads, void* cuda_stream) {
+  if (!net || !d_feat16 || !d_label || W < 1 || H < 1 || !(lr >= 0.f) || !std::isfinite(lr))
+    return fail(RT_ERR_INVALID_ARG, "bad argument");
+  if ((uint64_t)W * H > (1ull << 30)) return fail(RT_ERR_INVALID_ARG, "image too large");
+  const uint64_t P = (uint64_t)W * H;
+  int rc = net_buffers(net, P);
+  if (rc) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  const __nv_bfloat16* f16 = reinterpret_cast<const __nv_bfloat16*>(d_feat16);
+  cudaError_t e = rt::nn::forward(f16, net->params, net->wf, net->act[0], net->act[1], net->act[2],
+                                  net->prob, W, H, net->err, st);
+  if (e == cudaSuccess)
+    e = rt::nn::backward(f16, d_label, net->wb, net->act[0], net->act[1], net->act[2], net->prob,
+                         net->g16, net->g32, net->dz[0], net->dz[1], net->grads, net->loss, W, H,
+                         net->err, st);
+  if (e == cudaSuccess && d_grads)
+    e = cudaMemcpyAsync(d_grads, net->grads, (size_t)rt::nn::kParams * 4, cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess && lr > 0.f) {
+    net->step += 1;
+    e = rt::nn::adam(net->params, net->grads, net->m, net->v, rt::nn::kParams, lr, net->step, st);
+    if (e == cudaSuccess) e = rt::nn::pack_weights(net->params, net->wf, net->wb, st);
+  }
+  if (e == cudaSuccess && host_loss) {
+    float sum = 0.f;
+    e = cudaMemcpyAsync(&sum, net->loss, 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    *host_loss = sum / (float)P;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "network training step");
+  return RT_OK;
+}
+
+int rt_reproj_warp(const float* d_depth_L, const float* d_normal_L, const uint32_t* d_id_L,
+                   const float* d_rgb_L, uint32_t W, uint32_t H, float f_px, float eye_sep,
+                   float convergence, uint64_t* d_zbuf, uint16_t* d_feat16, float* d_feat32,
+                   uint8_t* d_hole, float* d_warped, void* cuda_stream) {
+  if (!d_depth_L || !d_normal_L || !d_id_L || !d_rgb_L || !d_zbuf || W < 1 || H < 1)
+    return fail(RT_ERR_INVALID_ARG, "bad argument");
+  if ((uint64_t)W * H > (1ull << 31)) return fail(RT_ERR_INVALID_ARG, "image too large");
+  if (!(f_px > 0.f) || !(eye_sep >= 0.f) || !(convergence > 0.f) || !std::isfinite(f_px) ||
+      !std::isfinite(eye_sep) || !std::isfinite(convergence))
+    return fail(RT_ERR_INVALID_ARG, "f_px, eye_sep, convergence out of range");
+  cudaError_t e = rt::reproj_warp(d_depth_L, d_normal_L, d_id_L, d_rgb_L, W, H, f_px, eye_sep,
+                                  convergence, reinterpret_cast<unsigned long long*>(d_zbuf),
+                                  reinterpret_cast<__nv_bfloat16*>(d_feat16), d_feat32, d_hole,
+                                  d_warped, static_cast<cudaStream_t>(cuda_stream));
+  if (e != cudaSuccess) return cuda_fail(e, "warp");
+  return RT_OK;
+}
+
+int rt_reproj_training_pair(const rt_scene* scene, const rt_camera* cam, float eye_sep,
+                            float convergence, uint32_t W, uint32_t H, uint32_t max_depth,
+                            float* d_out_L, float* d_out_R, uint16_t* d_feat16, float* d_label,
+                            float label_threshold, void* cuda_stream) {
+  rt::RenderArgs a;
+  int rc = rt::make_render_args(scene, cam, eye_sep, convergence, W, H, max_depth, a);
+  if (rc) return rc;
+  if (!d_out_L || !d_out_R || !d_feat16 || !d_label || !(label_threshold >= 0.f))
+    return fail(RT_ERR_INVALID_ARG, "bad argument");
+  const uint64_t P = (uint64_t)W * H;
+  rc = rt::ensure_workspace(scene, W, H);
+  if (!rc) rc = reproj_buffers(scene, P);
+  if (rc) return rc;
+  rt::ReprojBuffers& rp = const_cast<rt_scene*>(scene)->ws.rp;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  a.out_L = d_out_L; a.out_R = d_out_R;
+  a.hit_L = rp.id_L; a.depth_L = rp.depth_L; a.normal_L = rp.normal_L;
+  cudaError_t e = rt::render(a, const_cast<rt_scene*>(scene)->ws, st);
+  if (e == cudaSuccess)
+    e = rt::reproj_warp(rp.depth_L, rp.normal_L, rp.id_L, d_out_L, W, H, focal_px(cam, H), eye_sep,
+                        convergence, rp.zbuf, reinterpret_cast<__nv_bfloat16*>(d_feat16), nullptr,
+                        rp.hole, rp.warped, st);
+  if (e == cudaSuccess) e = rt::reproj_labels(rp.hole, rp.warped, d_out_R, (uint32_t)P, label_threshold, d_label, st);
+  if (e != cudaSuccess) return cuda_fail(e, "training pair");
+  return RT_OK;
+}
+
+int rt_render_stereo_reproj(const rt_scene* scene, const rt_camera* cam, float eye_sep,
+                            float convergence, uint32_t W, uint32_t H, uint32_t max_depth,
+                            rt_net* net, float threshold, float* d_out_L, float* d_out_R,
+                            uint32_t* d_n_retraced, void* cuda_stream) {
+  rt::RenderArgs a;
+  int rc = rt::make_render_args(scene, cam, eye_sep, convergence, W, H, max_depth, a);
+  if (rc) return rc;
+  if (!d_out_L || !d_out_R || !std::isfinite(threshold)) return fail(RT_ERR_INVALID_ARG, "bad argument");
+  const uint64_t P = (uint64_t)W * H;
+  rc = rt::ensure_workspace(scene, W, H);
+  if (!rc) rc = reproj_buffers(scene, P);
+  if (!rc && net) rc = net_buffers(net, P);
+  if (rc) return rc;
+  rt_scene* sc = const_cast<rt_scene*>(scene);
+  rt::ReprojBuffers& rp = sc->ws.rp;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  // 1. left eye with its G-buffer
+  a.eyes = 1u;
+  a.out_L = d_out_L; a.out_R = d_out_R;
+  a.hit_L = rp.id_L; a.depth_L = rp.depth_L; a.normal_L = rp.normal_L;
+  cudaError_t e = rt::render(a, sc->ws, st);
+  // 2. forward warp to the right grid, network features
+  if (e == cudaSuccess)
+    e = rt::reproj_warp(rp.depth_L, rp.normal_L, rp.id_L, d_out_L, W, H, focal_px(cam, H), eye_sep,
+                        convergence, rp.zbuf, rp.feat16, nullptr, rp.hole, rp.warped, st);
+  // 3. retrace probability
+  if (e == cudaSuccess && net)
+    e = rt::nn::forward(rp.feat16, net->params, net->wf, rp.act[0], rp.act[1], rp.act[2], rp.prob,
+                        W, H, net->err, st);
+  // 4. mask = hole or p > threshold, compacted
+  if (e == cudaSuccess)
+    e = rt::reproj_mask(rp.hole, net ? rp.prob : nullptr, (uint32_t)P, threshold, rp.mask, rp.plist,
+                        rp.count, st);
+  // 5. trace the masked right pixels (count read on the device)
+  if (e == cudaSuccess) {
+    rt::RenderArgs b = a;
+    b.eyes = 2u;
+    b.hit_L = nullptr; b.depth_L = nullptr; b.normal_L = nullptr;
+    b.plist = rp.plist;
+    b.plist_n = 0;
+    b.plist_n_dev = rp.count;
+    b.resolve = false;
+    e = rt::render(b, sc->ws, st);
+  }
+  // 6. compose the right image
+  if (e == cudaSuccess)
+    e = rt::reproj_compose(rp.mask, sc->ws.accum + 3 * P, rp.warped, (uint32_t)P,
+                           1.f / sc->color_scale, d_out_R, st);
+  if (e == cudaSuccess && d_n_retraced)
+    e = cudaMemcpyAsync(d_n_retraced, rp.count, 4, cudaMemcpyDeviceToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(e, "reprojection render");
+  return RT_OK;
+}
+
+}  // extern "C"

@@ -19,23 +19,7 @@ static thread_local std::string g_last_error;
 
 void rt_set_error(const std::string& msg) { g_last_error = msg; }
 
-struct rt_scene {
-  int device = 0;
-  uint32_t ns = 0, nt = 0, n = 0, nm = 0, nl = 0;
-  void* block = nullptr;       // persistent device allocation
-  float4* nodes = nullptr;
-  float4* prims = nullptr;
-  float4* mats = nullptr;
-  float4* lights = nullptr;
-  uint64_t* keys = nullptr;
-  int32_t* parent = nullptr;
-  uint32_t* err = nullptr;
-  uint32_t* h_err = nullptr;   // pinned
-  float color_scale = 1.f;
-  rt::Workspace ws;
-};
-
-namespace {
+namespace rt {
 
 int fail(int code, const std::string& msg) {
   rt_set_error(msg);
@@ -47,6 +31,13 @@ int cuda_fail(cudaError_t e, const char* what) {
               std::string(what) + ": " + cudaGetErrorString(e));
 }
 
+}  // namespace rt
+
+using rt::cuda_fail;
+using rt::fail;
+
+namespace {
+
 bool finite3(const float* v) { return std::isfinite(v[0]) && std::isfinite(v[1]) && std::isfinite(v[2]); }
 
 size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
@@ -54,11 +45,15 @@ size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 void free_workspace(rt::Workspace& ws) {
   if (ws.base) cudaFree(ws.base);
   if (ws.frame) cudaFree(ws.frame);
+  if (ws.rp.base) cudaFree(ws.rp.base);
   for (cudaEvent_t& e : ws.ev)
     if (e) cudaEventDestroy(e);
   ws = rt::Workspace();
 }
 
+}  // namespace
+
+namespace rt {
 // grow the scene's scratch to hold a W x H stereo pair with L lights:
 // fixed-point accumulators for both eyes and, per resident warp of the
 // render kernel, a shadow queue of 32 L + 32 and a mirror queue of 64
@@ -141,10 +136,15 @@ int make_render_args(const rt_scene* scene, const rt_camera* cam, float eye_sep,
   a.max_depth = max_depth;
   a.color_scale = scene->color_scale;
   a.err = scene->err;
+  a.eyes = 3u;
+  a.resolve = true;
   return RT_OK;
 }
 
-}  // namespace
+}  // namespace rt
+
+using rt::ensure_workspace;
+using rt::make_render_args;
 
 extern "C" {
 

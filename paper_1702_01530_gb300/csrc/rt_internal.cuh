@@ -14,6 +14,7 @@
 //   mats   : float4 (albedo rgb, reflectivity)
 //   lights : float4 (position xyz, intensity)
 #pragma once
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -52,6 +53,24 @@ struct CameraParams {
   uint32_t tiles_x, tiles_y;  // 8x4-pixel tiles per eye
 };
 
+// reprojection scratch of a scene (per right-eye pixel unless noted)
+struct ReprojBuffers {
+  void* base = nullptr;
+  uint64_t cap = 0;              // pixels per eye the buffers hold
+  float* depth_L = nullptr;      // left G-buffer: view depth, normal (3), hit id
+  float* normal_L = nullptr;
+  uint32_t* id_L = nullptr;
+  unsigned long long* zbuf = nullptr;  // forward-warp z-test keys
+  __nv_bfloat16* feat16 = nullptr;     // network input, 16 channels
+  uint8_t* hole = nullptr;
+  float* warped = nullptr;       // warped left RGB (3)
+  uint8_t* mask = nullptr;       // retrace mask
+  uint32_t* plist = nullptr;     // masked pixels (global indices)
+  uint32_t* count = nullptr;     // number of masked pixels
+  float* prob = nullptr;         // network output
+  __nv_bfloat16* act[3] = {nullptr, nullptr, nullptr};  // hidden activations (32 channels)
+};
+
 // scratch of one render (scene-owned, grown on demand)
 struct Workspace {
   size_t bytes = 0;
@@ -65,6 +84,7 @@ struct Workspace {
   float4* frame = nullptr;       // frame buffers for rt_render_stereo_host
   size_t frame_bytes = 0;
   uint32_t L = 0;
+  ReprojBuffers rp;
   // stage timing (CUDA events on the render stream), see Stage
   bool profile = false;
   cudaEvent_t ev[8] = {};
@@ -99,9 +119,16 @@ struct RenderArgs {
   uint32_t* hit_R;
   float* depth_L;
   float* depth_R;
+  float* normal_L;         // G-buffer: primary-hit normal (facing the ray), 3 floats/pixel
+  float* normal_R;
   uint64_t* ray_counts;
   uint64_t* work;          // non-null => instrumented traversal
   uint32_t* err;           // device error word
+  uint32_t eyes;           // 1 = left only, 2 = right only, 3 = both
+  const uint32_t* plist;   // optional list of pixels to trace (eye*P + y*W + x)
+  uint32_t plist_n;        // its length, or
+  const uint32_t* plist_n_dev;  // its length in device memory (read by the kernel)
+  bool resolve;            // write out_L/out_R from the sums (false: caller composes)
 };
 
 // entry points implemented in the .cu files
@@ -114,7 +141,63 @@ int num_sms();
 int render_grid();      // persistent blocks of the render kernel
 int render_threads();   // threads per block of the render kernel
 
+// reprojection (reproj.cu)
+cudaError_t reproj_warp(const float* depth_L, const float* normal_L, const uint32_t* id_L,
+                        const float* rgb_L, uint32_t W, uint32_t H, float f_px, float eye_sep,
+                        float convergence, unsigned long long* zbuf, __nv_bfloat16* feat16,
+                        float* feat32, uint8_t* hole, float* warped, cudaStream_t st);
+cudaError_t reproj_labels(const uint8_t* hole, const float* warped, const float* full_R, uint32_t P,
+                          float thr, float* label, cudaStream_t st);
+cudaError_t reproj_mask(const uint8_t* hole, const float* prob, uint32_t P, float threshold,
+                        uint8_t* mask, uint32_t* plist, uint32_t* count, cudaStream_t st);
+cudaError_t reproj_compose(const uint8_t* mask, const uint32_t* accum_R, const float* warped,
+                           uint32_t P, float inv_scale, float* out_R, cudaStream_t st);
+
+// retrace network (nn.cu)
+namespace nn {
+constexpr uint32_t kParams = 21409;
+void set_conv_smem_pad(int bytes);
+size_t packed_fwd_elems(int l);
+size_t packed_bwd_elems(int l);
+cudaError_t pack_weights(const float* params, __nv_bfloat16* const wf[4], __nv_bfloat16* const wb[4],
+                         cudaStream_t st);
+cudaError_t forward(const __nv_bfloat16* feat16, const float* params, __nv_bfloat16* const wf[4],
+                    __nv_bfloat16* act1, __nv_bfloat16* act2, __nv_bfloat16* act3, float* prob,
+                    uint32_t W, uint32_t H, uint32_t* err, cudaStream_t st);
+cudaError_t backward(const __nv_bfloat16* feat16, const float* label, __nv_bfloat16* const wb[4],
+                     const __nv_bfloat16* act1, const __nv_bfloat16* act2,
+                     const __nv_bfloat16* act3, const float* prob, __nv_bfloat16* g16, float* g32,
+                     __nv_bfloat16* dz_a, __nv_bfloat16* dz_b, float* grads, float* loss_sum,
+                     uint32_t W, uint32_t H, uint32_t* err, cudaStream_t st);
+cudaError_t adam(float* params, const float* grads, float* m, float* v, uint32_t n, float lr,
+                 uint32_t step, cudaStream_t st);
+}  // namespace nn
+
 }  // namespace rt
 
-// error message plumbing (rt_api.cu)
+// the opaque scene of the C-ABI
+struct rt_scene {
+  int device = 0;
+  uint32_t ns = 0, nt = 0, n = 0, nm = 0, nl = 0;
+  void* block = nullptr;       // persistent device allocation
+  float4* nodes = nullptr;
+  float4* prims = nullptr;
+  float4* mats = nullptr;
+  float4* lights = nullptr;
+  uint64_t* keys = nullptr;
+  int32_t* parent = nullptr;
+  uint32_t* err = nullptr;
+  uint32_t* h_err = nullptr;   // pinned
+  float color_scale = 1.f;
+  rt::Workspace ws;
+};
+
+// error message plumbing and host helpers (rt_api.cu)
 void rt_set_error(const std::string& msg);
+namespace rt {
+int fail(int code, const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);
+int ensure_workspace(const rt_scene* sc, uint32_t W, uint32_t H);
+int make_render_args(const rt_scene* scene, const rt_camera* cam, float eye_sep, float convergence,
+                     uint32_t W, uint32_t H, uint32_t max_depth, RenderArgs& a);
+}  // namespace rt

@@ -357,6 +357,8 @@ k_render(KParams kp) {
   uint32_t nS = 0, nR = 0;          // warp-uniform queue fills
   uint32_t made_s = 0, made_r = 0;  // rays this warp enqueued
   bool tiles_left = true;
+  const uint32_t plist_n = a.plist_n_dev ? *a.plist_n_dev : a.plist_n;
+  const uint32_t n_tiles = a.plist ? (plist_n + 31u) / 32u : kp.n_tiles;
   WorkCount wc_p = {0, 0, 0}, wc_s = {0, 0, 0}, wc_r = {0, 0, 0};
   const uint32_t L = a.sc.n_lights;
 
@@ -371,7 +373,7 @@ k_render(KParams kp) {
       uint32_t t = 0;
       if (lane == 0) t = atomicAdd(&kp.counters[C_TILE], 1u);
       t = __shfl_sync(0xFFFFFFFFu, t, 0);
-      if (t >= kp.n_tiles) { tiles_left = false; continue; }
+      if (t >= n_tiles) { tiles_left = false; continue; }
       mode = M_PRIMARY; tile = t;
     }
     else if (nS > 0) { mode = M_SHADOW; take = nS; base = 0; nS = 0; }
@@ -400,11 +402,24 @@ k_render(KParams kp) {
     V3 o, d, w = v3(1.f, 1.f, 1.f);
     uint32_t pix = 0, depth = 0;
     if (mode == M_PRIMARY) {
-      const uint32_t eye = tile & 1u, tt = tile >> 1;
-      const uint32_t px = (tt % cam.tiles_x) * 8u + (lane & 7u);
-      const uint32_t py = (tt / cam.tiles_x) * 4u + (lane >> 3);
-      active = px < cam.W && py < cam.H;
-      pix = eye * P + py * cam.W + px;
+      uint32_t eye, px, py;
+      if (a.plist) {                       // an explicit pixel list (masked retrace)
+        const uint32_t i = tile * 32u + lane;
+        active = i < plist_n;
+        pix = active ? a.plist[i] : 0u;
+        if (pix >= 2 * P) { active = false; pix = 0u; }
+        eye = pix >= P;
+        const uint32_t pi = pix - eye * P;
+        py = pi / cam.W;
+        px = pi - py * cam.W;
+      } else {                             // 8x4 tiles, alternating eyes when both are traced
+        const uint32_t tt = a.eyes == 3u ? tile >> 1 : tile;
+        eye = a.eyes == 3u ? (tile & 1u) : (a.eyes == 2u ? 1u : 0u);
+        px = (tt % cam.tiles_x) * 8u + (lane & 7u);
+        py = (tt / cam.tiles_x) * 4u + (lane >> 3);
+        active = px < cam.W && py < cam.H;
+        pix = eye * P + py * cam.W + px;
+      }
       const float nx = (2.f * ((float)px + 0.5f) / (float)cam.W - 1.f) * cam.tan_x;
       const float ny = (1.f - 2.f * ((float)py + 0.5f) / (float)cam.H) * cam.tan_y;
       const V3 E = v3(cam.eye[0], cam.eye[1], cam.eye[2]);
@@ -506,6 +521,12 @@ k_render(KParams kp) {
       float* dep = eye ? a.depth_R : a.depth_L;
       if (hid) hid[pi] = id;
       if (dep) dep[pi] = hit ? t * dot(d, v3(cam.fwd[0], cam.fwd[1], cam.fwd[2])) : INFINITY;
+      float* nr = eye ? a.normal_R : a.normal_L;
+      if (nr) {                            // zero normal on a miss
+        nr[3 * (size_t)pi + 0] = hit ? nrm.x : 0.f;
+        nr[3 * (size_t)pi + 1] = hit ? nrm.y : 0.f;
+        nr[3 * (size_t)pi + 2] = hit ? nrm.z : 0.f;
+      }
     }
     if (nS > kp.cap_s || nR > kp.cap_r) {  // cannot happen by construction; writes were skipped
       if (lane == 0) atomicOr(a.err, ERR_QUEUE);
@@ -560,7 +581,8 @@ cudaError_t render_impl(const RenderArgs& a, Workspace& ws, cudaStream_t st) {
   kp.counters = ws.counters;
   kp.cap_s = ws.cap_s;
   kp.cap_r = ws.cap_r;
-  kp.n_tiles = 2u * a.cam.tiles_x * a.cam.tiles_y;
+  kp.n_tiles = a.plist ? (a.plist_n + 31u) / 32u
+                       : (a.eyes == 3u ? 2u : 1u) * a.cam.tiles_x * a.cam.tiles_y;
   const int grid = render_grid();
   if ((uint64_t)grid * (kThreads / 32) > ws.n_warps) return cudaErrorInvalidValue;
   ws.n_ev = 0;
@@ -577,9 +599,11 @@ cudaError_t render_impl(const RenderArgs& a, Workspace& ws, cudaStream_t st) {
   k_render<COUNT><<<grid, kThreads, 0, st>>>(kp);
   mark(ST_TRACE);
   const uint32_t n3 = (uint32_t)(P * 3);
-  k_resolve<<<num_sms() * 8, 256, 0, st>>>(ws.accum, a.out_L, a.out_R, n3, 1.f / a.color_scale);
+  if (a.resolve)
+    k_resolve<<<num_sms() * 8, 256, 0, st>>>(ws.accum, a.out_L, a.out_R, n3, 1.f / a.color_scale);
   mark(ST_RESOLVE);
-  if (a.ray_counts) k_counts<<<1, 32, 0, st>>>(ws.counters, 2 * P, a.ray_counts);
+  const uint64_t primary = a.plist ? a.plist_n : (a.eyes == 3u ? 2 * P : P);
+  if (a.ray_counts && !a.plist_n_dev) k_counts<<<1, 32, 0, st>>>(ws.counters, primary, a.ray_counts);
   return cudaGetLastError();
 }
 

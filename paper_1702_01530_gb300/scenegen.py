@@ -357,3 +357,52 @@ def describe(scene: Scene) -> dict:
             "triangles": int(len(scene.triangles)), "lights": int(len(scene.lights)),
             "W": scene.W, "H": scene.H, "max_depth": scene.max_depth,
             "eye_sep": scene.eye_sep, "convergence": scene.convergence}
+
+
+# ----------------------------------------------------- reprojection inputs
+def gbuffer_synthetic(seed: int, W: int, H: int, miss_frac: float = 0.2,
+                      z_lo: float = 2.0, z_hi: float = 60.0):
+    """A random left-eye G-buffer (test input for the forward warp).
+
+    Draw order per pixel (row-major): miss coin, depth u (log-uniform in
+    [z_lo, z_hi)), normal x, y, z (uniform in [-1,1], then normalised), id u
+    (ids 0..999), r, g, b. Misses get depth +inf and id 0xFFFFFFFF. Returns
+    float32 depth (P), normal (P,3), rgb (P,3) and uint32 ids (P).
+    """
+    u = SplitMix64(seed).uniform(W * H * 9).reshape(W * H, 9)
+    miss = u[:, 0] < miss_frac
+    depth = (z_lo * (z_hi / z_lo) ** u[:, 1]).astype(np.float32)
+    depth[miss] = np.inf
+    n = 2.0 * u[:, 2:5] - 1.0
+    n /= np.maximum(np.linalg.norm(n, axis=1, keepdims=True), 1e-12)
+    ids = np.minimum((u[:, 5] * 1000).astype(np.uint32), 999).astype(np.uint32)
+    ids[miss] = 0xFFFFFFFF
+    return depth, n.astype(np.float32), ids, u[:, 6:9].astype(np.float32)
+
+
+NET_LAYERS = ((9, 32), (32, 32), (32, 32), (32, 1))
+NET_PARAMS = sum(co * ci * 9 + co for ci, co in NET_LAYERS)
+
+
+def net_params_he(seed: int) -> np.ndarray:
+    """He-normal initial weights (N(0, 2/(9 Cin))), zero biases, in the
+    parameter order W1, b1, W2, b2, W3, b3, W4, b4 (W as [Cout][Cin][3][3]).
+    Draw order: the weights of layer 1..4, each in that layout's order."""
+    rng = SplitMix64(seed)
+    out = []
+    for ci, co in NET_LAYERS:
+        w = rng.normal(co * ci * 9) * np.sqrt(2.0 / (9 * ci))
+        out += [w, np.zeros(co)]
+    p = np.concatenate(out).astype(np.float32)
+    assert p.size == NET_PARAMS
+    return p
+
+
+def bf16_features_synthetic(seed: int, W: int, H: int) -> np.ndarray:
+    """Random network inputs already representable in BF16: (P, 16) float32,
+    channels 0-8 uniform in [-1, 1) rounded to 8 significant bits, 9-15 zero."""
+    u = SplitMix64(seed).uniform(W * H * 9).reshape(W * H, 9) * 2.0 - 1.0
+    f = np.zeros((W * H, 16), np.float32)
+    m, e = np.frexp(u)
+    f[:, :9] = np.ldexp(np.round(m * 256.0) / 256.0, e)
+    return f

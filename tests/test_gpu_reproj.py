@@ -1,0 +1,196 @@
+"""Learned reprojection on the GPU vs the oracle, through the C-ABI.
+
+* forward warp: hole mask and source pixels exact (the target column is an
+  integer decided in float32 on both sides), features within 1e-6;
+* network forward (tcgen05, BF16 operands, FP32 accumulation): within 5e-3 of
+  the float64 oracle that rounds to BF16 at the same points;
+* gradients (tensor-core data gradients with BF16 intermediates, FP32 weight
+  gradients): relative L2 error per tensor <= 1e-2 against a float64
+  backward pass that rounds to BF16 at the same points, and cosine > 0.99
+  against plain float64 autograd;
+* the reprojected pair equals the full trace bit for bit when every right
+  pixel is retraced, and its left image always equals the full trace's.
+"""
+import numpy as np
+import pytest
+
+from oracle import reproj as orp
+from paper_1702_01530_gb300 import capi, scenegen as sg
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    from paper_1702_01530_gb300 import build
+    build.build()
+    torch.cuda.init()
+
+
+def _t(a, dtype=None):
+    import torch
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.cuda()
+
+
+@pytest.mark.parametrize("W,H,seed", [(97, 41, 1), (256, 3, 2), (1, 5, 3), (333, 20, 4)])
+def test_warp_matches_oracle(W, H, seed):
+    import torch
+    depth, normal, ids, rgb = sg.gbuffer_synthetic(seed, W, H)
+    f_px, s, zc = 731.25, 0.065 * 3, 9.0
+    P = W * H
+    zbuf = torch.empty(P, dtype=torch.int64, device="cuda")
+    f16 = torch.empty((P, 16), dtype=torch.bfloat16, device="cuda")
+    f32 = torch.empty((P, 9), dtype=torch.float32, device="cuda")
+    hole = torch.empty(P, dtype=torch.uint8, device="cuda")
+    warped = torch.empty((P, 3), dtype=torch.float32, device="cuda")
+    capi.rt_reproj_warp(_t(depth), _t(normal), _t(ids.view(np.int32)), _t(rgb), W, H, f_px, s, zc,
+                        zbuf, f16, f32, hole, warped)
+    torch.cuda.synchronize()
+    feat, ohole, owarp, src = orp.warp(depth, normal, ids, rgb, W, H, f_px, s, zc)
+    assert np.array_equal(hole.cpu().numpy().astype(bool), ohole)
+    g = f32.cpu().numpy()
+    assert np.abs(g - feat).max() <= 1e-6
+    assert np.abs(warped.cpu().numpy() - owarp).max() <= 1e-7
+    assert torch.equal(f16[:, :9].float(), f32.to(torch.bfloat16).float()) and (f16[:, 9:] == 0).all()
+    assert 0 < ohole.mean() < 1 or P < 10
+
+
+@pytest.mark.parametrize("W,H", [(300, 7), (128, 2), (1, 3), (1000, 5)])
+def test_network_forward_matches_oracle(W, H):
+    import torch
+    params = sg.net_params_he(11)
+    rng = np.random.default_rng(5)
+    params[2592:2624] = rng.normal(0, 0.1, 32)             # non-zero biases
+    params[21408] = -0.5
+    feat = sg.bf16_features_synthetic(12, W, H)
+    net = capi.Net(params)
+    try:
+        prob = torch.empty(W * H, dtype=torch.float32, device="cuda")
+        capi.rt_net_forward(net.handle, _t(feat, torch.bfloat16), W, H, prob)
+        capi.rt_net_status(net.handle)
+        got = prob.cpu().numpy().reshape(H, W)
+    finally:
+        net.close()
+    ref = orp.forward(params, feat, W, H, bf16=True)
+    err = np.abs(got - ref)
+    assert err.max() <= 5e-3 and err.mean() <= 2e-4, (err.max(), err.mean())
+    assert ref.std() > 1e-3
+
+
+def test_gradients_match_float64_autograd():
+    import torch
+    W, H = 200, 9
+    params = sg.net_params_he(21)
+    params[21408] = 0.2
+    feat = sg.bf16_features_synthetic(22, W, H)
+    label = (np.random.default_rng(6).random(W * H) < 0.3).astype(np.float32)
+    net = capi.Net(params)
+    try:
+        grads = torch.zeros(capi.RT_NET_PARAMS, dtype=torch.float32, device="cuda")
+        loss = capi.rt_net_train_step(net.handle, _t(feat, torch.bfloat16), _t(label), W, H, 0.0,
+                                      grads=grads)
+        capi.rt_net_status(net.handle)
+        g = grads.cpu().numpy().astype(np.float64)
+        assert np.array_equal(net.params(), params)        # lr = 0: no update
+    finally:
+        net.close()
+    ref_loss, ref = orp.loss_and_grads(params, feat, label, W, H)
+    assert abs(loss - ref_loss) <= 1e-3 * abs(ref_loss) + 1e-4
+    # against the backward pass that rounds to BF16 at the kernels' points:
+    # what remains is FP32-vs-FP64 accumulation and rare rounding flips
+    emu = orp.grads_emulated(params, feat, label, W, H, bf16=True)
+    k = 0
+    for ci, co in orp.LAYERS:
+        for n in (co * ci * 9, co):
+            a, b = g[k:k + n], emu[k:k + n]
+            rel = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-12)
+            assert rel <= 1e-2, (k, n, rel)
+            # and the plain float64 gradient points the same way
+            c = ref[k:k + n]
+            assert a @ c / (np.linalg.norm(a) * np.linalg.norm(c)) > 0.99
+            k += n
+
+
+def test_training_reduces_loss():
+    import torch
+    W, H = 256, 16
+    params = sg.net_params_he(31)
+    feat = sg.bf16_features_synthetic(32, W, H)
+    # a learnable rule: label = feature channel 0 > 0
+    label = (feat[:, 0] > 0).astype(np.float32)
+    net = capi.Net(params)
+    try:
+        f, y = _t(feat, torch.bfloat16), _t(label)
+        losses = [capi.rt_net_train_step(net.handle, f, y, W, H, 1e-2) for _ in range(40)]
+        capi.rt_net_status(net.handle)
+        assert not np.array_equal(net.params(), params)
+    finally:
+        net.close()
+    assert losses[-1] < 0.5 * losses[0], losses[::8]
+
+
+def _full_and_reproj(s, params, threshold):
+    import torch
+    g = capi.GpuScene(s)
+    net = capi.Net(params) if params is not None else None
+    try:
+        full = g.render()["rgb"]
+        L = torch.empty((s.H, s.W, 3), dtype=torch.float32, device="cuda")
+        R = torch.empty((s.H, s.W, 3), dtype=torch.float32, device="cuda")
+        n = torch.zeros(1, dtype=torch.int32, device="cuda")
+        capi.rt_render_stereo_reproj(g.handle, s.camera, s.eye_sep, s.convergence, s.W, s.H,
+                                     s.max_depth, net.handle if net else None, threshold, L, R, n)
+        capi.rt_sync_status(g.handle)
+        if net:
+            capi.rt_net_status(net.handle)
+        return full, L, R, int(n.item())
+    finally:
+        g.close()
+        if net:
+            net.close()
+
+
+def test_reprojection_with_everything_retraced_equals_full_trace():
+    import torch
+    s = sg.config_small(1, W=200, H=120)
+    params = np.zeros(sg.NET_PARAMS, np.float32)
+    params[-1] = 20.0                                     # p = sigmoid(20) ~ 1 everywhere
+    full, L, R, n = _full_and_reproj(s, params, 0.5)
+    assert n == s.W * s.H
+    assert torch.equal(L, full[0]) and torch.equal(R, full[1])
+
+
+def test_reprojection_holes_only_is_close_to_full_trace():
+    import torch
+    s = sg.config_small(2, W=320, H=240)
+    full, L, R, n = _full_and_reproj(s, None, 0.5)
+    assert torch.equal(L, full[0])
+    mse = torch.mean((R - full[1]) ** 2).item()
+    psnr = 10 * np.log10(1.0 / max(mse, 1e-12))
+    assert 0 < n < 0.1 * s.W * s.H and psnr > 25, (n, psnr)
+
+
+def test_training_pair_labels_cover_holes():
+    import torch
+    s = sg.config_small(3, W=160, H=96)
+    g = capi.GpuScene(s)
+    try:
+        P = s.W * s.H
+        L = torch.empty((s.H, s.W, 3), dtype=torch.float32, device="cuda")
+        R = torch.empty_like(L)
+        f16 = torch.empty((P, 16), dtype=torch.bfloat16, device="cuda")
+        lab = torch.empty(P, dtype=torch.float32, device="cuda")
+        capi.rt_reproj_training_pair(g.handle, s.camera, s.eye_sep, s.convergence, s.W, s.H,
+                                     s.max_depth, L, R, f16, lab, 1e-2)
+        capi.rt_sync_status(g.handle)
+        full = g.render()["rgb"]
+        assert torch.equal(L, full[0]) and torch.equal(R, full[1])
+        holes = (f16.float().abs().sum(dim=1) == 0)
+        assert bool((lab[holes] == 1).all())
+        assert 0.0 < lab.mean().item() < 0.5
+    finally:
+        g.close()

@@ -1,0 +1,174 @@
+"""Pins of the reprojection / network oracle (CPU only)."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import reproj as orp
+from paper_1702_01530_gb300 import scenegen as sg
+
+
+def _fmix32_int(h):
+    h &= 0xFFFFFFFF
+    h ^= h >> 16
+    h = (h * 0x85EBCA6B) & 0xFFFFFFFF
+    h ^= h >> 13
+    h = (h * 0xC2B2AE35) & 0xFFFFFFFF
+    h ^= h >> 16
+    return h
+
+
+def test_fmix32_matches_integer_definition_and_known_values():
+    assert _fmix32_int(0) == 0 and _fmix32_int(1) == 0x514E28B7
+    xs = np.array([0, 1, 2, 999, 0xFFFFFFFF, 123456789], np.uint32)
+    assert orp.fmix32(xs).tolist() == [_fmix32_int(int(x)) for x in xs]
+
+
+def _plane(W, H, z):
+    P = W * H
+    depth = np.full(P, z, np.float32)
+    normal = np.tile(np.array([0, 0, 1], np.float32), (P, 1))
+    ids = np.arange(P, dtype=np.uint32)
+    rgb = np.random.default_rng(0).random((P, 3)).astype(np.float32)
+    return depth, normal, ids, rgb
+
+
+def test_warp_of_fronto_parallel_plane_is_a_uniform_shift():
+    # D = f s (1/z - 1/zc) = 100 * 0.1 * (1/2.5 - 1/10) = 3 pixels exactly
+    W, H = 40, 6
+    depth, normal, ids, rgb = _plane(W, H, 2.5)
+    D = orp.disparity32(2.5, 100.0, 0.1, 10.0)
+    assert D == np.float32(3.0)
+    feat, hole, warped, src = orp.warp(depth, normal, ids, rgb, W, H, 100.0, 0.1, 10.0)
+    hole = hole.reshape(H, W)
+    assert hole[:, W - 3:].all() and not hole[:, :W - 3].any()     # right edge uncovered
+    src = src.reshape(H, W)
+    jj, ii = np.mgrid[0:H, 0:W - 3]
+    assert np.array_equal(src[:, :W - 3], jj * W + ii + 3)         # x_R = x_L - 3
+    f = feat.reshape(H, W, 9)
+    assert np.allclose(f[:, :W - 3, 8], 3.0 / 16) and np.allclose(f[:, :W - 3, 0], 0.025)
+    assert np.allclose(f[:, :W - 3, 1:4], [0, 0, 1]) and (f[:, W - 3:] == 0).all()
+    # misses are sources at infinity: D = -f s / zc = -1 -> they fill column 0.. from the left
+    depth_m = np.full(W * H, np.inf, np.float32)
+    _, hole_m, _, src_m = orp.warp(depth_m, normal, ids, rgb, W, H, 100.0, 0.1, 10.0)
+    assert hole_m.reshape(H, W)[:, 0].all() and not hole_m.reshape(H, W)[:, 1:].any()
+    assert src_m.reshape(H, W)[0, 1] == 0
+    # farther than the convergence plane: the shift goes the other way
+    depth2 = np.full(W * H, 40.0, np.float32)                      # D = 10 (0.025 - 0.1) = -0.75
+    _, hole2, _, src2 = orp.warp(depth2, normal, ids, rgb, W, H, 100.0, 0.1, 10.0)
+    assert hole2.reshape(H, W)[:, 0].all() and not hole2.reshape(H, W)[:, 1:].any()
+    assert src2.reshape(H, W)[0, 5] == 4                           # floor(4 + 0.75 + 0.5) = 5
+
+
+def test_warp_z_test_keeps_nearest_then_lowest_index():
+    W, H = 8, 1
+    depth = np.zeros(8, np.float32)       # depth <= 0: not a source
+    # pixels 5 and 6 both land on column 3 with f=100, s=0.1, zc=10:
+    # pixel 5 at D=2 (z=1/(0.2+0.1)), pixel 6 at D=3 (z=2.5)
+    z5 = np.float32(1.0 / 0.3)
+    depth[5], depth[6] = z5, 2.5
+    d5 = orp.disparity32(z5, 100.0, 0.1, 10.0)
+    assert math.floor(5 - d5 + 0.5) == 3
+    normal = np.zeros((8, 3), np.float32)
+    ids = np.arange(8, dtype=np.uint32)
+    rgb = np.zeros((8, 3), np.float32)
+    _, hole, _, src = orp.warp(depth, normal, ids, rgb, W, H, 100.0, 0.1, 10.0)
+    assert src[3] == 6                    # z = 2.5 is nearer than 3.33
+    depth[5] = 2.5                        # now equal depth: lands on 2.. move both to one target
+    depth[4] = 2.5                        # pixel 4 -> column 1, pixel 5 -> 2, pixel 6 -> 3
+    _, _, _, src = orp.warp(depth, normal, ids, rgb, W, H, 100.0, 0.1, 10.0)
+    assert src[1:4].tolist() == [4, 5, 6] and hole.sum() == 7
+
+
+def test_labels_definition():
+    hole = np.array([1, 0, 0, 0], bool)
+    w = np.zeros((4, 3))
+    f = np.array([[0, 0, 0], [0.005, 0, 0], [0, 0.0101, 0], [0, 0, 0]])
+    assert orp.labels(hole, w, f, 1e-2).tolist() == [1, 0, 1, 0]
+
+
+def _conv_loops(x, w, b):
+    """Explicit 3x3 zero-padded cross-correlation (independent of PyTorch)."""
+    C, H, W = x.shape
+    co = w.shape[0]
+    out = np.zeros((co, H, W))
+    xp = np.zeros((C, H + 2, W + 2))
+    xp[:, 1:-1, 1:-1] = x
+    for o in range(co):
+        for y in range(H):
+            for xx in range(W):
+                out[o, y, xx] = b[o] + np.sum(w[o] * xp[:, y:y + 3, xx:xx + 3])
+    return out
+
+
+def test_network_forward_matches_explicit_loops():
+    W, H = 5, 4
+    params = sg.net_params_he(3).astype(np.float64)
+    params[params.size - 1] = 0.3
+    feat = sg.bf16_features_synthetic(4, W, H)
+    x = feat[:, :9].reshape(H, W, 9).transpose(2, 0, 1).astype(np.float64)
+    for li, (w, b) in enumerate(orp.unpack(params)):
+        x = _conv_loops(x, w, b)
+        if li < 3:
+            x = np.maximum(x, 0)
+    ref = 1 / (1 + np.exp(-x[0]))
+    assert np.allclose(orp.forward(params, feat, W, H, bf16=False), ref, atol=1e-12)
+    assert np.abs(orp.forward(params, feat, W, H, bf16=True) - ref).max() < 2e-2
+
+
+def test_network_constant_output_and_bce_closed_form():
+    W, H = 6, 3
+    params = np.zeros(sg.NET_PARAMS)
+    params[-1] = 2.0
+    feat = sg.bf16_features_synthetic(5, W, H)
+    assert np.allclose(orp.forward(params, feat, W, H), 1 / (1 + math.exp(-2.0)))
+    y = (np.arange(W * H) % 3 == 0).astype(np.float64)
+    s = 1 / (1 + math.exp(-2.0))
+    loss, g = orp.loss_and_grads(params, feat, y, W, H)
+    assert abs(loss - (-(y * math.log(s) + (1 - y) * math.log(1 - s)).mean())) < 1e-12
+    assert abs(g[-1] - (s - y).mean()) < 1e-12          # d loss / d b4 = mean(p - y)
+
+
+def test_network_gradient_matches_central_differences():
+    W, H = 5, 4
+    params = sg.net_params_he(7).astype(np.float64)
+    params += 0.01 * np.random.default_rng(1).standard_normal(params.size)
+    feat = sg.bf16_features_synthetic(8, W, H)
+    y = (np.random.default_rng(2).random(W * H) < 0.3).astype(np.float64)
+    _, g = orp.loss_and_grads(params, feat, y, W, H)
+    rng = np.random.default_rng(3)
+    idx = np.concatenate([rng.choice(2592, 6, replace=False), [2600, 2624 + 5, 21087, 21120 + 7, 21408]])
+    h = 1e-6
+    for i in idx:
+        pp, pm = params.copy(), params.copy()
+        pp[i] += h
+        pm[i] -= h
+        fd = (orp.loss_and_grads(pp, feat, y, W, H)[0] - orp.loss_and_grads(pm, feat, y, W, H)[0]) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(g[i])) + 1e-9, (i, fd, g[i])
+
+
+def test_emulated_backward_equals_autograd_without_rounding():
+    W, H = 6, 5
+    params = sg.net_params_he(9).astype(np.float64)
+    params[2592:2624] = 0.05
+    feat = sg.bf16_features_synthetic(10, W, H)
+    y = (np.random.default_rng(4).random(W * H) < 0.4).astype(np.float64)
+    _, g = orp.loss_and_grads(params, feat, y, W, H)
+    ge = orp.grads_emulated(params, feat, y, W, H, bf16=False)
+    assert np.abs(ge - g).max() <= 1e-12 * max(1.0, np.abs(g).max())
+    gb = orp.grads_emulated(params, feat, y, W, H, bf16=True)
+    cos = gb @ g / (np.linalg.norm(gb) * np.linalg.norm(g))
+    assert cos > 0.99
+
+
+def test_generators_for_reprojection():
+    d, n, ids, rgb = sg.gbuffer_synthetic(1, 30, 20)
+    assert np.isinf(d).mean() == pytest.approx(0.2, abs=0.06)
+    assert np.allclose(np.linalg.norm(n, axis=1), 1.0, atol=1e-6)
+    assert (ids[np.isinf(d)] == 0xFFFFFFFF).all() and (ids[~np.isinf(d)] < 1000).all()
+    f = sg.bf16_features_synthetic(2, 10, 10)
+    import torch
+    t = torch.tensor(f)
+    assert torch.equal(t.to(torch.bfloat16).to(torch.float32), t)
+    p = sg.net_params_he(0)
+    assert p.size == sg.NET_PARAMS == 21409 and p[2592:2624].max() == 0
