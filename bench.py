@@ -57,6 +57,8 @@ def parse():
                          "(0 = every pixel of one stereo pair)")
     ap.add_argument("--ncu", action="store_true",
                     help="profiling mode: build the scene, render twice, exit")
+    ap.add_argument("--ncu-net", action="store_true",
+                    help="profiling mode: run the retrace network on 1080p features twice, exit")
     return ap.parse_args()
 
 
@@ -383,9 +385,35 @@ def run_reference(args, rank, world):
     print(json.dumps(line))
 
 
+def run_ncu_net(args):
+    """Two forward passes of the retrace network over a 1080p feature map."""
+    import torch
+
+    from paper_1702_01530_gb300 import build as rtbuild
+    from paper_1702_01530_gb300 import capi, train_reproj
+    rtbuild.build()
+    params, _ = train_reproj.load_weights()
+    W, H = args.W, args.H
+    f = torch.from_numpy(sg_features(W, H)).to(torch.bfloat16).cuda()
+    prob = torch.empty(W * H, dtype=torch.float32, device="cuda")
+    net = capi.Net(params)
+    for _ in range(2):
+        capi.rt_net_forward(net.handle, f, W, H, prob)
+    capi.rt_net_status(net.handle)
+    net.close()
+
+
+def sg_features(W, H):
+    from paper_1702_01530_gb300 import scenegen as sg
+    return sg.bf16_features_synthetic(5, W, H)
+
+
 def main():
     args = parse()
     rank, world, local = dist_setup(args)
+    if args.ncu_net:
+        run_ncu_net(args)
+        return
     if args.impl == "reference":
         run_reference(args, rank, world)
     else:

@@ -207,10 +207,13 @@ int rt_debug_set_node(rt_scene* scene, uint32_t node, int32_t left, int32_t righ
  * event on its stream after each stage. rt_profile_read waits for the last
  * render's events and writes RT_NUM_STAGES floats (milliseconds) to the
  * HOST array ms: [0] clears, [1] ray tracing (primary, shadow and mirror
- * rays of both eyes, one persistent kernel), [2] resolve to float RGB.
+ * rays, one persistent kernel), [2] resolve to float RGB, and for
+ * rt_render_stereo_reproj [3] forward warp, [4] retrace network, [5] retrace
+ * mask, [6] tracing the masked right pixels, [7] right-image composition
+ * (stages a call does not run read 0).
  * Returns RT_ERR_INVALID_ARG if profiling was off during the last render.
  */
-#define RT_NUM_STAGES 3
+#define RT_NUM_STAGES 8
 int rt_profile_enable(rt_scene* scene, int on);
 int rt_profile_read(const rt_scene* scene, float* ms);
 

@@ -202,7 +202,7 @@ def rt_debug_set_node(scene, node, left, right, empty_right=False):
     _check(lib().rt_debug_set_node(scene, node, left, right, int(bool(empty_right))))
 
 
-STAGES = ("clear", "trace", "resolve")
+STAGES = ("clear", "trace", "resolve", "warp", "net", "mask", "retrace", "compose")
 
 
 def rt_profile_enable(scene, on=True):

@@ -3,15 +3,17 @@
 // and FP32 accumulation on the 5th-generation tensor cores (sm_103a).
 //
 // Convolution as implicit GEMM on tcgen05:
-//   one CTA (128 threads) computes a tile of 128 consecutive pixels of one
-//   image row: D[128 pixels, Cout] = sum over the 9 taps (dy, dx) of
-//   A_tap[128, Cin] x B_tap[Cin, Cout]. The input halo (3 rows x 130 pixels x
+//   a persistent CTA (128 threads) computes tiles of R rows x 128 consecutive
+//   pixels: per row, D[128 pixels, Cout] = sum over the 9 taps (dy, dx) of
+//   A_tap[128, Cin] x B_tap[Cin, Cout]. The input halo (R+2 rows x 130 pixels x
 //   Cin channels, BF16) sits in shared memory as 16-byte (8-channel) chunks
 //   ordered [chunk][halo pixel], so A_tap for every tap is the same matrix
-//   shifted by dy*130 + dx rows: the K-major, non-swizzled operand layout
+//   shifted by (row+dy)*130 + dx rows: the K-major, non-swizzled operand layout
 //   with 8-row core matrices 128 B apart (SBO) and 8-channel chunks
-//   390*16 B apart (LBO). Weights are pre-packed in the same core-matrix
-//   layout. One elected thread issues 9 * Cin/16 tcgen05.mma (M=128,
+//   (R+2)*130*16 B apart (LBO). Weights are pre-packed in the same core-matrix
+//   layout. Halos stream in with 16-byte cp.async copies (zero-filled
+//   outside the image); with one buffer the next tile's copies start as soon
+//   as the MMAs of this tile have consumed it, under the epilogue. One elected thread issues 9 * Cin/16 tcgen05.mma (M=128,
 //   N=Cout, K=16, kind::f16 with BF16 inputs) into a TMEM accumulator,
 //   commits to an mbarrier; the four warps read their 32 TMEM lanes
 //   (tcgen05.ld 32x32b) for the fused epilogue (bias + ReLU -> BF16, or
@@ -34,9 +36,22 @@
 namespace rt {
 namespace nn {
 
-constexpr int kTileM = 128;          // pixels per tile (one MMA M block)
+// Tuning knobs: RT_CONV_ROWS = image rows per tile (R accumulators of
+// 128 pixels share one halo of R+2 rows); RT_CONV_DBUF = 1 double-buffers
+// the halo (the next tile loads while this one computes). Measured on GB300
+// at 1920x1080 (network forward, 4 layers, identical output bit for bit):
+// R=1 0.52 ms, R=2 0.45-0.48, R=4 0.42-0.43, R=8 single-buffered 0.40 ms.
+#ifndef RT_CONV_ROWS
+#define RT_CONV_ROWS 8
+#endif
+#ifndef RT_CONV_DBUF
+#define RT_CONV_DBUF 0
+#endif
+constexpr int kRows = RT_CONV_ROWS;
+constexpr int kBufs = RT_CONV_DBUF ? 2 : 1;
+constexpr int kTileM = 128;          // pixels per row tile (one MMA M block)
 constexpr int kHaloW = kTileM + 2;   // 130
-constexpr int kHaloRows = 3 * kHaloW;  // 390 halo pixels
+constexpr int kHaloRows = (kRows + 2) * kHaloW;  // halo pixels per tile
 constexpr uint32_t kWaitBound = 1u << 26;
 
 enum Epi : int { EPI_RELU_BF16 = 0, EPI_SIGMOID_F32 = 1, EPI_BWD_MASK_BF16 = 2 };
@@ -117,6 +132,15 @@ __device__ __forceinline__ void fence_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
+// 16-byte asynchronous global->shared copy; src_bytes = 0 writes zeros
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, uint32_t src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src),
+               "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
 // 16 consecutive TMEM columns of this warp's 32 lanes
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
   uint32_t r[16];
@@ -142,6 +166,26 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
 // EPI_RELU_BF16:     out16[P][COUT] = relu(acc + bias)
 // EPI_SIGMOID_F32:   out32[P] = sigmoid(acc[0] + bias[0])
 // EPI_BWD_MASK_BF16: out16[P][COUT] = acc * (mask16[P][COUT] > 0)
+template <int CIN>
+__device__ __forceinline__ void load_halo_async(unsigned char* halo, const __nv_bfloat16* in,
+                                                uint32_t tile, uint32_t tiles_x, uint32_t W,
+                                                uint32_t H, int tid) {
+  constexpr int kChunks = CIN / 8;
+  const int ty = (int)(tile / tiles_x);
+  const int y = ty * kRows;
+  const int x0 = (int)(tile - (uint32_t)ty * tiles_x) * kTileM;
+  // 16-byte chunk c of halo pixel r goes to ((c * kHaloRows) + r) * 16; consecutive
+  // threads take consecutive halo pixels of one chunk (conflict-free stores)
+  for (int k = tid; k < kHaloRows * kChunks; k += 128) {
+    const int c = k / kHaloRows, r = k - c * kHaloRows;
+    const int dy = r / kHaloW, xx = r - dy * kHaloW;
+    const int gy = y + dy - 1, gx = x0 + xx - 1;
+    const bool ok = gy >= 0 && gy < (int)H && gx >= 0 && gx < (int)W;
+    const __nv_bfloat16* src = ok ? in + ((size_t)gy * W + gx) * CIN + c * 8 : in;
+    cp_async16(halo + ((size_t)c * kHaloRows + r) * 16, src, ok ? 16u : 0u);
+  }
+}
+
 template <int CIN, int COUT, int EPI>
 __global__ void __launch_bounds__(128) k_conv_tc(const __nv_bfloat16* __restrict__ in,
                                                   const __nv_bfloat16* __restrict__ wpk,
@@ -153,19 +197,25 @@ __global__ void __launch_bounds__(128) k_conv_tc(const __nv_bfloat16* __restrict
   static_assert(CIN % 16 == 0 && (COUT == 16 || COUT == 32), "shape");
   constexpr int kChunks = CIN / 8;
   constexpr uint32_t kHaloBytes = kHaloRows * CIN * 2;
+  constexpr uint32_t kHaloStride = (kHaloBytes + 1023) & ~1023u;
   constexpr uint32_t kWBytes = 9 * COUT * CIN * 2;
   constexpr uint32_t kLBO_A = kHaloRows * 16;   // next 8-channel chunk of the halo
   constexpr uint32_t kLBO_B = COUT * 16;        // next 8-channel chunk of a weight tap
-  constexpr uint32_t kTmemCols = 32;
+  constexpr uint32_t kAccCols = kRows * COUT;   // one accumulator per output row
+  constexpr uint32_t kTmemCols = kAccCols <= 32 ? 32 : (kAccCols <= 64 ? 64 : (kAccCols <= 128 ? 128 : 256));
   extern __shared__ __align__(1024) unsigned char smem[];
-  unsigned char* halo = smem;
-  unsigned char* wsm = smem + ((kHaloBytes + 1023) & ~1023u);
+  unsigned char* halo0 = smem;                  // kBufs halo buffers
+  unsigned char* wsm = smem + kBufs * kHaloStride;
   float* bsm = reinterpret_cast<float*>(wsm + ((kWBytes + 127) & ~127u));
   uint64_t* bar = reinterpret_cast<uint64_t*>(bsm + 32);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 1);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  // weights and bias -> shared memory (once per CTA)
+  const uint32_t tiles_x = (W + kTileM - 1) / kTileM;
+  const uint32_t n_tiles = tiles_x * ((H + kRows - 1) / kRows);
+  // first halo in flight while the weights are copied
+  if (blockIdx.x < n_tiles) load_halo_async<CIN>(halo0, in, blockIdx.x, tiles_x, W, H, tid);
+  cp_async_commit();
   {
     const uint4* src = reinterpret_cast<const uint4*>(wpk);
     uint4* dst = reinterpret_cast<uint4*>(wsm);
@@ -183,101 +233,119 @@ __global__ void __launch_bounds__(128) k_conv_tc(const __nv_bfloat16* __restrict
   fence_after();
   const uint32_t tmem = *tslot;
   const uint32_t idesc = make_idesc(kTileM, COUT);
-  const uint32_t tiles_x = (W + kTileM - 1) / kTileM;
-  const uint32_t n_tiles = tiles_x * H;
   uint32_t phase = 0;
-  bool ok = true;
+  uint32_t it = 0;
 
-  for (uint32_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
-    const int y = (int)(tile / tiles_x);
-    const int x0 = (int)(tile - (uint32_t)y * tiles_x) * kTileM;
-    // halo -> shared: 16-byte chunk c of halo pixel r at ((c * 390) + r) * 16
-    for (int k = tid; k < kHaloRows * kChunks; k += 128) {
-      const int c = k / kHaloRows, r = k - c * kHaloRows;
-      const int dy = r / kHaloW, xx = r - dy * kHaloW;
-      const int gy = y + dy - 1, gx = x0 + xx - 1;
-      uint4 v = make_uint4(0u, 0u, 0u, 0u);
-      if (gy >= 0 && gy < (int)H && gx >= 0 && gx < (int)W)
-        v = *reinterpret_cast<const uint4*>(in + ((size_t)gy * W + gx) * CIN + c * 8);
-      *reinterpret_cast<uint4*>(halo + ((size_t)c * kHaloRows + r) * 16) = v;
+  for (uint32_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++it) {
+    unsigned char* halo = halo0 + (kBufs == 2 ? (it & 1u) : 0u) * kHaloStride;
+    const uint32_t next = tile + gridDim.x;
+    if (kBufs == 2) {
+      // next tile's halo into the other buffer (freed at the end of the last iteration)
+      if (next < n_tiles)
+        load_halo_async<CIN>(halo0 + ((it + 1) & 1u) * kHaloStride, in, next, tiles_x, W, H, tid);
+      cp_async_commit();
+      cp_async_wait_1();          // this tile's halo has landed
+    } else {
+      asm volatile("cp.async.wait_all;" ::: "memory");
     }
     fence_async_smem();
     fence_before();
     __syncthreads();
     fence_after();
+    const int ty = (int)(tile / tiles_x);
+    const int y = ty * kRows;
+    const int x0 = (int)(tile - (uint32_t)ty * tiles_x) * kTileM;
     if (tid == 0) {
       const uint32_t hbase = smem_u32(halo), wbase = smem_u32(wsm);
-      uint32_t acc = 0;
 #pragma unroll
-      for (int tap = 0; tap < 9; ++tap) {
-        const int dy = tap / 3, dx = tap % 3;
+      for (int ry = 0; ry < kRows; ++ry) {
+        uint32_t acc = 0;
 #pragma unroll
-        for (int ks = 0; ks < CIN / 16; ++ks) {
-          const uint64_t da =
-              make_desc(hbase + (uint32_t)((2 * ks) * kHaloRows + dy * kHaloW + dx) * 16u, kLBO_A, 128u);
-          const uint64_t db =
-              make_desc(wbase + (uint32_t)((tap * kChunks + 2 * ks) * COUT) * 16u, kLBO_B, 128u);
-          mma_bf16(tmem, da, db, idesc, acc);
-          acc = 1;
+        for (int tap = 0; tap < 9; ++tap) {
+          const int dy = tap / 3, dx = tap % 3;
+#pragma unroll
+          for (int ks = 0; ks < CIN / 16; ++ks) {
+            const uint64_t da = make_desc(
+                hbase + (uint32_t)((2 * ks) * kHaloRows + (ry + dy) * kHaloW + dx) * 16u, kLBO_A, 128u);
+            const uint64_t db =
+                make_desc(wbase + (uint32_t)((tap * kChunks + 2 * ks) * COUT) * 16u, kLBO_B, 128u);
+            mma_bf16(tmem + (uint32_t)(ry * COUT), da, db, idesc, acc);
+            acc = 1;
+          }
         }
       }
       mma_commit(bar);
     }
-    ok = mbar_wait(bar, phase);
+    const bool ok = mbar_wait(bar, phase);
     phase ^= 1u;
     fence_after();
     if (!ok) {
       if (tid == 0) atomicOr(err, ERR_ITER);
-      break;
+      break;                       // uniform: every thread saw the same barrier state
     }
-    // epilogue: warp w owns TMEM lanes (pixels) 32w .. 32w + 31
+    // epilogue: warp w owns TMEM lanes (pixels) 32w .. 32w + 31 of every row
+    if (kBufs == 1 && next < n_tiles) {
+      // single buffer: the halo was consumed by the MMAs (barrier passed), so
+      // the next tile's loads may start under the epilogue
+      fence_before();
+      __syncthreads();
+      fence_after();
+      load_halo_async<CIN>(halo0, in, next, tiles_x, W, H, tid);
+      cp_async_commit();
+    }
     const int x = x0 + warp * 32 + lane;
-    const size_t p = (size_t)y * W + x;
-    const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
-    if (EPI == EPI_SIGMOID_F32) {
-      float v[16];
-      tmem_ld16(lane_addr, v);
-      if (x < (int)W) out32[p] = 1.f / (1.f + __expf(-(v[0] + bsm[0])));
-    } else {
 #pragma unroll
-      for (int half = 0; half < COUT / 16; ++half) {
+    for (int ry = 0; ry < kRows; ++ry) {
+      const int yy = y + ry;
+      const bool valid = x < (int)W && yy < (int)H;
+      const size_t p = (size_t)yy * W + x;
+      const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(ry * COUT);
+      if (EPI == EPI_SIGMOID_F32) {
         float v[16];
-        tmem_ld16(lane_addr + half * 16, v);
-        if (x < (int)W) {
-          uint32_t packed[8];
-          if (EPI == EPI_RELU_BF16) {
+        tmem_ld16(lane_addr, v);
+        if (valid) out32[p] = 1.f / (1.f + __expf(-(v[0] + bsm[0])));
+      } else {
 #pragma unroll
-            for (int i = 0; i < 8; ++i)
-              packed[i] = pack_bf16(fmaxf(v[2 * i] + bsm[half * 16 + 2 * i], 0.f),
-                                    fmaxf(v[2 * i + 1] + bsm[half * 16 + 2 * i + 1], 0.f));
-          } else {
-            const uint4* m4 = reinterpret_cast<const uint4*>(mask16 + p * COUT + half * 16);
-            const uint4 ma = m4[0], mb = m4[1];
-            const uint32_t mw[8] = {ma.x, ma.y, ma.z, ma.w, mb.x, mb.y, mb.z, mb.w};
+        for (int half = 0; half < COUT / 16; ++half) {
+          float v[16];
+          tmem_ld16(lane_addr + half * 16, v);
+          if (valid) {
+            uint32_t packed[8];
+            if (EPI == EPI_RELU_BF16) {
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-              const __nv_bfloat162 mm = *reinterpret_cast<const __nv_bfloat162*>(&mw[i]);
-              const float m0 = __bfloat162float(mm.x), m1 = __bfloat162float(mm.y);
-              packed[i] = pack_bf16(m0 > 0.f ? v[2 * i] : 0.f, m1 > 0.f ? v[2 * i + 1] : 0.f);
+              for (int i = 0; i < 8; ++i)
+                packed[i] = pack_bf16(fmaxf(v[2 * i] + bsm[half * 16 + 2 * i], 0.f),
+                                      fmaxf(v[2 * i + 1] + bsm[half * 16 + 2 * i + 1], 0.f));
+            } else {
+              const uint4* m4 = reinterpret_cast<const uint4*>(mask16 + p * COUT + half * 16);
+              const uint4 ma = m4[0], mb = m4[1];
+              const uint32_t mw[8] = {ma.x, ma.y, ma.z, ma.w, mb.x, mb.y, mb.z, mb.w};
+#pragma unroll
+              for (int i = 0; i < 8; ++i) {
+                const __nv_bfloat162 mm = *reinterpret_cast<const __nv_bfloat162*>(&mw[i]);
+                const float m0 = __bfloat162float(mm.x), m1 = __bfloat162float(mm.y);
+                packed[i] = pack_bf16(m0 > 0.f ? v[2 * i] : 0.f, m1 > 0.f ? v[2 * i + 1] : 0.f);
+              }
             }
+            uint4* o = reinterpret_cast<uint4*>(out16 + p * COUT + half * 16);
+            o[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+            o[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
           }
-          uint4* o = reinterpret_cast<uint4*>(out16 + p * COUT + half * 16);
-          o[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
-          o[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
         }
       }
     }
     fence_before();
-    __syncthreads();  // TMEM read and halo consumed before the next tile
+    __syncthreads();  // TMEM read and this halo consumed before they are reused
     fence_after();
   }
+  asm volatile("cp.async.wait_all;" ::: "memory");
   __syncthreads();
   if (warp == 0) tmem_dealloc(tmem, kTmemCols);
 }
 
 template <int CIN, int COUT>
 constexpr size_t conv_smem_bytes() {
-  return ((kHaloRows * CIN * 2 + 1023) & ~1023) + ((9 * COUT * CIN * 2 + 127) & ~127) + 32 * 4 + 16;
+  return kBufs * ((kHaloRows * CIN * 2 + 1023) & ~1023) + ((9 * COUT * CIN * 2 + 127) & ~127) + 32 * 4 + 16;
 }
 
 // ------------------------------------------------ weight packing (FP32 -> BF16)
@@ -458,10 +526,12 @@ cudaError_t launch_conv(const __nv_bfloat16* in, const __nv_bfloat16* wpk, const
     if (e != cudaSuccess) return e;
     configured = smem;
   }
-  int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_conv_tc<CIN, COUT, EPI>, 128, smem);
+  // resident CTAs per SM from the shared-memory footprint (227 KB usable, 1 KB
+  // reserved per CTA); TMEM (32 columns each) and registers allow more
+  int per_sm = (int)((227u * 1024u) / (smem + 1024u));
   if (per_sm < 1) per_sm = 1;
-  const uint32_t tiles = ((W + kTileM - 1) / kTileM) * H;
+  if (per_sm > 8) per_sm = 8;
+  const uint32_t tiles = ((W + kTileM - 1) / kTileM) * ((H + kRows - 1) / kRows);
   uint32_t grid = (uint32_t)(num_sms() * per_sm);
   if (grid > tiles) grid = tiles;
   k_conv_tc<CIN, COUT, EPI><<<grid, 128, smem, st>>>(in, wpk, bias, mask16, out16, out32, W, H, err);

@@ -91,10 +91,17 @@ __global__ void k_warp_gather(const unsigned long long* __restrict__ zbuf,
       f[7] = rgb_L[3 * (size_t)q + 2];
       f[8] = disparity(z, fs, inv_zc) * kDispScale;
     }
-    if (feat16) {
-      __nv_bfloat16* o = feat16 + 16 * (size_t)p;
+    if (feat16) {                          // 32 bytes per pixel as two 16-byte stores
+      uint32_t w[8];
 #pragma unroll
-      for (int c = 0; c < 16; ++c) o[c] = __float2bfloat16_rn(c < 9 ? f[c] : 0.f);
+      for (int c = 0; c < 8; ++c) {
+        const float lo = 2 * c < 9 ? f[2 * c] : 0.f, hi = 2 * c + 1 < 9 ? f[2 * c + 1] : 0.f;
+        __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+        w[c] = *reinterpret_cast<uint32_t*>(&h);
+      }
+      uint4* o = reinterpret_cast<uint4*>(feat16 + 16 * (size_t)p);
+      o[0] = make_uint4(w[0], w[1], w[2], w[3]);
+      o[1] = make_uint4(w[4], w[5], w[6], w[7]);
     }
     if (feat32) {
 #pragma unroll

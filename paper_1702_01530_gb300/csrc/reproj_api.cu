@@ -242,6 +242,7 @@ int rt_reproj_training_pair(const rt_scene* scene, const rt_camera* cam, float e
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   a.out_L = d_out_L; a.out_R = d_out_R;
   a.hit_L = rp.id_L; a.depth_L = rp.depth_L; a.normal_L = rp.normal_L;
+  rt::profile_begin(const_cast<rt_scene*>(scene)->ws, st);
   cudaError_t e = rt::render(a, const_cast<rt_scene*>(scene)->ws, st);
   if (e == cudaSuccess)
     e = rt::reproj_warp(rp.depth_L, rp.normal_L, rp.id_L, d_out_L, W, H, focal_px(cam, H), eye_sep,
@@ -269,6 +270,7 @@ int rt_render_stereo_reproj(const rt_scene* scene, const rt_camera* cam, float e
   rt::ReprojBuffers& rp = sc->ws.rp;
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   // 1. left eye with its G-buffer
+  rt::profile_begin(sc->ws, st);
   a.eyes = 1u;
   a.out_L = d_out_L; a.out_R = d_out_R;
   a.hit_L = rp.id_L; a.depth_L = rp.depth_L; a.normal_L = rp.normal_L;
@@ -276,15 +278,20 @@ int rt_render_stereo_reproj(const rt_scene* scene, const rt_camera* cam, float e
   // 2. forward warp to the right grid, network features
   if (e == cudaSuccess)
     e = rt::reproj_warp(rp.depth_L, rp.normal_L, rp.id_L, d_out_L, W, H, focal_px(cam, H), eye_sep,
-                        convergence, rp.zbuf, rp.feat16, nullptr, rp.hole, rp.warped, st);
+                        convergence, rp.zbuf, net ? rp.feat16 : nullptr, nullptr, rp.hole,
+                        rp.warped, st);
+  rt::profile_mark(sc->ws, rt::ST_WARP, st);
   // 3. retrace probability
-  if (e == cudaSuccess && net)
+  if (e == cudaSuccess && net) {
     e = rt::nn::forward(rp.feat16, net->params, net->wf, rp.act[0], rp.act[1], rp.act[2], rp.prob,
                         W, H, net->err, st);
+    rt::profile_mark(sc->ws, rt::ST_NET, st);
+  }
   // 4. mask = hole or p > threshold, compacted
   if (e == cudaSuccess)
     e = rt::reproj_mask(rp.hole, net ? rp.prob : nullptr, (uint32_t)P, threshold, rp.mask, rp.plist,
                         rp.count, st);
+  rt::profile_mark(sc->ws, rt::ST_MASK, st);
   // 5. trace the masked right pixels (count read on the device)
   if (e == cudaSuccess) {
     rt::RenderArgs b = a;
@@ -294,12 +301,14 @@ int rt_render_stereo_reproj(const rt_scene* scene, const rt_camera* cam, float e
     b.plist_n = 0;
     b.plist_n_dev = rp.count;
     b.resolve = false;
+    b.trace_stage = rt::ST_RETRACE;
     e = rt::render(b, sc->ws, st);
   }
   // 6. compose the right image
   if (e == cudaSuccess)
     e = rt::reproj_compose(rp.mask, sc->ws.accum + 3 * P, rp.warped, (uint32_t)P,
                            1.f / sc->color_scale, d_out_R, st);
+  rt::profile_mark(sc->ws, rt::ST_COMPOSE, st);
   if (e == cudaSuccess && d_n_retraced)
     e = cudaMemcpyAsync(d_n_retraced, rp.count, 4, cudaMemcpyDeviceToDevice, st);
   if (e != cudaSuccess) return cuda_fail(e, "reprojection render");

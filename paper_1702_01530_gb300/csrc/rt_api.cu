@@ -138,6 +138,7 @@ int make_render_args(const rt_scene* scene, const rt_camera* cam, float eye_sep,
   a.err = scene->err;
   a.eyes = 3u;
   a.resolve = true;
+  a.trace_stage = rt::ST_TRACE;
   return RT_OK;
 }
 
@@ -280,7 +281,9 @@ int rt_render_stereo_aux(const rt_scene* scene, const rt_camera* cam, float eye_
   a.depth_L = depth_L; a.depth_R = depth_R;
   a.ray_counts = ray_counts;
   a.work = work;
-  cudaError_t e = rt::render(a, const_cast<rt_scene*>(scene)->ws, static_cast<cudaStream_t>(cuda_stream));
+  rt::Workspace& ws = const_cast<rt_scene*>(scene)->ws;
+  rt::profile_begin(ws, static_cast<cudaStream_t>(cuda_stream));
+  cudaError_t e = rt::render(a, ws, static_cast<cudaStream_t>(cuda_stream));
   if (e != cudaSuccess) return cuda_fail(e, "render launch");
   return RT_OK;
 }

@@ -53,6 +53,20 @@ struct CameraParams {
   uint32_t tiles_x, tiles_y;  // 8x4-pixel tiles per eye
 };
 
+// stages of one render, in launch order
+enum Stage : int {
+  ST_CLEAR = 0,     // counter and accumulator clears
+  ST_TRACE = 1,     // all rays: primary, shadow and mirror (one persistent kernel)
+  ST_RESOLVE = 2,   // fixed-point sums to float RGB
+  ST_WARP = 3,      // reprojection: forward warp and features
+  ST_NET = 4,       // reprojection: retrace network
+  ST_MASK = 5,      // reprojection: retrace mask and compaction
+  ST_RETRACE = 6,   // reprojection: tracing the masked right pixels
+  ST_COMPOSE = 7,   // reprojection: right image composition
+  ST_COUNT = 8
+};
+constexpr int kMaxEvents = 24;
+
 // reprojection scratch of a scene (per right-eye pixel unless noted)
 struct ReprojBuffers {
   void* base = nullptr;
@@ -87,17 +101,9 @@ struct Workspace {
   ReprojBuffers rp;
   // stage timing (CUDA events on the render stream), see Stage
   bool profile = false;
-  cudaEvent_t ev[8] = {};
-  int ev_stage[8] = {};          // stage that ends at event k
+  cudaEvent_t ev[kMaxEvents] = {};
+  int ev_stage[kMaxEvents] = {};  // stage that ends at event k
   int n_ev = 0;
-};
-
-// stages of one render, in launch order
-enum Stage : int {
-  ST_CLEAR = 0,     // counter and accumulator clears
-  ST_TRACE = 1,     // all rays: primary, shadow and mirror (one persistent kernel)
-  ST_RESOLVE = 2,   // fixed-point sums to float RGB
-  ST_COUNT = 3
 };
 
 // counters block layout (uint32 each)
@@ -129,6 +135,7 @@ struct RenderArgs {
   uint32_t plist_n;        // its length, or
   const uint32_t* plist_n_dev;  // its length in device memory (read by the kernel)
   bool resolve;            // write out_L/out_R from the sums (false: caller composes)
+  int trace_stage;         // stage the tracing kernel is timed as (ST_TRACE or ST_RETRACE)
 };
 
 // entry points implemented in the .cu files
@@ -137,6 +144,9 @@ cudaError_t build_lbvh(const float4* d_sph_in, const float* d_tri_in, uint32_t n
                        void* d_tmp, size_t tmp_bytes, uint32_t* d_err, cudaStream_t st);
 size_t lbvh_tmp_bytes(uint32_t n);
 cudaError_t render(const RenderArgs& a, Workspace& ws, cudaStream_t st);
+// stage timing: start a profiled call (resets the event list) / mark the end of a stage
+void profile_begin(Workspace& ws, cudaStream_t st);
+void profile_mark(Workspace& ws, int stage, cudaStream_t st);
 int num_sms();
 int render_grid();      // persistent blocks of the render kernel
 int render_threads();   // threads per block of the render kernel

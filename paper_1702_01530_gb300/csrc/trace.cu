@@ -585,23 +585,21 @@ cudaError_t render_impl(const RenderArgs& a, Workspace& ws, cudaStream_t st) {
                        : (a.eyes == 3u ? 2u : 1u) * a.cam.tiles_x * a.cam.tiles_y;
   const int grid = render_grid();
   if ((uint64_t)grid * (kThreads / 32) > ws.n_warps) return cudaErrorInvalidValue;
-  ws.n_ev = 0;
-  auto mark = [&](int stage) {  // stage timing: an event after each stage
-    if (!ws.profile) return;
-    ws.ev_stage[ws.n_ev] = stage;
-    cudaEventRecord(ws.ev[ws.n_ev++], st);
-  };
-  mark(-1);
   cudaMemsetAsync(ws.counters, 0, C_TOTAL * sizeof(uint32_t), st);
-  cudaMemsetAsync(ws.accum, 0, 2 * P * 3 * sizeof(uint32_t), st);
+  // clear the colour sums of the eyes this render traces
+  const bool left = !a.plist && (a.eyes & 1u), right = a.plist || (a.eyes & 2u);
+  if (left && right) cudaMemsetAsync(ws.accum, 0, 2 * P * 3 * sizeof(uint32_t), st);
+  else if (left) cudaMemsetAsync(ws.accum, 0, P * 3 * sizeof(uint32_t), st);
+  else cudaMemsetAsync(ws.accum + 3 * P, 0, P * 3 * sizeof(uint32_t), st);
   if (a.work) cudaMemsetAsync(a.work, 0, 9 * sizeof(uint64_t), st);
-  mark(ST_CLEAR);
+  profile_mark(ws, ST_CLEAR, st);
   k_render<COUNT><<<grid, kThreads, 0, st>>>(kp);
-  mark(ST_TRACE);
+  profile_mark(ws, a.trace_stage, st);
   const uint32_t n3 = (uint32_t)(P * 3);
-  if (a.resolve)
+  if (a.resolve) {
     k_resolve<<<num_sms() * 8, 256, 0, st>>>(ws.accum, a.out_L, a.out_R, n3, 1.f / a.color_scale);
-  mark(ST_RESOLVE);
+    profile_mark(ws, ST_RESOLVE, st);
+  }
   const uint64_t primary = a.plist ? a.plist_n : (a.eyes == 3u ? 2 * P : P);
   if (a.ray_counts && !a.plist_n_dev) k_counts<<<1, 32, 0, st>>>(ws.counters, primary, a.ray_counts);
   return cudaGetLastError();
@@ -627,6 +625,19 @@ int render_grid() {
 }
 
 int render_threads() { return kThreads; }
+
+void profile_begin(Workspace& ws, cudaStream_t st) {
+  ws.n_ev = 0;
+  if (!ws.profile) return;
+  ws.ev_stage[0] = -1;
+  cudaEventRecord(ws.ev[ws.n_ev++], st);
+}
+
+void profile_mark(Workspace& ws, int stage, cudaStream_t st) {
+  if (!ws.profile || ws.n_ev >= kMaxEvents) return;
+  ws.ev_stage[ws.n_ev] = stage;
+  cudaEventRecord(ws.ev[ws.n_ev++], st);
+}
 
 cudaError_t render(const RenderArgs& a, Workspace& ws, cudaStream_t st) {
   return a.work ? render_impl<true>(a, ws, st) : render_impl<false>(a, ws, st);
