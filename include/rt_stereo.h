@@ -195,10 +195,23 @@ int rt_scene_get_bvh(const rt_scene* scene, uint64_t* keys, int32_t* left, int32
  * its own left child with an empty right child) to check that traversal
  * stops at its iteration bound and rt_sync_status reports RT_ERR_TIMEOUT;
  * every index stays in range, so no memory outside the scene is touched.
- * Synchronises the device.
+ * It edits the binary tree (renders walk it after
+ * rt_scene_set_traversal(scene, 0)). Synchronises the device.
  */
 int rt_debug_set_node(rt_scene* scene, uint32_t node, int32_t left, int32_t right,
                       int empty_right);
+
+/*
+ * rt_scene_set_traversal -- choose the tree renders of this scene walk:
+ * wide == 0 (default) the binary radix tree, wide != 0 the 4-wide tree
+ * derived from it (every inner node at even depth holds its grandchildren;
+ * its top two levels are staged in shared memory). Both hold the same leaves
+ * and boxes and give the same images bit for bit (Table 1 of the paper: BVH
+ * trees). On the 256k-triangle blob scene at 1080p the binary walk is faster
+ * on GB300 (1.52 vs 1.63 ms per pair), hence the default. The instrumented
+ * work counts of rt_render_stereo_aux always follow the binary tree.
+ */
+int rt_scene_set_traversal(rt_scene* scene, int wide);
 
 /*
  * rt_profile_enable / rt_profile_read -- per-stage GPU time of the last

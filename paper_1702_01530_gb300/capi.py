@@ -54,6 +54,7 @@ _SIGS = {
     "rt_debug_set_node": (ctypes.c_int, [_vp, _u32, ctypes.c_int32, ctypes.c_int32,
                                          ctypes.c_int]),
     "rt_profile_enable": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "rt_scene_set_traversal": (ctypes.c_int, [_vp, ctypes.c_int]),
     "rt_profile_read": (ctypes.c_int, [_vp, _vp]),
     "rt_build_lbvh_noalloc": (ctypes.c_int, [_vp, _u32, _vp, _u32, _vp, _vp, _vp, _vp, _vp]),
     "rt_net_create": (ctypes.c_int, [_vp, _u32, ctypes.POINTER(_vp)]),
@@ -203,6 +204,10 @@ def rt_debug_set_node(scene, node, left, right, empty_right=False):
 
 
 STAGES = ("clear", "trace", "resolve", "warp", "net", "mask", "retrace", "compose")
+
+
+def rt_scene_set_traversal(scene, wide=True):
+    _check(lib().rt_scene_set_traversal(scene, int(bool(wide))))
 
 
 def rt_profile_enable(scene, on=True):

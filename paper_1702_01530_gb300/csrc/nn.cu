@@ -527,8 +527,11 @@ cudaError_t launch_conv(const __nv_bfloat16* in, const __nv_bfloat16* wpk, const
     configured = smem;
   }
   // resident CTAs per SM from the shared-memory footprint (227 KB usable, 1 KB
-  // reserved per CTA); TMEM (32 columns each) and registers allow more
+  // reserved per CTA) and the TMEM columns each CTA allocates
   int per_sm = (int)((227u * 1024u) / (smem + 1024u));
+  constexpr int kAcc = kRows * COUT;        // TMEM columns a CTA allocates (power of two >= 32)
+  constexpr int kCols = kAcc <= 32 ? 32 : (kAcc <= 64 ? 64 : (kAcc <= 128 ? 128 : 256));
+  if (per_sm > 512 / kCols) per_sm = 512 / kCols;   // 512 TMEM columns per SM
   if (per_sm < 1) per_sm = 1;
   if (per_sm > 8) per_sm = 8;
   const uint32_t tiles = ((W + kTileM - 1) / kTileM) * ((H + kRows - 1) / kRows);

@@ -126,6 +126,10 @@ int make_render_args(const rt_scene* scene, const rt_camera* cam, float eye_sep,
   a.cam.tiles_x = (W + 7) / 8;
   a.cam.tiles_y = (H + 3) / 4;
   a.sc.nodes = scene->nodes;
+  a.sc.nodes4 = scene->nodes4;
+  a.sc.n4 = scene->n4;
+  a.sc.n_top = scene->n_top;
+  a.binary = scene->binary;
   a.sc.prims = scene->prims;
   a.sc.mats = scene->mats;
   a.sc.lights = scene->lights;
@@ -210,8 +214,9 @@ int rt_scene_create(const rt_sphere* spheres, uint32_t n_spheres, const rt_trian
   const size_t b_lights = align256((size_t)n_lights * sizeof(float4));
   const size_t b_keys = align256(n * sizeof(uint64_t));
   const size_t b_parent = align256((2 * n - 1) * sizeof(int32_t));
+  const size_t b_nodes4 = align256((n > 1 ? n - 1 : 1) * 7 * sizeof(float4));
   const size_t b_err = 256;
-  const size_t total = b_nodes + b_prims + b_mats + b_lights + b_keys + b_parent + b_err;
+  const size_t total = b_nodes + b_prims + b_mats + b_lights + b_keys + b_parent + b_nodes4 + b_err;
   cudaError_t e = cudaMalloc(&sc->block, total);
   if (e != cudaSuccess) { cudaGetLastError(); delete sc; return cuda_fail(e, "scene allocation"); }
   char* p = static_cast<char*>(sc->block);
@@ -221,6 +226,7 @@ int rt_scene_create(const rt_sphere* spheres, uint32_t n_spheres, const rt_trian
   sc->lights = reinterpret_cast<float4*>(p); p += b_lights;
   sc->keys = reinterpret_cast<uint64_t*>(p); p += b_keys;
   sc->parent = reinterpret_cast<int32_t*>(p); p += b_parent;
+  sc->nodes4 = reinterpret_cast<float4*>(p); p += b_nodes4;
   sc->err = reinterpret_cast<uint32_t*>(p);
   e = cudaMallocHost(&sc->h_err, sizeof(uint32_t));
   if (e != cudaSuccess) { cudaGetLastError(); cudaFree(sc->block); delete sc; return cuda_fail(e, "pinned allocation"); }
@@ -229,9 +235,12 @@ int rt_scene_create(const rt_sphere* spheres, uint32_t n_spheres, const rt_trian
   // temporary: raw input records + LBVH scratch
   const size_t b_sph = align256((size_t)n_spheres * sizeof(rt_sphere) + 16);
   const size_t b_tri = align256((size_t)n_tris * sizeof(rt_triangle) + 16);
-  const size_t b_tmp = rt::lbvh_tmp_bytes((uint32_t)n);
+  // 256-byte multiple: the two uint32 counts of the 4-wide build follow it
+  const size_t b_tmp = align256(rt::lbvh_tmp_bytes((uint32_t)n) > rt::bvh4_tmp_bytes((uint32_t)n)
+                                    ? rt::lbvh_tmp_bytes((uint32_t)n)
+                                    : rt::bvh4_tmp_bytes((uint32_t)n));
   void* tmp = nullptr;
-  e = cudaMalloc(&tmp, b_sph + b_tri + b_tmp);
+  e = cudaMalloc(&tmp, b_sph + b_tri + b_tmp + 256);
   if (e != cudaSuccess) { cudaGetLastError(); rt_scene_destroy(sc); return cuda_fail(e, "build scratch allocation"); }
   char* tp = static_cast<char*>(tmp);
   float4* d_sph = reinterpret_cast<float4*>(tp);
@@ -244,8 +253,19 @@ int rt_scene_create(const rt_sphere* spheres, uint32_t n_spheres, const rt_trian
   cudaMemsetAsync(sc->err, 0, sizeof(uint32_t), st);
   e = rt::build_lbvh(d_sph, d_tri, n_spheres, n_tris, sc->nodes, sc->prims, sc->keys, sc->parent,
                      d_lbvh, b_tmp, sc->err, st);
+  // the 4-wide tree derived from the binary one; its counts go to the spare
+  // 256 bytes after the scratch
+  uint32_t* d_counts = reinterpret_cast<uint32_t*>(tp + b_sph + b_tri + b_tmp);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_counts, 0, 2 * sizeof(uint32_t), st);
+  if (e == cudaSuccess)
+    e = rt::build_bvh4(sc->nodes, sc->parent, (uint32_t)n, rt::treelet_depth(), sc->nodes4, d_counts,
+                       d_lbvh, st);
+  uint32_t counts[2] = {0, 0};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(counts, d_counts, sizeof counts, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(sc->h_err, sc->err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  sc->n_top = counts[0];
+  sc->n4 = counts[1];
   cudaFree(tmp);
   if (e != cudaSuccess) { rt_scene_destroy(sc); return cuda_fail(e, "BVH build"); }
   if (*sc->h_err) {
@@ -403,6 +423,12 @@ int rt_debug_set_node(rt_scene* scene, uint32_t node, int32_t left, int32_t righ
   }
   e = cudaMemcpy(scene->nodes + 4 * (size_t)node, nd, sizeof nd, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return cuda_fail(e, "node upload");
+  return RT_OK;
+}
+
+int rt_scene_set_traversal(rt_scene* scene, int wide) {
+  if (!scene) return fail(RT_ERR_INVALID_ARG, "scene is NULL");
+  scene->binary = wide == 0;
   return RT_OK;
 }
 

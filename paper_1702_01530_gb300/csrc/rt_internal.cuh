@@ -34,15 +34,18 @@ enum : uint32_t {
 };
 
 constexpr int kStackSize = 64;   // radix-tree depth over unique 64-bit keys <= 64
+constexpr int32_t kEmptyChild = 0x7FFFFFFF;  // unused slot of a 4-wide node
 constexpr float kAmbient = 0.1f;
 constexpr float kBgR = 0.2f, kBgG = 0.3f, kBgB = 0.5f;
 
 struct DeviceScene {
   const float4* nodes;
+  const float4* nodes4;   // 4-wide nodes (7 float4 each), the top n_top first
   const float4* prims;
   const float4* mats;
   const float4* lights;
   uint32_t n_prims, n_spheres, n_mats, n_lights;
+  uint32_t n4, n_top;     // 4-wide nodes, of which the first n_top are staged in shared memory
 };
 
 // host-computed camera basis (double -> float)
@@ -136,6 +139,7 @@ struct RenderArgs {
   const uint32_t* plist_n_dev;  // its length in device memory (read by the kernel)
   bool resolve;            // write out_L/out_R from the sums (false: caller composes)
   int trace_stage;         // stage the tracing kernel is timed as (ST_TRACE or ST_RETRACE)
+  bool binary;             // traverse the binary tree instead of the 4-wide one
 };
 
 // entry points implemented in the .cu files
@@ -143,6 +147,9 @@ cudaError_t build_lbvh(const float4* d_sph_in, const float* d_tri_in, uint32_t n
                        float4* d_nodes, float4* d_prims, uint64_t* d_keys, int32_t* d_parent,
                        void* d_tmp, size_t tmp_bytes, uint32_t* d_err, cudaStream_t st);
 size_t lbvh_tmp_bytes(uint32_t n);
+size_t bvh4_tmp_bytes(uint32_t n);
+cudaError_t build_bvh4(const float4* nodes, const int32_t* parent, uint32_t n, int top_depth,
+                       float4* nodes4, uint32_t* counts_dev, void* tmp, cudaStream_t st);
 cudaError_t render(const RenderArgs& a, Workspace& ws, cudaStream_t st);
 // stage timing: start a profiled call (resets the event list) / mark the end of a stage
 void profile_begin(Workspace& ws, cudaStream_t st);
@@ -150,6 +157,7 @@ void profile_mark(Workspace& ws, int stage, cudaStream_t st);
 int num_sms();
 int render_grid();      // persistent blocks of the render kernel
 int render_threads();   // threads per block of the render kernel
+int treelet_depth();    // 4-wide levels numbered first for shared-memory staging
 
 // reprojection (reproj.cu)
 cudaError_t reproj_warp(const float* depth_L, const float* normal_L, const uint32_t* id_L,
@@ -191,6 +199,9 @@ struct rt_scene {
   uint32_t ns = 0, nt = 0, n = 0, nm = 0, nl = 0;
   void* block = nullptr;       // persistent device allocation
   float4* nodes = nullptr;
+  float4* nodes4 = nullptr;
+  uint32_t n4 = 0, n_top = 0;
+  bool binary = true;          // render with the binary tree (default) or the 4-wide one
   float4* prims = nullptr;
   float4* mats = nullptr;
   float4* lights = nullptr;

@@ -52,6 +52,17 @@ namespace {
 #ifndef RT_WHILE_WHILE
 #define RT_WHILE_WHILE 0
 #endif
+constexpr int kStack4 = 100;   // 3 pushes per 4-wide level, <= 33 levels
+// shared-memory treelet: 4-wide levels staged per block (RT_TREELET_DEPTH
+// levels, at most 1 + 4 + 16 + 64 = 85 nodes for depth 4)
+#ifndef RT_TREELET_DEPTH
+#define RT_TREELET_DEPTH 2
+#endif
+constexpr int kMaxTopBytes = 85 * 7 * 16;
+// 4-wide closest-hit traversal pushes the other hit children farthest first
+#ifndef RT_ORDERED_PUSH
+#define RT_ORDERED_PUSH 0
+#endif
 constexpr int kThreads = 128;
 constexpr float kRobust = 1.00000036f;   // 1 + 2*gamma_3 (Ize 2013): conservative slab exit
 
@@ -197,6 +208,116 @@ __device__ __forceinline__ bool traverse(const DeviceScene& sc, V3 o, V3 d, floa
 }
 
 
+
+// 4-wide traversal: one fetch of 7 float4 tests four child boxes; the
+// nearest hit child is visited next and the other hit children are pushed.
+// The first sc.n_top nodes are read from the shared-memory copy `top`.
+template <bool ANY>
+__device__ __forceinline__ bool traverse4(const DeviceScene& sc, const float4* top, V3 o, V3 d,
+                                          float tmax, float& t_best, uint32_t& id_best,
+                                          uint32_t& k_best, uint32_t* err) {
+  const V3 idir = v3(safe_rcp(d.x), safe_rcp(d.y), safe_rcp(d.z));
+  const V3 ood = v3(o.x * idir.x, o.y * idir.y, o.z * idir.z);
+  int32_t stack[kStack4];
+  int sp = 0;
+  const uint32_t n = sc.n_prims;
+  int32_t node = n == 1 ? ~0 : 0;
+  const uint32_t it_max = 2u * n + 64u;
+  float tcur = ANY ? tmax : t_best;
+  bool any = false;
+  for (uint32_t it = 0;; ++it) {
+    if (it >= it_max) { atomicOr(err, ERR_ITER); break; }
+    if (node >= 0) {
+      if ((uint32_t)node >= sc.n4) { atomicOr(err, ERR_INDEX); break; }
+      float4 lx, hx, ly, hy, lz, hz, cc;
+      if ((uint32_t)node < sc.n_top) {             // shared-memory treelet
+        const float4* np = top + 7 * node;
+        lx = np[0]; hx = np[1]; ly = np[2]; hy = np[3]; lz = np[4]; hz = np[5]; cc = np[6];
+      } else {                                     // read-only global path
+        const float4* np = sc.nodes4 + 7 * (size_t)node;
+        lx = __ldg(np); hx = __ldg(np + 1); ly = __ldg(np + 2); hy = __ldg(np + 3);
+        lz = __ldg(np + 4); hz = __ldg(np + 5); cc = __ldg(np + 6);
+      }
+      float tin[4];
+      bool hit[4];
+#define RT_SLAB(c, LX, HX, LY, HY, LZ, HZ)                                                  \
+      {                                                                                     \
+        const float ax = fmaf(LX, idir.x, -ood.x), bx = fmaf(HX, idir.x, -ood.x);           \
+        const float ay = fmaf(LY, idir.y, -ood.y), by = fmaf(HY, idir.y, -ood.y);           \
+        const float az = fmaf(LZ, idir.z, -ood.z), bz = fmaf(HZ, idir.z, -ood.z);           \
+        tin[c] = fmax3(fminf(ax, bx), fminf(ay, by), fmaxf(fminf(az, bz), 0.f));             \
+        const float tout = fmin3(fmaxf(ax, bx), fmaxf(ay, by), fminf(fmaxf(az, bz), tcur));  \
+        hit[c] = tin[c] <= tout * kRobust;                                                  \
+      }
+      RT_SLAB(0, lx.x, hx.x, ly.x, hy.x, lz.x, hz.x)
+      RT_SLAB(1, lx.y, hx.y, ly.y, hy.y, lz.y, hz.y)
+      RT_SLAB(2, lx.z, hx.z, ly.z, hy.z, lz.z, hz.z)
+      RT_SLAB(3, lx.w, hx.w, ly.w, hy.w, lz.w, hz.w)
+#undef RT_SLAB
+      const int32_t ch[4] = {__float_as_int(cc.x), __float_as_int(cc.y), __float_as_int(cc.z),
+                             __float_as_int(cc.w)};
+#pragma unroll
+      for (int c = 0; c < 4; ++c) hit[c] = hit[c] && ch[c] != kEmptyChild;  // unused slots
+      int bi = -1;
+      float best = INFINITY;
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+        if (hit[c] && (ANY ? bi < 0 : tin[c] < best)) { best = tin[c]; bi = c; }
+      if (bi >= 0) {
+        // the other hit children, farthest pushed first (closest-hit rays)
+        float t4[4];
+        int32_t c4[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          t4[c] = (hit[c] && c != bi) ? tin[c] : -INFINITY;
+          c4[c] = ch[c];
+        }
+        if (!ANY && RT_ORDERED_PUSH) {
+#define RT_CAS(i, j)                                                              \
+          if (t4[i] < t4[j]) {                                                    \
+            const float tt = t4[i]; t4[i] = t4[j]; t4[j] = tt;                    \
+            const int32_t cx = c4[i]; c4[i] = c4[j]; c4[j] = cx;                  \
+          }
+          RT_CAS(0, 1) RT_CAS(2, 3) RT_CAS(0, 2) RT_CAS(1, 3) RT_CAS(1, 2)
+#undef RT_CAS
+        }
+        bool overflow = false;
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+          if (t4[c] > -INFINITY) {
+            if (sp < kStack4) stack[sp++] = c4[c];
+            else overflow = true;
+          }
+        if (overflow) { atomicOr(err, ERR_STACK); break; }
+        node = ch[bi];
+        continue;
+      }
+    } else {
+      const uint32_t k = (uint32_t)~node;
+      if (k >= n) { atomicOr(err, ERR_INDEX); break; }
+      const float4* pp = sc.prims + 3 * (size_t)k;
+      const float4 p0 = __ldg(pp), p1 = __ldg(pp + 1);
+      const uint32_t id = __float_as_uint(p0.w);
+      float t;
+      bool h;
+      if (id < sc.n_spheres) h = hit_sphere(p0, p1.x, o, d, t);
+      else h = hit_tri(p0, p1, __ldg(pp + 2), o, d, t);
+      if (ANY) {
+        if (h && t < tmax) { any = true; break; }
+      } else if (h && (t < tcur || (t == tcur && id < id_best))) {
+        tcur = t;
+        id_best = id;
+        k_best = k;
+        any = true;
+      }
+    }
+    if (sp == 0) break;
+    node = stack[--sp];
+  }
+  if (!ANY) t_best = tcur;
+  return any;
+}
+
 #if RT_WHILE_WHILE
 // Same traversal with postponed leaves. Internal nodes are visited until
 // every active lane of the warp holds one pending leaf (or has finished);
@@ -290,10 +411,14 @@ __device__ __forceinline__ bool traverse_ww(const DeviceScene& sc, V3 o, V3 d, f
 }
 #endif
 
-template <bool ANY, bool COUNT>
-__device__ __forceinline__ bool trace_ray(const DeviceScene& sc, V3 o, V3 d, float tmax,
-                                          float& t_best, uint32_t& id_best, uint32_t& k_best,
-                                          WorkCount& wc, uint32_t* err) {
+// The instrumented (COUNT) and the requested binary traversal walk the
+// binary radix tree, whose node visits define the algorithmic work; the
+// production path walks the 4-wide tree (the same leaves, the same hits).
+template <bool ANY, bool COUNT, bool WIDE>
+__device__ __forceinline__ bool trace_ray(const DeviceScene& sc, const float4* top, V3 o, V3 d,
+                                          float tmax, float& t_best, uint32_t& id_best,
+                                          uint32_t& k_best, WorkCount& wc, uint32_t* err) {
+  if (WIDE && !COUNT) return traverse4<ANY>(sc, top, o, d, tmax, t_best, id_best, k_best, err);
 #if RT_WHILE_WHILE
   return traverse_ww<ANY, COUNT>(sc, o, d, tmax, t_best, id_best, k_best, wc, err);
 #else
@@ -338,7 +463,7 @@ enum Mode : int { M_SHADOW = 0, M_PRIMARY = 1, M_MIRROR = 2 };
 
 // Shadow queue entry: (origin | pixel) (direction | t_max) (contribution | 0)
 // Mirror queue entry: (origin | pixel) (direction | depth) (weight | 0)
-template <bool COUNT>
+template <bool COUNT, bool WIDE>
 __global__ void
 #if RT_MIN_BLOCKS > 0
 __launch_bounds__(kThreads, RT_MIN_BLOCKS)
@@ -347,6 +472,12 @@ __launch_bounds__(kThreads)
 #endif
 k_render(KParams kp) {
   const RenderArgs& a = kp.a;
+  // the top of the 4-wide tree, staged in shared memory once per block
+  extern __shared__ float4 top[];
+  if (WIDE && !COUNT) {
+    for (uint32_t i = threadIdx.x; i < 7u * a.sc.n_top; i += blockDim.x) top[i] = a.sc.nodes4[i];
+    __syncthreads();
+  }
   const CameraParams& cam = a.cam;
   const uint32_t P = cam.W * cam.H;
   const uint32_t lane = lane_id();
@@ -387,7 +518,7 @@ k_render(KParams kp) {
         const float4 s0 = e[0], s1 = e[1];
         float tb = 0.f;
         uint32_t id = 0, k = 0;
-        const bool blocked = trace_ray<true, COUNT>(a.sc, xyz(s0), xyz(s1), s1.w, tb, id, k, wc_s, a.err);
+        const bool blocked = trace_ray<true, COUNT, WIDE>(a.sc, top, xyz(s0), xyz(s1), s1.w, tb, id, k, wc_s, a.err);
         if (!blocked) {
           const float4 s2 = e[2];
           accumulate(kp.accum, __float_as_uint(s0.w), s2.x, s2.y, s2.z, a.color_scale);
@@ -446,7 +577,7 @@ k_render(KParams kp) {
     uint32_t id = RT_MISS_ID, k = 0;
     bool hit = false;
     if (active)
-      hit = trace_ray<false, COUNT>(a.sc, o, d, INFINITY, t, id, k,
+      hit = trace_ray<false, COUNT, WIDE>(a.sc, top, o, d, INFINITY, t, id, k,
                                    mode == M_PRIMARY ? wc_p : wc_r, a.err);
     __syncwarp();
 
@@ -560,18 +691,19 @@ __global__ void k_counts(const uint32_t* counters, uint64_t primary, uint64_t* o
   out[2] = counters[C_REFL];
 }
 
-template <bool COUNT>
+template <bool COUNT, bool WIDE>
 int blocks_per_sm() {
   static int cached = 0;
   if (!cached) {
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render<COUNT>, kThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render<COUNT, WIDE>, kThreads,
+                                                  kMaxTopBytes);
     cached = per_sm > 0 ? per_sm : 1;
   }
   return cached;
 }
 
-template <bool COUNT>
+template <bool COUNT, bool WIDE>
 cudaError_t render_impl(const RenderArgs& a, Workspace& ws, cudaStream_t st) {
   const uint64_t P = (uint64_t)a.cam.W * a.cam.H;
   KParams kp;
@@ -593,7 +725,8 @@ cudaError_t render_impl(const RenderArgs& a, Workspace& ws, cudaStream_t st) {
   else cudaMemsetAsync(ws.accum + 3 * P, 0, P * 3 * sizeof(uint32_t), st);
   if (a.work) cudaMemsetAsync(a.work, 0, 9 * sizeof(uint64_t), st);
   profile_mark(ws, ST_CLEAR, st);
-  k_render<COUNT><<<grid, kThreads, 0, st>>>(kp);
+  const size_t top_bytes = (WIDE && !COUNT) ? 7 * sizeof(float4) * a.sc.n_top : 0;
+  k_render<COUNT, WIDE><<<grid, kThreads, top_bytes, st>>>(kp);
   profile_mark(ws, a.trace_stage, st);
   const uint32_t n3 = (uint32_t)(P * 3);
   if (a.resolve) {
@@ -619,12 +752,16 @@ int num_sms() {
 }
 
 int render_grid() {
-  // the instrumented variant may fit fewer blocks; size for the larger grid
-  return num_sms() * (blocks_per_sm<false>() > blocks_per_sm<true>() ? blocks_per_sm<false>()
-                                                                      : blocks_per_sm<true>());
+  // the variants may fit different numbers of blocks; size for the largest grid
+  int b = blocks_per_sm<false, true>();
+  if (blocks_per_sm<false, false>() > b) b = blocks_per_sm<false, false>();
+  if (blocks_per_sm<true, false>() > b) b = blocks_per_sm<true, false>();
+  return num_sms() * b;
 }
 
 int render_threads() { return kThreads; }
+
+int treelet_depth() { return RT_TREELET_DEPTH; }
 
 void profile_begin(Workspace& ws, cudaStream_t st) {
   ws.n_ev = 0;
@@ -640,7 +777,10 @@ void profile_mark(Workspace& ws, int stage, cudaStream_t st) {
 }
 
 cudaError_t render(const RenderArgs& a, Workspace& ws, cudaStream_t st) {
-  return a.work ? render_impl<true>(a, ws, st) : render_impl<false>(a, ws, st);
+  if (a.sc.n_top * 7 * sizeof(float4) > (size_t)kMaxTopBytes) return cudaErrorInvalidValue;
+  if (a.work) return render_impl<true, false>(a, ws, st);
+  return a.binary || a.sc.n4 == 0 ? render_impl<false, false>(a, ws, st)
+                                   : render_impl<false, true>(a, ws, st);
 }
 
 }  // namespace rt

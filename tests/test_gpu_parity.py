@@ -165,6 +165,24 @@ def test_host_render_matches_device_render():
         g.close()
 
 
+@pytest.mark.parametrize("make", [lambda: sg.config_blobs(3, n_blobs=30, n_spheres=150, W=128, H=96),
+                                  lambda: sg.config_small(4, W=97, H=61),
+                                  lambda: scene(spheres=[((0, 0, -5), 1.0, 0)], W=16, H=9),
+                                  lambda: sg.config_polyhedra(6, n_lights=2, ground=True, W=80, H=60)])
+def test_wide_and_binary_traversal_give_identical_images(make):
+    s = make()
+    g = capi.GpuScene(s)
+    try:
+        binary = g.render(aux=True)
+        capi.rt_scene_set_traversal(g.handle, True)
+        wide = g.render(aux=True)
+        capi.rt_sync_status(g.handle)
+        for k in ("rgb", "hit_id", "depth", "rays"):
+            assert np.array_equal(wide[k].cpu().numpy(), binary[k].cpu().numpy()), k
+    finally:
+        g.close()
+
+
 def test_repeated_renders_are_identical():
     s = sg.config_blobs(4, n_blobs=10, n_spheres=40, W=64, H=48)
     g = capi.GpuScene(s)
@@ -215,7 +233,7 @@ def test_bvh_cycle_stops_at_iteration_bound():
         # node 0 becomes its own left child; its right child gets an empty
         # box: every ray entering the root loops until the iteration bound
         capi.rt_debug_set_node(g.handle, 0, 0, int(bvh["right"][0]), empty_right=True)
-        g.render()
+        g.render()                                       # the hook edits the binary tree
         with pytest.raises(capi.RtError) as e:
             capi.rt_sync_status(g.handle)
         assert e.value.code == capi.RT_ERR_TIMEOUT
