@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--W", type=int, default=1920)
     ap.add_argument("--H", type=int, default=1080)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-reproj", action="store_true",
+                    help="skip the learned-reprojection measurement")
     ap.add_argument("--cpu-sample", type=int, default=0,
                     help="pixels of the workload the CPU oracle traces for cpu_baseline "
                          "(0 = every pixel of one stereo pair)")
@@ -172,6 +174,37 @@ def cpu_baseline(scene, n_pixels: int, seed: int = 7):
     return {"seconds": dt, "rays": rays, "pixels": n_pixels, "cores": cores,
             "mrays_per_s": rays / dt / 1e6,
             "pairs_per_s_est": (n_pixels / (2 * scene.W * scene.H)) / dt}
+
+
+# ----------------------------------------------------- learned reprojection
+def reproj_leg(blob_scene):
+    """Full two-eye trace vs learned right-eye reprojection at 1920x1080 per
+    eye: three held-out config-1-style scenes (the network's workload) and the
+    blob scene; median of 20 CUDA-event runs each, PSNR of the right eye
+    against its full trace."""
+    from paper_1702_01530_gb300 import capi, scenegen as sg, train_reproj as tr
+    params, thr = tr.load_weights()
+    net = capi.Net(params)
+    try:
+        out = {"weights": "paper_1702_01530_gb300/weights/reproj_net.bin", "threshold": thr}
+        for name, seeds, make in (
+                ("small_scenes_1080p", range(2000, 2003),
+                 lambda seed: sg.config_small(seed, W=1920, H=1080)),
+                ("blob_scene_1080p", (blob_scene.name,), lambda _: blob_scene)):
+            rows = tr.evaluate(net.handle, seeds, 1920, 1080, thresholds=(thr,), make_scene=make)
+            base = tr.evaluate(None, seeds, 1920, 1080, make_scene=make)
+            a, b = tr.summarise(rows, thr), tr.summarise(base, None)
+            out[name] = {
+                "full_pair_ms": round(a["ms_full"], 4),
+                "learned": {"pair_ms": round(a["ms_reproj"], 4), "speedup": round(a["speedup"], 3),
+                            "right_psnr_db_min": round(a["psnr_min"], 2),
+                            "retraced_fraction": round(a["retraced_mean"], 5)},
+                "holes_only": {"pair_ms": round(b["ms_reproj"], 4), "speedup": round(b["speedup"], 3),
+                               "right_psnr_db_min": round(b["psnr_min"], 2),
+                               "retraced_fraction": round(b["retraced_mean"], 5)}}
+        return out
+    finally:
+        net.close()
 
 
 # ---------------------------------------------------------------- our arm
@@ -335,6 +368,8 @@ def run_ours(args, rank, world, local):
     if clocks and clocks.get("sm_mhz"):
         line["roofline"]["frac_at_sampled_clock"] = round(
             achieved / alu_peak_tops(n_sms, clocks["sm_mhz"]), 4)
+    if rank == 0 and not args.no_reproj:
+        line["reproj"] = reproj_leg(s)
     if rank == 0 and not args.no_cpu_baseline:
         cb = cpu_baseline(s, args.cpu_sample)
         line["cpu_baseline"] = {"value": round(cb["mrays_per_s"], 4), "unit": UNIT,

@@ -360,6 +360,24 @@ int rt_render_stereo_reproj(const rt_scene* scene, const rt_camera* cam, float e
                             rt_net* net, float threshold, float* d_out_L, float* d_out_R,
                             uint32_t* d_n_retraced, void* cuda_stream);
 
+/*
+ * rt_stereo_composite -- convert a stereo pair into a display frame.
+ * Paper Sec. 3: GPU post-processing turns the stereo pair into the frame
+ * format of the display device, e.g. an anaglyph.
+ *   d_L, d_R: DEVICE, H*W*3 float32 each (as written by rt_render_stereo).
+ *   mode RT_COMPOSITE_ANAGLYPH_COLOR: out = (L.r, R.g, R.b) per pixel;
+ *   mode RT_COMPOSITE_ANAGLYPH_GRAY:  out = (y(L), y(R), y(R)) with
+ *        y = fma(0.114, b, fma(0.587, g, 0.299 r)) in FP32;
+ *   mode RT_COMPOSITE_SIDE_BY_SIDE:   out = H rows of 2W pixels, left eye first.
+ *   d_out: DEVICE, H*W*3 floats (H*2W*3 side by side), caller-owned.
+ * Asynchronous on cuda_stream. Errors: RT_ERR_INVALID_ARG, RT_ERR_CUDA.
+ */
+#define RT_COMPOSITE_ANAGLYPH_COLOR 0
+#define RT_COMPOSITE_ANAGLYPH_GRAY 1
+#define RT_COMPOSITE_SIDE_BY_SIDE 2
+int rt_stereo_composite(const float* d_L, const float* d_R, uint32_t W, uint32_t H, int mode,
+                        float* d_out, void* cuda_stream);
+
 /* Number of primitives of the scene (0 for NULL). */
 uint32_t rt_scene_num_prims(const rt_scene* scene);
 

@@ -22,14 +22,22 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
-_LIB_PATH = os.path.join(_HERE, "_build", "liboracle.so")
+# ORACLE_LIB points the wrapper at another build of oracle.c (the mutation
+# test loads deliberately broken copies this way)
+_LIB_PATH = os.environ.get("ORACLE_LIB") or os.path.join(_HERE, "_build", "liboracle.so")
 _lib = None
 
 MISS_ID = 0xFFFFFFFF
 
 
-def build(force: bool = False) -> str:
-    """Compile oracle.c with gcc (FP64, no FMA contraction)."""
+def build(force: bool = False, src: str = _SRC, out: str | None = None) -> str:
+    """Compile oracle.c (or ``src``) with gcc: FP64, no FMA contraction."""
+    if out is not None:
+        subprocess.run(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-shared", "-fPIC",
+                        "-pthread", src, "-o", out, "-lm"], check=True)
+        return out
+    if os.environ.get("ORACLE_LIB"):
+        return _LIB_PATH
     os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
         tmp = _LIB_PATH + f".tmp{os.getpid()}"

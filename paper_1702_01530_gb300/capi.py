@@ -69,6 +69,7 @@ _SIGS = {
                                                _vp, _vp, _f32, _vp]),
     "rt_render_stereo_reproj": (ctypes.c_int, [_vp, _vp, _f32, _f32, _u32, _u32, _u32, _vp, _f32,
                                                _vp, _vp, _vp, _vp]),
+    "rt_stereo_composite": (ctypes.c_int, [_vp, _vp, _u32, _u32, ctypes.c_int, _vp, _vp]),
     "rt_last_error": (ctypes.c_char_p, []),
     "rt_version": (ctypes.c_char_p, []),
 }
@@ -245,6 +246,13 @@ def rt_build_lbvh_noalloc(d_spheres, n_spheres, d_tris, n_tris, d_nodes, d_prims
     _check(lib().rt_build_lbvh_noalloc(_dptr(d_spheres), n_spheres, _dptr(d_tris), n_tris,
                                        _dptr(d_nodes), _dptr(d_prims), _dptr(d_keys),
                                        _dptr(d_parent), _stream(stream)))
+
+
+COMPOSITE_ANAGLYPH_COLOR, COMPOSITE_ANAGLYPH_GRAY, COMPOSITE_SIDE_BY_SIDE = 0, 1, 2
+
+
+def rt_stereo_composite(L, R, W, H, mode, out, stream=None):
+    _check(lib().rt_stereo_composite(_dptr(L), _dptr(R), W, H, mode, _dptr(out), _stream(stream)))
 
 
 RT_NET_PARAMS = 21409

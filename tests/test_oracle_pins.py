@@ -122,6 +122,20 @@ def test_mirror_symmetric_scene_gives_mirrored_eyes():
     assert not np.allclose(r["rgb"][0], r["rgb"][1])   # the eyes do differ
 
 
+def test_image_orientation_row0_top_and_right_is_plus_x():
+    # camera at the origin looking down -z with +y up: a sphere above the
+    # view axis lands in the top rows, one at +x in the right half
+    for centre, where in (((0, 2.5, -10), "top"), ((3.5, 0, -10), "right")):
+        s = scene(spheres=[(centre, 1.0, 0)], W=40, H=30)
+        hit = oracle.render(s)["hit_id"][0] != MISS
+        rows, cols = np.nonzero(hit)
+        assert len(rows) > 10
+        if where == "top":
+            assert rows.max() < 15 and abs(cols.mean() - 19.5) < 1
+        else:
+            assert cols.min() > 20 and abs(rows.mean() - 14.5) < 1
+
+
 # ------------------------------------------------------------ T4 disparity
 def _disparity_scene(W=200, H=480, s=1.0, zc=8.0, z=4.0, tiles=True):
     vfov = math.degrees(2 * math.atan(0.5))          # tan(vfov/2) = 1/2: f_px = H
@@ -206,6 +220,13 @@ def test_lbvh_keys_quantisation():
     # x in [0,3]: q = floor(x/3*1024) = 0, 341, 682, 1024 -> 1023; y, z extent 0
     expect = sorted((_interleave_by_strings(q, 0, 0) << 32) | i
                     for i, q in enumerate([0, 341, 682, 1023]))
+    assert b["keys"].tolist() == expect
+
+
+def test_lbvh_quantisation_uses_1024_cells():
+    # x = 0, 0.5, 1 on [0, 1]: floor(0.5 * 1024) = 512 (a 1023-cell grid would give 511)
+    b = oracle.OracleScene(_spheres_at([0, 0.5, 1])).lbvh()
+    expect = sorted((_interleave_by_strings(q, 0, 0) << 32) | i for i, q in enumerate([0, 512, 1023]))
     assert b["keys"].tolist() == expect
 
 

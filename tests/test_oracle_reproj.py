@@ -172,3 +172,16 @@ def test_generators_for_reprojection():
     assert torch.equal(t.to(torch.bfloat16).to(torch.float32), t)
     p = sg.net_params_he(0)
     assert p.size == sg.NET_PARAMS == 21409 and p[2592:2624].max() == 0
+
+
+def test_composite_oracle_definitions():
+    from oracle import post
+    L = np.zeros((2, 3, 3), np.float32)
+    R = np.ones((2, 3, 3), np.float32)
+    L[..., 0] = 0.25
+    c = post.composite(L, R, 0)
+    assert (c[..., 0] == 0.25).all() and (c[..., 1:] == 1).all()
+    g = post.composite(L, R, 1)
+    assert np.allclose(g[..., 0], 0.299 * 0.25) and np.allclose(g[..., 1:], 1.0, atol=1e-6)
+    sbs = post.composite(L, R, 2)
+    assert sbs.shape == (2, 6, 3) and (sbs[:, :3] == L).all() and (sbs[:, 3:] == R).all()
