@@ -153,10 +153,12 @@ int rt_render_stereo_aux(const rt_scene* scene, const rt_camera* cam,
 /*
  * rt_render_stereo_host -- end-to-end render into HOST buffers.
  * Paper: Sec. 4-5 (the synthesis time splits into GPU computation and the
- * copies between CPU and GPU memory). Renders like rt_render_stereo into
- * scene-owned device buffers, copies both images to host_L/host_R (H*W*3
- * float32 each, same layout; pinned memory gives full copy speed) and
- * synchronises the stream before returning.
+ * copies between CPU and GPU memory). Both images land in host_L/host_R
+ * (H*W*3 float32 each, same layout) and the stream is synchronised before
+ * returning. Pinned host buffers that the GPU can address (cudaHostAlloc /
+ * pinned torch tensors) are written directly by the final kernel over the
+ * CPU-GPU link; other host memory is filled by a copy from scene-owned
+ * device frames.
  */
 int rt_render_stereo_host(const rt_scene* scene, const rt_camera* cam,
                           float eye_sep, float convergence,

@@ -315,12 +315,35 @@ int rt_render_stereo(const rt_scene* scene, const rt_camera* cam, float eye_sep,
                               nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, cuda_stream);
 }
 
+namespace {
+// device address of a host buffer the GPU can write directly (pinned and
+// mapped; on GB300 the write goes over the coherent CPU-GPU link), or null
+float* device_view(float* host) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, host) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+  if (at.type != cudaMemoryTypeHost || !at.devicePointer) return nullptr;
+  return static_cast<float*>(at.devicePointer);
+}
+}  // namespace
+
 int rt_render_stereo_host(const rt_scene* scene, const rt_camera* cam, float eye_sep,
                           float convergence, uint32_t W, uint32_t H, uint32_t max_depth,
                           float* host_L, float* host_R, void* cuda_stream) {
   if (!host_L || !host_R) return fail(RT_ERR_INVALID_ARG, "host output buffer is NULL");
   if (!scene) return fail(RT_ERR_INVALID_ARG, "scene is NULL");
   rt_scene* sc = const_cast<rt_scene*>(scene);
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  // pinned, device-mapped host buffers: the resolve kernel writes them directly
+  float* vL = device_view(host_L);
+  float* vR = vL ? device_view(host_R) : nullptr;
+  if (vL && vR) {
+    int rc = rt_render_stereo(scene, cam, eye_sep, convergence, W, H, max_depth, vL, vR, cuda_stream);
+    if (rc) return rc;
+    const cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "render to host memory");
+    return RT_OK;
+  }
+  // otherwise render to scene-owned device frames and copy
   const size_t bytes = 2ull * W * H * 3 * sizeof(float);
   if (2ull * W * H <= (1ull << 31) && sc->ws.frame_bytes < bytes) {
     if (sc->ws.frame) cudaFree(sc->ws.frame);
@@ -334,7 +357,6 @@ int rt_render_stereo_host(const rt_scene* scene, const rt_camera* cam, float eye
   float* dR = dL + (size_t)W * H * 3;
   int rc = rt_render_stereo(scene, cam, eye_sep, convergence, W, H, max_depth, dL, dR, cuda_stream);
   if (rc) return rc;
-  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   cudaError_t e = cudaMemcpyAsync(host_L, dL, bytes / 2, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(host_R, dR, bytes / 2, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);

@@ -161,6 +161,12 @@ def test_host_render_matches_device_render():
         capi.rt_render_stereo_host(g.handle, s.camera, s.eye_sep, s.convergence, 80, 60,
                                    s.max_depth, hl, hr)
         assert np.array_equal(dev[0], hl.numpy()) and np.array_equal(dev[1], hr.numpy())
+        # pageable numpy buffers take the copy path
+        pl = np.zeros((60, 80, 3), np.float32)
+        pr = np.zeros((60, 80, 3), np.float32)
+        capi.rt_render_stereo_host(g.handle, s.camera, s.eye_sep, s.convergence, 80, 60,
+                                   s.max_depth, pl, pr)
+        assert np.array_equal(dev[0], pl) and np.array_equal(dev[1], pr)
     finally:
         g.close()
 
