@@ -61,6 +61,14 @@ def parse():
                     help="profiling mode: build the scene, render twice, exit")
     ap.add_argument("--ncu-net", action="store_true",
                     help="profiling mode: run the retrace network on 1080p features twice, exit")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="skip the batched-requests measurement")
+    ap.add_argument("--batch-only", action="store_true",
+                    help="print only the batched-requests measurement as one JSON object")
+    ap.add_argument("--study", action="store_true",
+                    help="print one JSON object with the stage split of the small and blob "
+                         "scenes, the polyhedra complexity sweep, the L2 / MUFU probes and the "
+                         "oracle's single-core rate, then exit")
     return ap.parse_args()
 
 
@@ -205,6 +213,66 @@ def reproj_leg(blob_scene):
         return out
     finally:
         net.close()
+
+
+# --------------------------------------------------------- batched requests
+def batch_leg(stream, reps=5, warm=2):
+    """64 stereo requests of uneven resolutions (640x360 .. 3840x2160 per eye)
+    and depths (2-6) over 16 blob scenes of 1.3k-2.0M triangles, in one
+    persistent launch replayed from a CUDA graph, launch shape chosen by the
+    library's autotuner; against the same requests rendered one
+    ``rt_render_stereo`` after another on the same stream."""
+    import torch
+
+    from paper_1702_01530_gb300 import capi, scenegen as sg
+    scenes, reqs = sg.config_batch()
+    t0 = time.perf_counter()
+    gs = [capi.GpuScene(s) for s in scenes]
+    build_s = time.perf_counter() - t0
+    outs = [torch.empty((2, H, W, 3), dtype=torch.float32, device="cuda") for _, W, H, _ in reqs]
+    items = [(gs[si].handle, scenes[si].camera, scenes[si].eye_sep, scenes[si].convergence, W, H, D,
+              o[0], o[1]) for (si, W, H, D), o in zip(reqs, outs)]
+    b = capi.rt_batch_create(capi.make_requests(items))
+    try:
+        t0 = time.perf_counter()
+        cfg, tuned_ms = capi.rt_batch_autotune(b, reps=2, stream=stream)
+        tune_s = time.perf_counter() - t0
+        launch = lambda: capi.rt_batch_launch(b, stream)   # noqa: E731
+        ms = _event_ms(launch, stream, reps=reps, warm=warm)
+        rays, lat, c = capi.rt_batch_stats(b, len(reqs))
+        keep = {i: outs[i].clone() for i in (0, 1, len(reqs) - 1)}
+
+        def sequential():
+            for (si, W, H, D), o in zip(reqs, outs):
+                s = scenes[si]
+                capi.rt_render_stereo(gs[si].handle, s.camera, s.eye_sep, s.convergence, W, H, D,
+                                      o[0], o[1], stream)
+        seq_ms = _event_ms(sequential, stream, reps=3, warm=1)
+        for g in gs:
+            capi.rt_sync_status(g.handle)
+        same = all(torch.equal(keep[i], outs[i]) for i in keep)
+    finally:
+        capi.rt_batch_destroy(b)
+        for g in gs:
+            g.close()
+    total_rays = int(rays.sum())
+    lat = np.asarray(lat, np.float64)
+    return {"workload": "64 requests, 16 blob scenes of 1280-1999360 triangles, "
+                        "640x360..3840x2160 per eye, depth 2-6 (scenegen.config_batch seed 3)",
+            "stereo_pixels": int(sum(2 * W * H for _, W, H, _ in reqs)),
+            "scene_build_s": round(build_s, 2),
+            "autotune": {"config": {k: int(cfg[k][0]) for k in cfg.dtype.names},
+                         "best_ms": round(tuned_ms, 3), "seconds": round(tune_s, 1)},
+            "ms_per_batch": round(ms, 3), "rays": [int(x) for x in rays],
+            "mrays_per_s": round(total_rays / (ms * 1e-3) / 1e6, 1),
+            "stereo_pairs_per_s": round(len(reqs) / (ms * 1e-3), 1),
+            "request_latency_ms": {"min": round(float(lat.min()), 3),
+                                   "p50": round(float(np.median(lat)), 3),
+                                   "p90": round(float(np.percentile(lat, 90)), 3),
+                                   "max": round(float(lat.max()), 3)},
+            "sequential_ms": round(seq_ms, 3),
+            "speedup_vs_sequential": round(seq_ms / ms, 3),
+            "sequential_images_identical": bool(same)}
 
 
 # ---------------------------------------------------------------- our arm
@@ -370,6 +438,8 @@ def run_ours(args, rank, world, local):
             achieved / alu_peak_tops(n_sms, clocks["sm_mhz"]), 4)
     if rank == 0 and not args.no_reproj:
         line["reproj"] = reproj_leg(s)
+    if rank == 0 and not args.no_batch:
+        line["batch"] = batch_leg(stream)
     if rank == 0 and not args.no_cpu_baseline:
         cb = cpu_baseline(s, args.cpu_sample)
         line["cpu_baseline"] = {"value": round(cb["mrays_per_s"], 4), "unit": UNIT,
@@ -449,6 +519,178 @@ def run_ncu_net(args):
     net.close()
 
 
+# ------------------------------------------------------------------ study
+def _event_ms(fn, stream, reps=20, warm=3, flush=None):
+    """Median CUDA-event time of fn() on ``stream``."""
+    import torch
+    for _ in range(warm):
+        fn()
+    ts = []
+    for _ in range(reps):
+        if flush is not None:
+            flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return float(np.median(ts))
+
+
+def _counts(g):
+    from paper_1702_01530_gb300 import capi
+    aux = g.render(count_work=True)
+    capi.rt_sync_status(g.handle)
+    return (aux["rays"].cpu().numpy().astype(np.int64),
+            aux["work"].cpu().numpy().reshape(3, 3).astype(np.int64),
+            int((aux["hit_id"] != -1).sum().item()))
+
+
+def stage_split(s, stream, flush):
+    """Scene upload + BVH build, trace stages and the read-back of both
+    images: the analogue of the paper's computation / transfer split
+    (Figure 7)."""
+    import torch
+    from paper_1702_01530_gb300 import capi
+    builds = []
+    for _ in range(5):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g = capi.GpuScene(s)
+        torch.cuda.synchronize()
+        builds.append((time.perf_counter() - t0) * 1e3)
+        g.close()
+    g = capi.GpuScene(s)
+    img = torch.empty((2, s.H, s.W, 3), dtype=torch.float32, device="cuda")
+
+    def render():
+        capi.rt_render_stereo(g.handle, s.camera, s.eye_sep, s.convergence, s.W, s.H,
+                              s.max_depth, img[0], img[1], stream)
+    render()
+    capi.rt_profile_enable(g.handle, True)
+    stages = {k: [] for k in capi.STAGES}
+    for _ in range(20):
+        flush.fill_(1.0)
+        render()
+        for k, v in capi.rt_profile_read(g.handle).items():
+            stages[k].append(v)
+    capi.rt_profile_enable(g.handle, False)
+    host = torch.empty(img.shape, dtype=torch.float32).pin_memory()
+    d2h = _event_ms(lambda: host.copy_(img, non_blocking=True), stream)
+    capi.rt_sync_status(g.handle)
+    g.close()
+    st = {k: round(float(np.median(v)), 4) for k, v in stages.items() if np.median(v) > 0}
+    compute = sum(st.values())
+    return {"W": s.W, "H": s.H, "prims": len(s.spheres) + len(s.triangles),
+            "upload_and_bvh_build_ms": round(float(np.median(builds)), 3),
+            "render_stage_ms": st, "d2h_ms": round(d2h, 4),
+            "d2h_gbs": round(img.numel() * 4 / (d2h * 1e-3) / 1e9, 1),
+            "compute_share_of_frame": round(compute / (compute + d2h), 3)}
+
+
+def complexity_sweep(stream, flush, objects=(1, 2, 3, 5, 6), lights=(1, 2, 4, 8)):
+    """The Figure 3-6 study: the polyhedra scene with 1-6 objects and 1-8
+    lights at 1920x1080 per eye, reflection depth 3."""
+    import torch
+    from paper_1702_01530_gb300 import capi, scenegen as sg
+    rows = []
+    img = torch.empty((2, 1080, 1920, 3), dtype=torch.float32, device="cuda")
+    for n_obj in objects:
+        for n_l in lights:
+            s = sg.config_polyhedra(n_obj, n_l, W=1920, H=1080)
+            g = capi.GpuScene(s)
+            rays, work, hits = _counts(g)
+            ms = _event_ms(lambda: capi.rt_render_stereo(
+                g.handle, s.camera, s.eye_sep, s.convergence, s.W, s.H, s.max_depth, img[0],
+                img[1], stream), stream, flush=flush)
+            capi.rt_sync_status(g.handle)
+            g.close()
+            rows.append({"objects": n_obj, "lights": n_l, "triangles": len(s.triangles),
+                         "ms_per_pair": round(ms, 4), "rays": int(rays.sum()),
+                         "shadow_rays": int(rays[1]), "node_visits": int(work[:, 0].sum()),
+                         "mrays_per_s": round(rays.sum() / (ms * 1e-3) / 1e6, 1)})
+    t = np.array([r["ms_per_pair"] for r in rows])
+    x = np.array([r["rays"] for r in rows], np.float64)
+    A = np.stack([x, np.ones_like(x)], 1)
+    coef, *_ = np.linalg.lstsq(A, t, rcond=None)
+    pred = A @ coef
+    r2 = 1 - np.sum((t - pred) ** 2) / max(np.sum((t - t.mean()) ** 2), 1e-30)
+    return {"rows": rows, "fit_ms_vs_rays": {"ms_per_mray": round(coef[0] * 1e6, 5),
+                                             "intercept_ms": round(coef[1], 4),
+                                             "r2": round(float(r2), 4)}}
+
+
+def probes(stream):
+    """L2 read bandwidth (cache-global loads over buffers below and above L2)
+    and MUFU reciprocal-square-root throughput."""
+    import torch
+    from paper_1702_01530_gb300 import capi
+    out = {"l2_read": []}
+    sink = torch.empty(capi.rt_probe_l2_threads() * 4, dtype=torch.int32, device="cuda")
+    for mib, reps in ((16, 400), (32, 200), (64, 100), (2048, 3)):
+        n_vec = mib * 2 ** 20 // 16
+        buf = torch.ones(n_vec * 4, dtype=torch.int32, device="cuda")
+        ms = _event_ms(lambda: capi.rt_probe_l2_read(buf, n_vec, reps, sink, stream), stream,
+                       reps=10)
+        out["l2_read"].append({"buffer_mib": mib, "passes": reps,
+                               "gbs": round(16 * n_vec * reps / (ms * 1e-3) / 1e9, 1)})
+        del buf
+    msink = torch.empty(capi.rt_probe_mufu_threads(), dtype=torch.float32, device="cuda")
+    iters = 4096
+    ms = _event_ms(lambda: capi.rt_probe_mufu(iters, msink, stream), stream, reps=10)
+    ops = capi.rt_probe_mufu_threads() * iters * 8
+    out["mufu_rsqrt_tops"] = round(ops / (ms * 1e-3) / 1e12, 3)
+    return out
+
+
+def run_study(args):
+    import torch
+
+    from paper_1702_01530_gb300 import build as rtbuild
+    from paper_1702_01530_gb300 import capi, scenegen as sg
+    rtbuild.build()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    n_sms = torch.cuda.get_device_properties(0).multi_processor_count
+    out = {"stage_split": {}}
+    blobs = workload(args)
+    for name, s in (("small_320x240_seed1", sg.config_small(1)),
+                    ("blobs_1920x1080_seed2", blobs)):
+        out["stage_split"][name] = stage_split(s, stream, flush)
+    out["complexity"] = complexity_sweep(stream, flush)
+    pr = probes(stream)
+    out["probes"] = pr
+    # the blob pair against the probed ceilings
+    g = capi.GpuScene(blobs)
+    rays, work, hits = _counts(g)
+    g.close()
+    l2 = max(r["gbs"] for r in pr["l2_read"] if r["buffer_mib"] <= 64)
+    fetched = int(work[:, 0].sum()) * 64 + int(work[:, 1].sum() + work[:, 2].sum()) * 48
+    mufu_ops = int(work[:, 1].sum() + work[:, 2].sum()) + 4 * int(rays.sum()) + hits
+    trace_ms = out["stage_split"]["blobs_1920x1080_seed2"]["render_stage_ms"]["trace"]
+    out["blob_pair_vs_probes"] = {
+        "trace_ms": trace_ms,
+        "fetched_bytes": fetched, "fetched_over_l2_ms": round(fetched / (l2 * 1e9) * 1e3, 4),
+        "mufu_ops": mufu_ops,
+        "mufu_bound_ms": round(mufu_ops / (pr["mufu_rsqrt_tops"] * 1e12) * 1e3, 4),
+        "mufu_per_sm_per_clk": round(pr["mufu_rsqrt_tops"] * 1e12 / (n_sms * 2070e6), 2)}
+    # the oracle on one core and on all cores, small scene
+    import oracle
+    s = sg.config_small(1)
+    osc = oracle.OracleScene(s)
+    res = {}
+    for n in (1, oracle.default_threads()):
+        t0 = time.perf_counter()
+        r = osc.render(n_threads=n)
+        dt = time.perf_counter() - t0
+        res[f"cores_{n}"] = {"seconds": round(dt, 3),
+                             "mrays_per_s": round(int(r["rays"].sum()) / dt / 1e6, 3)}
+    out["oracle_small_320x240"] = res
+    print(json.dumps(out))
+
+
 def sg_features(W, H):
     from paper_1702_01530_gb300 import scenegen as sg
     return sg.bf16_features_synthetic(5, W, H)
@@ -459,6 +701,18 @@ def main():
     rank, world, local = dist_setup(args)
     if args.ncu_net:
         run_ncu_net(args)
+        return
+    if args.study:
+        if rank == 0:
+            run_study(args)
+        return
+    if args.batch_only:
+        if rank == 0:
+            import torch
+
+            from paper_1702_01530_gb300 import build as rtbuild
+            rtbuild.build()
+            print(json.dumps(batch_leg(torch.cuda.current_stream())))
         return
     if args.impl == "reference":
         run_reference(args, rank, world)

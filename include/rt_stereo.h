@@ -380,6 +380,117 @@ int rt_render_stereo_reproj(const rt_scene* scene, const rt_camera* cam, float e
 int rt_stereo_composite(const float* d_L, const float* d_R, uint32_t W, uint32_t H, int mode,
                         float* d_out, void* cuda_stream);
 
+/*
+ * Batched stereo rendering: many stereo requests of uneven resolutions,
+ * depths and scenes traced by ONE persistent kernel launch, replayed from a
+ * captured CUDA graph. Paper Sec. 3 splits the image over parallel workers
+ * (Figure 1) and Sec. 4 / Figure 8 studies how the CUDA launch shape ("network
+ * size") affects the time; here every tile of every request is one unit of a
+ * shared work list, and the launch shape (tile shape, resident blocks per SM,
+ * mirror-queue capacity, request order) is chosen by a measured autotuner.
+ * Each request's images equal, bit for bit, what rt_render_stereo gives for
+ * the same scene and arguments.
+ *
+ * rt_request (88 bytes, little-endian, naturally aligned):
+ *   scene       a scene from rt_scene_create; it must outlive the batch and
+ *               must not be rendered by another call while a launch of the
+ *               batch is in flight (the batch reads its BVH, not its scratch)
+ *   camera, eye_sep, convergence, W, H, max_depth   as for rt_render_stereo
+ *   reserved    must be 0
+ *   d_out_L, d_out_R   DEVICE, H*W*3 float32 each, caller-owned
+ * Limits: 1 <= n_requests <= RT_BATCH_MAX_REQUESTS; sum of 2*W*H over the
+ * requests < 2^32; every request as rt_render_stereo validates it.
+ *
+ * rt_batch_config (24 bytes):
+ *   tile_w x tile_h   pixels per 32-ray tile: (4,8), (8,4), (16,2) or (32,1)
+ *   blocks_per_sm     resident blocks of 128 threads per SM, 1..the kernel's
+ *                     occupancy limit (0 = that limit)
+ *   cap_r             mirror-queue entries per warp: 64, 128 or 256
+ *   order             tile order over requests: RT_BATCH_ORDER_GIVEN,
+ *                     RT_BATCH_ORDER_LARGEST_FIRST, RT_BATCH_ORDER_SMALLEST_FIRST
+ *   track_latency     1 = record per request the device time at which its
+ *                     last ray finished (read with rt_batch_stats)
+ */
+#define RT_BATCH_MAX_REQUESTS 4096
+#define RT_BATCH_ORDER_GIVEN 0
+#define RT_BATCH_ORDER_LARGEST_FIRST 1
+#define RT_BATCH_ORDER_SMALLEST_FIRST 2
+typedef struct {
+  const rt_scene* scene;
+  rt_camera camera;
+  float eye_sep, convergence;
+  uint32_t W, H, max_depth, reserved;
+  float* d_out_L;
+  float* d_out_R;
+} rt_request;
+typedef struct {
+  uint32_t tile_w, tile_h, blocks_per_sm, cap_r, order, track_latency;
+} rt_batch_config;
+typedef struct rt_batch rt_batch;  /* opaque */
+
+/*
+ * rt_batch_create -- validate the requests, allocate the batch's device
+ * memory (colour sums for every pixel of every request, per-warp ray queues,
+ * the request table) and capture the launch sequence (request-table upload,
+ * clears, the persistent render kernel, the resolve kernel) into a CUDA
+ * graph.
+ *   reqs: host array of n_requests records (copied).
+ *   cfg:  host pointer or NULL (= tile 8x4, occupancy limit, cap_r 64,
+ *         largest request first, latency tracking on).
+ *   out_batch: receives the batch; released with rt_batch_destroy.
+ * Synchronous. Errors: RT_ERR_INVALID_ARG, RT_ERR_OOM, RT_ERR_CUDA.
+ */
+int rt_batch_create(const rt_request* reqs, uint32_t n_requests, const rt_batch_config* cfg,
+                    rt_batch** out_batch);
+
+/* Release the batch (waits for its last launch). NULL is ignored. */
+void rt_batch_destroy(rt_batch* batch);
+
+/*
+ * rt_batch_launch -- replay the batch's graph on cuda_stream: every request
+ * is traced and its two images written. Asynchronous; a device-side check
+ * that trips is reported by rt_batch_stats. Launches of one batch must not
+ * overlap each other.
+ */
+int rt_batch_launch(rt_batch* batch, void* cuda_stream);
+
+/*
+ * rt_batch_set_camera -- change request i's camera, eye_sep and convergence
+ * for the following launches (the graph uploads the request table from
+ * pinned host memory each launch). Waits for the previous launch to finish
+ * before editing that table. Errors: RT_ERR_INVALID_ARG.
+ */
+int rt_batch_set_camera(rt_batch* batch, uint32_t i, const rt_camera* cam, float eye_sep,
+                        float convergence);
+
+/*
+ * rt_batch_autotune -- time candidate configurations of this batch with CUDA
+ * events on cuda_stream (each: one warm-up launch, then `reps` timed
+ * launches, median) by coordinate descent over tile shape, blocks per SM,
+ * mirror-queue capacity and request order, starting from the current
+ * configuration; keep the fastest and re-capture the graph with it.
+ *   chosen: host, receives the configuration kept (may be NULL).
+ *   best_ms: host, receives its median launch time in ms (may be NULL).
+ * Synchronous; the request outputs hold the last candidate's (identical)
+ * images. Errors: RT_ERR_INVALID_ARG, RT_ERR_CUDA, RT_ERR_OOM, and the
+ * device-check codes of rt_batch_stats.
+ */
+int rt_batch_autotune(rt_batch* batch, uint32_t reps, void* cuda_stream, rt_batch_config* chosen,
+                      float* best_ms);
+
+/*
+ * rt_batch_stats -- wait for the batch's last launch and report it.
+ *   ray_counts: host uint64[3] or NULL: primary, shadow and mirror rays of
+ *     the last launch, all requests together.
+ *   request_ms: host float[n_requests] or NULL: per request, the time from
+ *     the start of the render kernel to the completion of its last ray
+ *     (needs track_latency; else filled with -1).
+ *   cfg: host or NULL: the configuration in use.
+ * Errors: RT_ERR_TIMEOUT / RT_ERR_DEVICE_CHECK if a device bound tripped in
+ * the last launch, RT_ERR_CUDA.
+ */
+int rt_batch_stats(rt_batch* batch, uint64_t* ray_counts, float* request_ms, rt_batch_config* cfg);
+
 /* Number of primitives of the scene (0 for NULL). */
 uint32_t rt_scene_num_prims(const rt_scene* scene);
 

@@ -1,4 +1,5 @@
-"""Python binding of the C-ABI in ``include/rt_stereo.h`` (ctypes).
+"""Python binding of the C-ABI in ``include/rt_stereo.h`` and
+``include/rt_probes.h`` (ctypes).
 
 Argument marshalling only: every step of BVH construction and rendering
 runs in the CUDA library ``_build/librtstereo.so``. Functions keep the C
@@ -70,6 +71,16 @@ _SIGS = {
     "rt_render_stereo_reproj": (ctypes.c_int, [_vp, _vp, _f32, _f32, _u32, _u32, _u32, _vp, _f32,
                                                _vp, _vp, _vp, _vp]),
     "rt_stereo_composite": (ctypes.c_int, [_vp, _vp, _u32, _u32, ctypes.c_int, _vp, _vp]),
+    "rt_batch_create": (ctypes.c_int, [_vp, _u32, _vp, ctypes.POINTER(_vp)]),
+    "rt_batch_destroy": (None, [_vp]),
+    "rt_batch_launch": (ctypes.c_int, [_vp, _vp]),
+    "rt_batch_set_camera": (ctypes.c_int, [_vp, _u32, _vp, _f32, _f32]),
+    "rt_batch_autotune": (ctypes.c_int, [_vp, _u32, _vp, _vp, _vp]),
+    "rt_batch_stats": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "rt_probe_l2_read": (ctypes.c_int, [_vp, ctypes.c_uint64, _u32, _vp, ctypes.c_uint64, _vp]),
+    "rt_probe_l2_threads": (ctypes.c_uint64, []),
+    "rt_probe_mufu": (ctypes.c_int, [_u32, _vp, ctypes.c_uint64, _vp]),
+    "rt_probe_mufu_threads": (ctypes.c_uint64, []),
     "rt_last_error": (ctypes.c_char_p, []),
     "rt_version": (ctypes.c_char_p, []),
 }
@@ -96,8 +107,9 @@ def lib():
 
 
 def header_functions() -> list[str]:
-    """Names of the functions declared in include/rt_stereo.h."""
-    src = open(HEADER).read()
+    """Names of the functions declared in include/*.h."""
+    import glob
+    src = "".join(open(h).read() for h in sorted(glob.glob(os.path.join(INCLUDE, "*.h"))))
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     return sorted(set(re.findall(r"\b(rt_[a-z0-9_]+)\s*\(", src)))
 
@@ -249,6 +261,96 @@ def rt_build_lbvh_noalloc(d_spheres, n_spheres, d_tris, n_tris, d_nodes, d_prims
 
 
 COMPOSITE_ANAGLYPH_COLOR, COMPOSITE_ANAGLYPH_GRAY, COMPOSITE_SIDE_BY_SIDE = 0, 1, 2
+
+
+# ------------------------------------------------------------- batching
+RT_BATCH_MAX_REQUESTS = 4096
+RT_BATCH_ORDER_GIVEN, RT_BATCH_ORDER_LARGEST_FIRST, RT_BATCH_ORDER_SMALLEST_FIRST = 0, 1, 2
+REQUEST_DT = np.dtype({"names": ["scene", "camera", "eye_sep", "convergence", "W", "H",
+                                 "max_depth", "reserved", "d_out_L", "d_out_R"],
+                       "formats": ["<u8", scenegen.CAMERA_DT, "<f4", "<f4", "<u4", "<u4", "<u4",
+                                   "<u4", "<u8", "<u8"],
+                       "offsets": [0, 8, 48, 52, 56, 60, 64, 68, 72, 80], "itemsize": 88})
+BATCH_CONFIG_DT = np.dtype([(k, "<u4") for k in ("tile_w", "tile_h", "blocks_per_sm", "cap_r",
+                                                  "order", "track_latency")])
+
+
+def batch_config(tile_w=8, tile_h=4, blocks_per_sm=0, cap_r=64, order=RT_BATCH_ORDER_LARGEST_FIRST,
+                 track_latency=1) -> np.ndarray:
+    c = np.zeros(1, BATCH_CONFIG_DT)
+    for k, v in dict(tile_w=tile_w, tile_h=tile_h, blocks_per_sm=blocks_per_sm, cap_r=cap_r,
+                     order=order, track_latency=track_latency).items():
+        c[k] = v
+    return c
+
+
+def make_requests(items) -> np.ndarray:
+    """items: (scene handle, camera record, eye_sep, convergence, W, H,
+    max_depth, out_L, out_R) per request; outputs are CUDA tensors or device
+    addresses."""
+    r = np.zeros(len(items), REQUEST_DT)
+    for i, (h, cam, es, cv, W, H, D, oL, oR) in enumerate(items):
+        r["scene"][i] = h or 0
+        r["camera"][i] = np.asarray(cam, scenegen.CAMERA_DT).reshape(())
+        r["eye_sep"][i], r["convergence"][i] = es, cv
+        r["W"][i], r["H"][i], r["max_depth"][i] = W, H, D
+        r["d_out_L"][i] = _dptr(oL) or 0
+        r["d_out_R"][i] = _dptr(oR) or 0
+    return r
+
+
+def rt_batch_create(reqs: np.ndarray, cfg: np.ndarray | None = None):
+    reqs = np.ascontiguousarray(reqs, REQUEST_DT)
+    out = _vp()
+    c = None if cfg is None else np.ascontiguousarray(cfg, BATCH_CONFIG_DT)
+    _check(lib().rt_batch_create(reqs.ctypes.data if len(reqs) else None, len(reqs),
+                                 None if c is None else c.ctypes.data, ctypes.byref(out)))
+    return out.value
+
+
+def rt_batch_destroy(b):
+    lib().rt_batch_destroy(b)
+
+
+def rt_batch_launch(b, stream=None):
+    _check(lib().rt_batch_launch(b, _stream(stream)))
+
+
+def rt_batch_set_camera(b, i, cam, eye_sep, convergence):
+    c = np.ascontiguousarray(np.asarray(cam, scenegen.CAMERA_DT).reshape(1))
+    _check(lib().rt_batch_set_camera(b, i, c.ctypes.data, eye_sep, convergence))
+
+
+def rt_batch_autotune(b, reps=3, stream=None):
+    c = np.zeros(1, BATCH_CONFIG_DT)
+    ms = ctypes.c_float()
+    _check(lib().rt_batch_autotune(b, reps, _stream(stream), c.ctypes.data, ctypes.byref(ms)))
+    return c, ms.value
+
+
+def rt_batch_stats(b, n_requests):
+    rays = np.zeros(3, np.uint64)
+    lat = np.zeros(n_requests, np.float32)
+    c = np.zeros(1, BATCH_CONFIG_DT)
+    _check(lib().rt_batch_stats(b, rays.ctypes.data, lat.ctypes.data, c.ctypes.data))
+    return rays, lat, c
+
+
+def rt_probe_l2_read(buf, n_vec, reps, sink, stream=None):
+    n_sink = sink.numel() * sink.element_size() // 16
+    _check(lib().rt_probe_l2_read(_dptr(buf), n_vec, reps, _dptr(sink), n_sink, _stream(stream)))
+
+
+def rt_probe_l2_threads() -> int:
+    return int(lib().rt_probe_l2_threads())
+
+
+def rt_probe_mufu(iters, sink, stream=None):
+    _check(lib().rt_probe_mufu(iters, _dptr(sink), sink.numel(), _stream(stream)))
+
+
+def rt_probe_mufu_threads() -> int:
+    return int(lib().rt_probe_mufu_threads())
 
 
 def rt_stereo_composite(L, R, W, H, mode, out, stream=None):

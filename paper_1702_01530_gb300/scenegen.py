@@ -263,6 +263,37 @@ def icosphere(subdiv: int) -> tuple[np.ndarray, np.ndarray]:
     return np.array(verts), np.array(faces, np.int64)
 
 
+BATCH_RESOLUTIONS = ((640, 360), (1280, 720), (1920, 1080), (3840, 2160))
+
+
+def config_batch(seed: int = 3, n_scenes: int = 16, n_requests: int = 64):
+    """The batched workload: n_requests stereo requests over n_scenes blob
+    scenes whose triangle counts are log-spaced from 1e3 to 2e6.
+
+    Scene k has n_blobs = max(1, round(1e3 * 2000^(k/(n_scenes-1)) / 1280))
+    displaced icospheres (1,280 triangles each) and 5 spheres per blob, built
+    by ``config_blobs`` with seed 100*seed + k, 4 lights, and a box scaled by
+    (n_blobs/200)^(1/3) so the density matches the 200-blob scene. Request i
+    draws (from SplitMix64(seed), three uniforms per request in this order)
+    its scene index floor(16 u), its per-eye resolution
+    BATCH_RESOLUTIONS[floor(4 u)] and its reflection depth 2 + floor(5 u).
+    Returns (scenes, [(scene index, W, H, max_depth), ...]).
+    """
+    scenes = []
+    for k in range(n_scenes):
+        ntri = 1e3 * 2000.0 ** (k / max(1, n_scenes - 1))
+        nb = max(1, int(round(ntri / 1280.0)))
+        scenes.append(config_blobs(100 * seed + k, n_blobs=nb, n_spheres=5 * nb,
+                                   box=50.0 * (nb / 200.0) ** (1.0 / 3.0)))
+    u = SplitMix64(seed).uniform(3 * n_requests).reshape(n_requests, 3)
+    reqs = []
+    for i in range(n_requests):
+        si = min(n_scenes - 1, int(u[i, 0] * n_scenes))
+        W, H = BATCH_RESOLUTIONS[min(3, int(u[i, 1] * 4))]
+        reqs.append((si, W, H, 2 + min(4, int(u[i, 2] * 5))))
+    return scenes, reqs
+
+
 def config_polyhedra(n_objects: int = 5, n_lights: int = 1, W: int = 320, H: int = 240,
                      max_depth: int = 3, ground: bool = False) -> Scene:
     """The Sec. 4 test scenes (Figures 3-7): up to 6 polyhedra and 1-8 lights.

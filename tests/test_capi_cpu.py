@@ -86,3 +86,17 @@ def test_struct_layouts_match_header():
                  "float albedo[3]; float reflectivity;",
                  "float position[3]; float intensity;"):
         assert frag in src
+
+
+def test_batch_create_rejects_empty_and_null_requests_before_any_device_work():
+    import ctypes
+    L = capi.lib()
+    out = ctypes.c_void_p()
+    assert L.rt_batch_create(None, 0, None, ctypes.byref(out)) == capi.RT_ERR_INVALID_ARG
+    reqs = capi.make_requests([(None, scenegen.config_small(1).camera, 0.065, 10.0, 8, 8, 1, 16, 16)])
+    assert L.rt_batch_create(reqs.ctypes.data, 1, None, ctypes.byref(out)) == capi.RT_ERR_INVALID_ARG
+    assert "scene is NULL" in capi.rt_last_error()
+    assert out.value is None
+    reqs["scene"][0] = 0
+    reqs["reserved"][0] = 0
+    assert capi.REQUEST_DT.itemsize == 88 and capi.BATCH_CONFIG_DT.itemsize == 24
