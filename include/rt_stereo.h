@@ -303,7 +303,9 @@ int rt_net_status(const rt_net* net, void* cuda_stream);
 
 /*
  * rt_net_forward -- retrace probability of every pixel of a W x H feature map.
- *   d_feat16: DEVICE, W*H*16 BF16 (as uint16 bits), row-major pixels.
+ *   d_feat16: DEVICE, W*H*16 BF16 (as uint16 bits), row-major pixels,
+ *             16-byte aligned (it is read by the tensor-memory-access engine;
+ *             a misaligned pointer gives RT_ERR_CUDA).
  *   d_prob:   DEVICE, W*H float32 output in (0, 1).
  * Asynchronous on cuda_stream; the network's activation buffers are grown
  * on demand (allocation on the first call at a size).

@@ -2,29 +2,38 @@
 // (9 -> 32 -> 32 -> 32 -> 1, zero padding 1, ReLU, sigmoid), BF16 operands
 // and FP32 accumulation on the 5th-generation tensor cores (sm_103a).
 //
-// Convolution as implicit GEMM on tcgen05:
-//   a persistent CTA (128 threads) computes tiles of R rows x 128 consecutive
-//   pixels: per row, D[128 pixels, Cout] = sum over the 9 taps (dy, dx) of
+// Convolution as implicit GEMM on tcgen05 (k_conv_tma):
+//   a persistent CTA computes tiles of R rows x 128 consecutive pixels: per
+//   row, D[128 pixels, Cout] = sum over the 9 taps (dy, dx) of
 //   A_tap[128, Cin] x B_tap[Cin, Cout]. The input halo (R+2 rows x 130 pixels x
 //   Cin channels, BF16) sits in shared memory as 16-byte (8-channel) chunks
 //   ordered [chunk][halo pixel], so A_tap for every tap is the same matrix
 //   shifted by (row+dy)*130 + dx rows: the K-major, non-swizzled operand layout
-//   with 8-row core matrices 128 B apart (SBO) and 8-channel chunks
-//   (R+2)*130*16 B apart (LBO). Weights are pre-packed in the same core-matrix
-//   layout. Halos stream in with 16-byte cp.async copies (zero-filled
-//   outside the image); with one buffer the next tile's copies start as soon
-//   as the MMAs of this tile have consumed it, under the epilogue. One elected thread issues 9 * Cin/16 tcgen05.mma (M=128,
-//   N=Cout, K=16, kind::f16 with BF16 inputs) into a TMEM accumulator,
-//   commits to an mbarrier; the four warps read their 32 TMEM lanes
-//   (tcgen05.ld 32x32b) for the fused epilogue (bias + ReLU -> BF16, or
-//   bias + sigmoid -> FP32, or the backward ReLU mask).
+//   with 8-row core matrices 128 B apart (SBO) and 8-channel chunk planes
+//   (R+2)*130*16 B (rounded up to 128 B) apart (LBO). Weights are pre-packed in
+//   the same core-matrix layout.
+//   The CTA is warp-specialised. A producer thread loads each halo with one
+//   TMA box per 8-channel chunk (cp.async.bulk.tensor, zeros outside the
+//   image) into a ring of halo buffers, up to RT_CONV_STAGES - 1 tiles ahead,
+//   and issues the tile's 9 * Cin/16 tcgen05.mma per row (M=128, N=Cout, K=16,
+//   kind::f16 with BF16 inputs) into one of two TMEM accumulator sets; the
+//   epilogue warps read their TMEM lanes (tcgen05.ld 32x32b) for the fused
+//   epilogue (bias + ReLU -> BF16, bias + sigmoid -> FP32, or the backward
+//   ReLU mask), so loads, MMAs and epilogues of consecutive tiles overlap.
 //   Every mbarrier wait has an iteration bound; on expiry the kernel sets the
-//   error word, skips the tile and still frees its TMEM.
+//   error word, waits (bounded) for what it has in flight and frees its TMEM.
+//
+// Layouts in HBM: the 16-channel maps (network input features, the BCE
+// gradient) are interleaved [P][16]; the 32-channel activations and data
+// gradients are chunk-planar [4][P][8] (plane k holds channels 8k..8k+7 of
+// every pixel), so each TMA box row is one contiguous run of 130 x 16 bytes
+// and each warp's epilogue store is a contiguous 512-byte run per plane.
 //
 // Backward pass: data gradients are convolutions with the 3x3 taps flipped
 // and Cin/Cout swapped (same tensor-core kernel); weight gradients are an
 // FP32 CUDA-core reduction over pixels; BCE on the sigmoid output; Adam on
 // FP32 master weights.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -36,19 +45,30 @@
 namespace rt {
 namespace nn {
 
-// Tuning knobs: RT_CONV_ROWS = image rows per tile (R accumulators of
-// 128 pixels share one halo of R+2 rows); RT_CONV_DBUF = 1 double-buffers
-// the halo (the next tile loads while this one computes). Measured on GB300
-// at 1920x1080 (network forward, 4 layers, identical output bit for bit):
-// R=1 0.52 ms, R=2 0.45-0.48, R=4 0.42-0.43, R=8 single-buffered 0.40 ms.
+// Tuning knobs: RT_CONV_ROWS = image rows per tile (R accumulators of 128
+// pixels share one halo of R+2 rows); RT_CONV_STAGES = halo buffers (the
+// producer loads up to RT_CONV_STAGES - 1 tiles ahead of the MMAs);
+// RT_CONV_EPI_WG = epilogue warpgroups (4 warps each; group g takes the rows
+// ry with ry % RT_CONV_EPI_WG == g of every tile). Measured on GB300 at
+// 1920x1080 (network forward, 4 layers, identical output bit for bit), with
+// interleaved 32-channel maps: R=8 / 2 stages 0.45 ms, R=4 with 2 / 3 / 4
+// stages 0.41 / 0.318 / 0.321, R=2 with 3 / 4 / 6 stages 0.377 / 0.377 /
+// 0.386, epilogue groups 1, 2, 4 alike; an earlier single-role kernel
+// (16-byte cp.async halos, one buffer, one accumulator set, 2 CTAs per SM)
+// took 0.385 ms at R=8.
 #ifndef RT_CONV_ROWS
-#define RT_CONV_ROWS 8
+#define RT_CONV_ROWS 4
 #endif
-#ifndef RT_CONV_DBUF
-#define RT_CONV_DBUF 0
+#ifndef RT_CONV_STAGES
+#define RT_CONV_STAGES 3
 #endif
+#ifndef RT_CONV_EPI_WG
+#define RT_CONV_EPI_WG 2
+#endif
+constexpr int kStages = RT_CONV_STAGES;
+constexpr int kEpiWarps = 4 * RT_CONV_EPI_WG;
+constexpr int kConvTmaThreads = 32 * (kEpiWarps + 1);
 constexpr int kRows = RT_CONV_ROWS;
-constexpr int kBufs = RT_CONV_DBUF ? 2 : 1;
 constexpr int kTileM = 128;          // pixels per row tile (one MMA M block)
 constexpr int kHaloW = kTileM + 2;   // 130
 constexpr int kHaloRows = (kRows + 2) * kHaloW;  // halo pixels per tile
@@ -61,20 +81,24 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-// tcgen05 shared-memory matrix descriptor, no swizzle
-__device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
-  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
-  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
-  d |= 1ull << 46;  // descriptor version for tcgen05
-  return d;        // base offset 0, relative LBO mode, swizzle none
-}
-
 // instruction descriptor: kind::f16, D = F32, A = B = BF16, both K-major
 __host__ __device__ constexpr uint32_t make_idesc(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
          ((uint32_t)(M >> 4) << 24);
+}
+
+// Low and high words of a no-swizzle descriptor. A descriptor of the same
+// operand at byte offset k from its base is the base's low word plus k >> 4
+// (the start-address field cannot carry: shared addresses stay below 2^18),
+// so the unrolled MMA loops below pay one integer add per descriptor.
+__device__ __forceinline__ uint32_t desc_lo(uint32_t saddr, uint32_t lbo) {
+  return ((saddr >> 4) & 0x3FFFu) | (((lbo >> 4) & 0x3FFFu) << 16);
+}
+__host__ __device__ constexpr uint32_t desc_hi(uint32_t sbo) {
+  return ((sbo >> 4) & 0x3FFFu) | (1u << 14);   // bit 46 of the descriptor: tcgen05 version
+}
+__device__ __forceinline__ uint64_t desc_join(uint32_t lo, uint32_t hi) {
+  return ((uint64_t)hi << 32) | lo;
 }
 
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
@@ -132,14 +156,24 @@ __device__ __forceinline__ void fence_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
-// 16-byte asynchronous global->shared copy; src_bytes = 0 writes zeros
-__device__ __forceinline__ void cp_async16(void* dst, const void* src, uint32_t src_bytes) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src),
-               "r"(src_bytes)
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
                : "memory");
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+// 4-D tiled TMA load of one box into shared memory, completion counted in
+// bytes on the mbarrier; out-of-range elements are written as zeros
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int c0, int c1,
+                                            int c2, int c3, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+      : "memory");
+}
 
 // 16 consecutive TMEM columns of this warp's 32 lanes
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
@@ -155,198 +189,258 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// the same load without the wait: several loads may share one tcgen05.wait::ld
+__device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t r[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
   __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
   return *reinterpret_cast<uint32_t*>(&h);
 }
 
-// ------------------------------------------------------------ conv kernel
-// in:  BF16 [P][CIN] activations (CIN = 16 or 32)
-// wpk: BF16 packed weights, [tap][CIN/8][COUT][8]
-// EPI_RELU_BF16:     out16[P][COUT] = relu(acc + bias)
-// EPI_SIGMOID_F32:   out32[P] = sigmoid(acc[0] + bias[0])
-// EPI_BWD_MASK_BF16: out16[P][COUT] = acc * (mask16[P][COUT] > 0)
-template <int CIN>
-__device__ __forceinline__ void load_halo_async(unsigned char* halo, const __nv_bfloat16* in,
-                                                uint32_t tile, uint32_t tiles_x, uint32_t W,
-                                                uint32_t H, int tid) {
+// All MMAs of one tile: per output row ry, D[128 px, COUT] (TMEM columns
+// dtmem + ry*COUT) = sum over taps (dy, dx) and 16-channel K steps of the halo
+// shifted by (ry+dy)*130 + dx pixels times the packed weights of the tap.
+// `plane` is the byte distance between 8-channel chunk planes of the halo.
+template <int CIN, int COUT, uint32_t kPlaneBytes>
+__device__ __forceinline__ void issue_tile_mmas(uint32_t hbase, uint32_t wbase, uint32_t dtmem,
+                                                uint32_t idesc) {
   constexpr int kChunks = CIN / 8;
-  const int ty = (int)(tile / tiles_x);
-  const int y = ty * kRows;
-  const int x0 = (int)(tile - (uint32_t)ty * tiles_x) * kTileM;
-  // 16-byte chunk c of halo pixel r goes to ((c * kHaloRows) + r) * 16; consecutive
-  // threads take consecutive halo pixels of one chunk (conflict-free stores)
-  for (int k = tid; k < kHaloRows * kChunks; k += 128) {
-    const int c = k / kHaloRows, r = k - c * kHaloRows;
-    const int dy = r / kHaloW, xx = r - dy * kHaloW;
-    const int gy = y + dy - 1, gx = x0 + xx - 1;
-    const bool ok = gy >= 0 && gy < (int)H && gx >= 0 && gx < (int)W;
-    const __nv_bfloat16* src = ok ? in + ((size_t)gy * W + gx) * CIN + c * 8 : in;
-    cp_async16(halo + ((size_t)c * kHaloRows + r) * 16, src, ok ? 16u : 0u);
+  const uint32_t a_lo = desc_lo(hbase, kPlaneBytes), b_lo = desc_lo(wbase, COUT * 16);
+  constexpr uint32_t hi = desc_hi(128u);
+#pragma unroll
+  for (int ry = 0; ry < kRows; ++ry) {
+#pragma unroll
+    for (int tap = 0; tap < 9; ++tap) {
+      const int dy = tap / 3, dx = tap % 3;
+#pragma unroll
+      for (int ks = 0; ks < CIN / 16; ++ks) {
+        const uint32_t a_off = (2u * ks) * kPlaneBytes + (uint32_t)((ry + dy) * kHaloW + dx) * 16u;
+        const uint32_t b_off = (uint32_t)((tap * kChunks + 2 * ks) * COUT) * 16u;
+        mma_bf16(dtmem + (uint32_t)(ry * COUT), desc_join(a_lo + (a_off >> 4), hi),
+                 desc_join(b_lo + (b_off >> 4), hi), idesc, (tap | ks) ? 1u : 0u);
+      }
+    }
   }
 }
 
-template <int CIN, int COUT, int EPI>
-__global__ void __launch_bounds__(128) k_conv_tc(const __nv_bfloat16* __restrict__ in,
-                                                  const __nv_bfloat16* __restrict__ wpk,
-                                                  const float* __restrict__ bias,
-                                                  const __nv_bfloat16* __restrict__ mask16,
-                                                  __nv_bfloat16* __restrict__ out16,
-                                                  float* __restrict__ out32, uint32_t W, uint32_t H,
-                                                  uint32_t* err) {
+// ------------------------------------------------------------ conv kernel
+// in:  BF16, [P][16] interleaved (CIN = 16) or [4][P][8] planar (CIN = 32)
+// wpk: BF16 packed weights, [tap][CIN/8][COUT][8]
+// EPI_RELU_BF16:     out16 (planar [4][P][8]) = relu(acc + bias)
+// EPI_SIGMOID_F32:   out32[P] = sigmoid(acc[0] + bias[0])
+// EPI_BWD_MASK_BF16: out16 (planar) = acc * (mask16 (planar) > 0)
+//
+// The last warp is the producer: its first lane loads each tile's halo as one
+// TMA box per 8-channel chunk (8 channels x 130 pixels x R+2 rows, zeros
+// outside the image) into a ring of RT_CONV_STAGES halo buffers, up to
+// RT_CONV_STAGES - 1 tiles ahead, and issues the tile's MMAs into one of two
+// TMEM accumulator sets as soon as its halo has landed and the epilogue has
+// drained that set. The epilogue warps (RT_CONV_EPI_WG warpgroups; warp w
+// reads TMEM lanes 32 (w % 4) .. +31) run the epilogue of tile i while the
+// tensor cores work on tile i+1 and the TMA engine fetches the next tiles.
+//   halo_full[b]: TMA bytes of halo buffer b arrived (expect_tx by the producer)
+//   acc_full[s]:  MMAs of accumulator set s done (tcgen05.commit); this also
+//                 frees the halo buffer they read (the producer waits on it
+//                 before reloading that buffer)
+//   acc_empty[s]: every epilogue thread has read set s
+// Every wait is bounded; a wait that gives up sets the error word, and before
+// the CTA frees TMEM and exits the producer waits (bounded) for the copies and
+// MMAs it has issued.
+template <int CIN, int COUT>
+struct ConvTmaLayout {
+  static constexpr int kChunks = CIN / 8;
+  static constexpr uint32_t kBox = (uint32_t)kHaloRows * 16u;          // bytes of one TMA box
+  static constexpr uint32_t kPlane = (kBox + 127u) & ~127u;            // chunk plane stride
+  static constexpr uint32_t kHalo = ((kChunks * kPlane) + 1023u) & ~1023u;
+  static constexpr uint32_t kW = ((9u * COUT * CIN * 2u) + 127u) & ~127u;
+  static constexpr uint32_t kAcc = (uint32_t)kRows * COUT;
+  static constexpr uint32_t kSet = kAcc <= 32 ? 32 : (kAcc <= 64 ? 64 : (kAcc <= 128 ? 128 : 256));
+  static constexpr uint32_t kTmemCols = 2 * kSet;
+  static constexpr size_t kSmem = kStages * (size_t)kHalo + kW + 32 * 4 + 16 * 8 + 16;
+};
+
+template <int CIN, int COUT, int EPI, bool PLANAR_IN>
+__global__ void __launch_bounds__(kConvTmaThreads, 1)
+    k_conv_tma(const __grid_constant__ CUtensorMap tmap, const __nv_bfloat16* __restrict__ wpk,
+               const float* __restrict__ bias, const __nv_bfloat16* __restrict__ mask16,
+               __nv_bfloat16* __restrict__ out16, float* __restrict__ out32, uint32_t W, uint32_t H,
+               uint32_t* err) {
+  using Lt = ConvTmaLayout<CIN, COUT>;
   static_assert(CIN % 16 == 0 && (COUT == 16 || COUT == 32), "shape");
-  constexpr int kChunks = CIN / 8;
-  constexpr uint32_t kHaloBytes = kHaloRows * CIN * 2;
-  constexpr uint32_t kHaloStride = (kHaloBytes + 1023) & ~1023u;
-  constexpr uint32_t kWBytes = 9 * COUT * CIN * 2;
-  constexpr uint32_t kLBO_A = kHaloRows * 16;   // next 8-channel chunk of the halo
-  constexpr uint32_t kLBO_B = COUT * 16;        // next 8-channel chunk of a weight tap
-  constexpr uint32_t kAccCols = kRows * COUT;   // one accumulator per output row
-  constexpr uint32_t kTmemCols = kAccCols <= 32 ? 32 : (kAccCols <= 64 ? 64 : (kAccCols <= 128 ? 128 : 256));
+  static_assert(Lt::kTmemCols <= 512, "two accumulator sets must fit in TMEM");
   extern __shared__ __align__(1024) unsigned char smem[];
-  unsigned char* halo0 = smem;                  // kBufs halo buffers
-  unsigned char* wsm = smem + kBufs * kHaloStride;
-  float* bsm = reinterpret_cast<float*>(wsm + ((kWBytes + 127) & ~127u));
-  uint64_t* bar = reinterpret_cast<uint64_t*>(bsm + 32);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 1);
+  static_assert(kStages >= 2 && kStages <= 8, "halo stages");
+  unsigned char* halo0 = smem;
+  unsigned char* wsm = smem + kStages * Lt::kHalo;
+  float* bsm = reinterpret_cast<float*>(wsm + Lt::kW);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(bsm + 32);
+  uint64_t* halo_full = bars;        // [kStages]
+  uint64_t* acc_full = bars + 8;     // [2]
+  uint64_t* acc_empty = bars + 10;   // [2]
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 12);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint32_t tiles_x = (W + kTileM - 1) / kTileM;
   const uint32_t n_tiles = tiles_x * ((H + kRows - 1) / kRows);
-  // first halo in flight while the weights are copied
-  if (blockIdx.x < n_tiles) load_halo_async<CIN>(halo0, in, blockIdx.x, tiles_x, W, H, tid);
-  cp_async_commit();
   {
     const uint4* src = reinterpret_cast<const uint4*>(wpk);
     uint4* dst = reinterpret_cast<uint4*>(wsm);
-    for (uint32_t i = tid; i < kWBytes / 16; i += 128) dst[i] = src[i];
+    for (uint32_t i = tid; i < 9u * COUT * CIN * 2u / 16u; i += blockDim.x) dst[i] = src[i];
     if (tid < COUT) bsm[tid] = bias ? bias[tid] : 0.f;
   }
   if (tid == 0) {
-    mbar_init(bar, 1);
+    for (int b = 0; b < kStages; ++b) mbar_init(halo_full + b, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(acc_full + b, 1);
+      mbar_init(acc_empty + b, 32 * kEpiWarps);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmap)) : "memory");
   }
-  if (warp == 0) tmem_alloc(tslot, kTmemCols);
+  if (warp == 0) tmem_alloc(tslot, Lt::kTmemCols);
   fence_async_smem();
   fence_before();
   __syncthreads();
   fence_after();
   const uint32_t tmem = *tslot;
-  const uint32_t idesc = make_idesc(kTileM, COUT);
-  uint32_t phase = 0;
-  uint32_t it = 0;
 
-  for (uint32_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++it) {
-    unsigned char* halo = halo0 + (kBufs == 2 ? (it & 1u) : 0u) * kHaloStride;
-    const uint32_t next = tile + gridDim.x;
-    if (kBufs == 2) {
-      // next tile's halo into the other buffer (freed at the end of the last iteration)
-      if (next < n_tiles)
-        load_halo_async<CIN>(halo0 + ((it + 1) & 1u) * kHaloStride, in, next, tiles_x, W, H, tid);
-      cp_async_commit();
-      cp_async_wait_1();          // this tile's halo has landed
-    } else {
-      asm volatile("cp.async.wait_all;" ::: "memory");
-    }
-    fence_async_smem();
-    fence_before();
-    __syncthreads();
-    fence_after();
-    const int ty = (int)(tile / tiles_x);
-    const int y = ty * kRows;
-    const int x0 = (int)(tile - (uint32_t)ty * tiles_x) * kTileM;
-    if (tid == 0) {
-      const uint32_t hbase = smem_u32(halo), wbase = smem_u32(wsm);
+  if (warp == kEpiWarps) {
+    if (lane == 0) {
+      const uint32_t idesc = make_idesc(kTileM, COUT);
+      const uint32_t wbase = smem_u32(wsm);
+      bool issued_halo[kStages], issued_acc[2] = {false, false};
+      uint32_t halo_par[kStages], acc_par[2] = {0, 0};     // parity of the last issued use
 #pragma unroll
-      for (int ry = 0; ry < kRows; ++ry) {
-        uint32_t acc = 0;
+      for (int b = 0; b < kStages; ++b) { issued_halo[b] = false; halo_par[b] = 0; }
+      bool ok = true;
+      // tile number j of this CTA's sequence goes to halo buffer j % kStages
+      auto load = [&](uint32_t j) {
+        const uint32_t tile = blockIdx.x + j * gridDim.x;
+        const int b = (int)(j % kStages);
+        const int ty = (int)(tile / tiles_x);
+        const int y = ty * kRows, x0 = (int)(tile - (uint32_t)ty * tiles_x) * kTileM;
+        mbar_arrive_expect_tx(halo_full + b, (uint32_t)Lt::kChunks * Lt::kBox);
 #pragma unroll
-        for (int tap = 0; tap < 9; ++tap) {
-          const int dy = tap / 3, dx = tap % 3;
-#pragma unroll
-          for (int ks = 0; ks < CIN / 16; ++ks) {
-            const uint64_t da = make_desc(
-                hbase + (uint32_t)((2 * ks) * kHaloRows + (ry + dy) * kHaloW + dx) * 16u, kLBO_A, 128u);
-            const uint64_t db =
-                make_desc(wbase + (uint32_t)((tap * kChunks + 2 * ks) * COUT) * 16u, kLBO_B, 128u);
-            mma_bf16(tmem + (uint32_t)(ry * COUT), da, db, idesc, acc);
-            acc = 1;
-          }
+        for (int c = 0; c < Lt::kChunks; ++c)
+          if (PLANAR_IN)   // tensor {8, W, H, CIN/8}
+            tma_load_4d(halo0 + (size_t)b * Lt::kHalo + (size_t)c * Lt::kPlane, &tmap, 0, x0 - 1,
+                        y - 1, c, halo_full + b);
+          else             // tensor {8, CIN/8, W, H}
+            tma_load_4d(halo0 + (size_t)b * Lt::kHalo + (size_t)c * Lt::kPlane, &tmap, 0, c, x0 - 1,
+                        y - 1, halo_full + b);
+        issued_halo[b] = true;
+        halo_par[b] = (j / kStages) & 1u;
+      };
+      const uint32_t my_tiles = blockIdx.x < n_tiles ? (n_tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+      for (uint32_t j = 0; j + 1 < (uint32_t)kStages && j < my_tiles; ++j) load(j);
+      for (uint32_t it = 0; it < my_tiles && ok; ++it) {
+        const int b = (int)(it % kStages), sa = (int)(it & 1u);
+        if (!mbar_wait(halo_full + b, (it / kStages) & 1u)) { ok = false; break; }
+        issued_halo[b] = false;
+        if (it >= 2 && !mbar_wait(acc_empty + sa, ((it >> 1) - 1) & 1u)) { ok = false; break; }
+        fence_after();
+        issue_tile_mmas<CIN, COUT, Lt::kPlane>(smem_u32(halo0 + (size_t)b * Lt::kHalo), wbase,
+                                               tmem + (uint32_t)sa * Lt::kSet, idesc);
+        mma_commit(acc_full + sa);
+        issued_acc[sa] = true;
+        acc_par[sa] = (it >> 1) & 1u;
+        const uint32_t j = it + kStages - 1;
+        if (j < my_tiles) {
+          // buffer j % kStages last held tile it - 1: free once its MMAs completed
+          if (it >= 1 && !mbar_wait(acc_full + ((it - 1) & 1u), ((it - 1) >> 1) & 1u)) { ok = false; break; }
+          load(j);
         }
       }
-      mma_commit(bar);
+      if (!ok) atomicOr(err, ERR_ITER);
+      // drain: copies and MMAs this thread issued complete before TMEM is freed
+      for (int b = 0; b < kStages; ++b)
+        if (issued_halo[b]) mbar_wait(halo_full + b, halo_par[b]);
+      for (int b = 0; b < 2; ++b)
+        if (issued_acc[b]) mbar_wait(acc_full + b, acc_par[b]);
     }
-    const bool ok = mbar_wait(bar, phase);
-    phase ^= 1u;
-    fence_after();
-    if (!ok) {
-      if (tid == 0) atomicOr(err, ERR_ITER);
-      break;                       // uniform: every thread saw the same barrier state
-    }
-    // epilogue: warp w owns TMEM lanes (pixels) 32w .. 32w + 31 of every row
-    if (kBufs == 1 && next < n_tiles) {
-      // single buffer: the halo was consumed by the MMAs (barrier passed), so
-      // the next tile's loads may start under the epilogue
-      fence_before();
-      __syncthreads();
+    __syncwarp();
+  } else {
+    uint32_t it = 0;
+    for (uint32_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++it) {
+      const int s = (int)(it & 1u);
+      // warp-uniform outcome: tcgen05.ld below is a warp-collective instruction
+      if (!__all_sync(0xFFFFFFFFu, mbar_wait(acc_full + s, (it >> 1) & 1u))) {
+        if (lane == 0) atomicOr(err, ERR_ITER);
+        break;
+      }
       fence_after();
-      load_halo_async<CIN>(halo0, in, next, tiles_x, W, H, tid);
-      cp_async_commit();
-    }
-    const int x = x0 + warp * 32 + lane;
+      const int ty = (int)(tile / tiles_x);
+      const int y = ty * kRows;
+      const int x0 = (int)(tile - (uint32_t)ty * tiles_x) * kTileM;
+      const int quarter = warp & 3, group = warp >> 2;   // TMEM lanes 32*quarter .. +31
+      const int x = x0 + quarter * 32 + lane;
 #pragma unroll
-    for (int ry = 0; ry < kRows; ++ry) {
-      const int yy = y + ry;
-      const bool valid = x < (int)W && yy < (int)H;
-      const size_t p = (size_t)yy * W + x;
-      const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(ry * COUT);
-      if (EPI == EPI_SIGMOID_F32) {
-        float v[16];
-        tmem_ld16(lane_addr, v);
-        if (valid) out32[p] = 1.f / (1.f + __expf(-(v[0] + bsm[0])));
-      } else {
-#pragma unroll
-        for (int half = 0; half < COUT / 16; ++half) {
+      for (int ry = group; ry < kRows; ry += RT_CONV_EPI_WG) {
+        const int yy = y + ry;
+        const bool valid = x < (int)W && yy < (int)H;
+        const size_t p = (size_t)yy * W + x;
+        const size_t P = (size_t)W * H;
+        const uint32_t lane_addr =
+            tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)s * Lt::kSet + (uint32_t)(ry * COUT);
+        if (EPI == EPI_SIGMOID_F32) {
           float v[16];
-          tmem_ld16(lane_addr + half * 16, v);
-          if (valid) {
-            uint32_t packed[8];
-            if (EPI == EPI_RELU_BF16) {
+          tmem_ld16(lane_addr, v);
+          if (valid) out32[p] = 1.f / (1.f + __expf(-(v[0] + bsm[0])));
+        } else {
+          uint32_t r[COUT / 16][16];                 // all columns of the row, one wait
 #pragma unroll
-              for (int i = 0; i < 8; ++i)
-                packed[i] = pack_bf16(fmaxf(v[2 * i] + bsm[half * 16 + 2 * i], 0.f),
-                                      fmaxf(v[2 * i + 1] + bsm[half * 16 + 2 * i + 1], 0.f));
-            } else {
-              const uint4* m4 = reinterpret_cast<const uint4*>(mask16 + p * COUT + half * 16);
-              const uint4 ma = m4[0], mb = m4[1];
-              const uint32_t mw[8] = {ma.x, ma.y, ma.z, ma.w, mb.x, mb.y, mb.z, mb.w};
+          for (int half = 0; half < COUT / 16; ++half) tmem_ld16_nowait(lane_addr + half * 16, r[half]);
+          tmem_wait_ld();
 #pragma unroll
-              for (int i = 0; i < 8; ++i) {
-                const __nv_bfloat162 mm = *reinterpret_cast<const __nv_bfloat162*>(&mw[i]);
-                const float m0 = __bfloat162float(mm.x), m1 = __bfloat162float(mm.y);
-                packed[i] = pack_bf16(m0 > 0.f ? v[2 * i] : 0.f, m1 > 0.f ? v[2 * i + 1] : 0.f);
+          for (int half = 0; half < COUT / 16; ++half) {
+            float v[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[half][i]);
+            if (valid) {
+              uint32_t packed[8];
+              if (EPI == EPI_RELU_BF16) {
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+                  packed[i] = pack_bf16(fmaxf(v[2 * i] + bsm[half * 16 + 2 * i], 0.f),
+                                        fmaxf(v[2 * i + 1] + bsm[half * 16 + 2 * i + 1], 0.f));
+              } else {
+                // planar: channels 16 half + 0..7 and + 8..15 sit in planes 2 half, 2 half + 1
+                const uint4 ma = *reinterpret_cast<const uint4*>(mask16 + ((2 * half) * P + p) * 8);
+                const uint4 mb = *reinterpret_cast<const uint4*>(mask16 + ((2 * half + 1) * P + p) * 8);
+                const uint32_t mw[8] = {ma.x, ma.y, ma.z, ma.w, mb.x, mb.y, mb.z, mb.w};
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                  const __nv_bfloat162 mm = *reinterpret_cast<const __nv_bfloat162*>(&mw[i]);
+                  const float m0 = __bfloat162float(mm.x), m1 = __bfloat162float(mm.y);
+                  packed[i] = pack_bf16(m0 > 0.f ? v[2 * i] : 0.f, m1 > 0.f ? v[2 * i + 1] : 0.f);
+                }
               }
+              *reinterpret_cast<uint4*>(out16 + ((2 * half) * P + p) * 8) =
+                  make_uint4(packed[0], packed[1], packed[2], packed[3]);
+              *reinterpret_cast<uint4*>(out16 + ((2 * half + 1) * P + p) * 8) =
+                  make_uint4(packed[4], packed[5], packed[6], packed[7]);
             }
-            uint4* o = reinterpret_cast<uint4*>(out16 + p * COUT + half * 16);
-            o[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
-            o[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
           }
         }
       }
+      fence_before();
+      mbar_arrive(acc_empty + s);
     }
-    fence_before();
-    __syncthreads();  // TMEM read and this halo consumed before they are reused
-    fence_after();
   }
-  asm volatile("cp.async.wait_all;" ::: "memory");
+  fence_before();
   __syncthreads();
-  if (warp == 0) tmem_dealloc(tmem, kTmemCols);
+  fence_after();
+  if (warp == 0) tmem_dealloc(tmem, Lt::kTmemCols);
 }
 
-template <int CIN, int COUT>
-constexpr size_t conv_smem_bytes() {
-  return kBufs * ((kHaloRows * CIN * 2 + 1023) & ~1023) + ((9 * COUT * CIN * 2 + 127) & ~127) + 32 * 4 + 16;
-}
 
 // ------------------------------------------------ weight packing (FP32 -> BF16)
 // Canonical parameter layout of a layer: W[Cout][Cin][3][3] then b[Cout].
@@ -409,13 +503,16 @@ __global__ void k_bce(const float* __restrict__ prob, const float* __restrict__ 
 // dW[co][ci][ky][kx] += scale * sum_x dZ[y][x][co] * A[y+ky-1][x+kx-1][ci],
 // db[co] += scale * sum_x dZ[y][x][co]; one CTA per image row, a 128-pixel
 // chunk at a time through shared memory, FP32 accumulation, atomics at the end.
-// dZ comes as FP32 (layer 4, one channel) or BF16 [P][dz_stride].
+// A is interleaved [P][16] when CIN_PAD = 16 (the input features) and planar
+// [4][P][8] when CIN_PAD = 32 (activations); dZ comes as FP32 (layer 4, one
+// channel) or as a planar 32-channel BF16 map.
 template <int CIN_PAD, int COUT>
 __global__ void __launch_bounds__(256) k_wgrad(const __nv_bfloat16* __restrict__ A, int cin,
                                                const __nv_bfloat16* __restrict__ dz16,
-                                               const float* __restrict__ dz32, int dz_stride,
-                                               uint32_t W, uint32_t H, float scale,
-                                               float* __restrict__ dW, float* __restrict__ db) {
+                                               const float* __restrict__ dz32, uint32_t W,
+                                               uint32_t H, float scale, float* __restrict__ dW,
+                                               float* __restrict__ db) {
+  const size_t P = (size_t)W * H;
   constexpr int kChunk = 64;
   constexpr int kOut = COUT * CIN_PAD * 9;
   constexpr int kPer = (kOut + 255) / 256;
@@ -435,7 +532,9 @@ __global__ void __launch_bounds__(256) k_wgrad(const __nv_bfloat16* __restrict__
         const int gy = (int)y + dy - 1, gx = (int)x0 + xx - 1;
         float v = 0.f;
         if (c < cin && gy >= 0 && gy < (int)H && gx >= 0 && gx < (int)W)
-          v = __bfloat162float(A[((size_t)gy * W + gx) * CIN_PAD + c]);
+          v = __bfloat162float(CIN_PAD == 32
+                                   ? A[((size_t)(c >> 3) * P + (size_t)gy * W + gx) * 8 + (c & 7)]
+                                   : A[((size_t)gy * W + gx) * CIN_PAD + c]);
         sA[dy][xx][c] = v;
       }
       for (int k = tid; k < kChunk * COUT; k += 256) {
@@ -444,7 +543,7 @@ __global__ void __launch_bounds__(256) k_wgrad(const __nv_bfloat16* __restrict__
         float v = 0.f;
         if (gx < W) {
           const size_t p = (size_t)y * W + gx;
-          v = dz32 ? dz32[p] : __bfloat162float(dz16[p * dz_stride + co]);
+          v = dz32 ? dz32[p] : __bfloat162float(dz16[((size_t)(co >> 3) * P + p) * 8 + (co & 7)]);
         }
         sZ[xx][co] = v;
       }
@@ -514,30 +613,91 @@ int conv_smem_pad() {
 }
 int g_conv_smem_pad = 0;
 
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime
+// (no link-time dependency on libcuda)
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+// Tensor map of a BF16 map for the halo boxes of k_conv_tma. Interleaved
+// [H][W][CIN] is viewed as {8, CIN/8, W, H} with box {8, 1, 130, R+2};
+// planar [CIN/8][H][W][8] as {8, W, H, CIN/8} with box {8, 130, R+2, 1}.
+template <int CIN, bool PLANAR>
+cudaError_t make_halo_map(CUtensorMap* map, const __nv_bfloat16* in, uint32_t W, uint32_t H) {
+  const EncodeTiledFn fn = encode_tiled();
+  if (!fn) return cudaErrorNotSupported;
+  if (reinterpret_cast<uintptr_t>(in) & 15u) return cudaErrorInvalidValue;
+  const cuuint64_t P = (cuuint64_t)W * H;
+  cuuint64_t dims[4], strides[3];
+  cuuint32_t box[4];
+  if (PLANAR) {
+    const cuuint64_t d[4] = {8, W, H, (cuuint64_t)(CIN / 8)};
+    const cuuint64_t st[3] = {16, (cuuint64_t)W * 16, P * 16};
+    const cuuint32_t bx[4] = {8, (cuuint32_t)kHaloW, (cuuint32_t)(kRows + 2), 1};
+    for (int i = 0; i < 4; ++i) { dims[i] = d[i]; box[i] = bx[i]; }
+    for (int i = 0; i < 3; ++i) strides[i] = st[i];
+  } else {
+    const cuuint64_t d[4] = {8, (cuuint64_t)(CIN / 8), W, H};
+    const cuuint64_t st[3] = {16, (cuuint64_t)CIN * 2, (cuuint64_t)W * CIN * 2};
+    const cuuint32_t bx[4] = {8, 1, (cuuint32_t)kHaloW, (cuuint32_t)(kRows + 2)};
+    for (int i = 0; i < 4; ++i) { dims[i] = d[i]; box[i] = bx[i]; }
+    for (int i = 0; i < 3; ++i) strides[i] = st[i];
+  }
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<__nv_bfloat16*>(in), dims,
+                        strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+// in: interleaved [P][16] when CIN = 16, planar [4][P][8] when CIN = 32
 template <int CIN, int COUT, int EPI>
 cudaError_t launch_conv(const __nv_bfloat16* in, const __nv_bfloat16* wpk, const float* bias,
                         const __nv_bfloat16* mask16, __nv_bfloat16* out16, float* out32,
                         uint32_t W, uint32_t H, uint32_t* err, cudaStream_t st) {
-  const size_t smem = conv_smem_bytes<CIN, COUT>() + (size_t)(g_conv_smem_pad + conv_smem_pad());
+  constexpr bool kPlanarIn = CIN == 32;
+  const uint32_t tiles = ((W + kTileM - 1) / kTileM) * ((H + kRows - 1) / kRows);
+  using Lt = ConvTmaLayout<CIN, COUT>;
+  size_t smem = Lt::kSmem + (size_t)(g_conv_smem_pad + conv_smem_pad());
+  // a CTA that takes all 512 TMEM columns must be alone on its SM: ask for
+  // more than half of the SM's shared memory so a second one cannot be placed
+  if (Lt::kTmemCols == 512 && smem < 116u * 1024u) smem = 116u * 1024u;
   static size_t configured = 0;
   if (configured < smem) {
-    cudaError_t e = cudaFuncSetAttribute(k_conv_tc<CIN, COUT, EPI>,
+    cudaError_t e = cudaFuncSetAttribute(k_conv_tma<CIN, COUT, EPI, kPlanarIn>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     configured = smem;
   }
-  // resident CTAs per SM from the shared-memory footprint (227 KB usable, 1 KB
-  // reserved per CTA) and the TMEM columns each CTA allocates
+  CUtensorMap map;
+  cudaError_t e = make_halo_map<CIN, kPlanarIn>(&map, in, W, H);
+  if (e != cudaSuccess) return e;
+  // resident CTAs per SM from the shared-memory footprint (227 KB usable,
+  // 1 KB reserved per CTA) and the TMEM columns (512 per SM) each CTA takes
   int per_sm = (int)((227u * 1024u) / (smem + 1024u));
-  constexpr int kAcc = kRows * COUT;        // TMEM columns a CTA allocates (power of two >= 32)
-  constexpr int kCols = kAcc <= 32 ? 32 : (kAcc <= 64 ? 64 : (kAcc <= 128 ? 128 : 256));
-  if (per_sm > 512 / kCols) per_sm = 512 / kCols;   // 512 TMEM columns per SM
+  if (per_sm > (int)(512 / Lt::kTmemCols)) per_sm = (int)(512 / Lt::kTmemCols);
   if (per_sm < 1) per_sm = 1;
-  if (per_sm > 8) per_sm = 8;
-  const uint32_t tiles = ((W + kTileM - 1) / kTileM) * ((H + kRows - 1) / kRows);
   uint32_t grid = (uint32_t)(num_sms() * per_sm);
   if (grid > tiles) grid = tiles;
-  k_conv_tc<CIN, COUT, EPI><<<grid, 128, smem, st>>>(in, wpk, bias, mask16, out16, out32, W, H, err);
+  k_conv_tma<CIN, COUT, EPI, kPlanarIn><<<grid, kConvTmaThreads, smem, st>>>(
+      map, wpk, bias, mask16, out16, out32, W, H, err);
   return cudaGetLastError();
 }
 }  // namespace
@@ -592,22 +752,22 @@ cudaError_t backward(const __nv_bfloat16* feat16, const float* label, __nv_bfloa
   cudaMemsetAsync(loss_sum, 0, sizeof(float), st);
   k_bce<<<num_sms() * 8, 256, 0, st>>>(prob, label, P, g16, g32, loss_sum);
   // layer 4: dW from g32 (one channel), data gradient into dz_a (masked by act3 > 0)
-  k_wgrad<32, 1><<<rows_grid, 256, 0, st>>>(act3, 32, nullptr, g32, 1, W, H, scale,
+  k_wgrad<32, 1><<<rows_grid, 256, 0, st>>>(act3, 32, nullptr, g32, W, H, scale,
                                              grads + kOffW[3], grads + kOffB[3]);
   cudaError_t e = launch_conv<16, 32, EPI_BWD_MASK_BF16>(g16, wb[3], nullptr, act3, dz_a, nullptr, W, H, err, st);
   if (e != cudaSuccess) return e;
   // layer 3
-  k_wgrad<32, 32><<<rows_grid, 256, 0, st>>>(act2, 32, dz_a, nullptr, 32, W, H, scale,
+  k_wgrad<32, 32><<<rows_grid, 256, 0, st>>>(act2, 32, dz_a, nullptr, W, H, scale,
                                               grads + kOffW[2], grads + kOffB[2]);
   e = launch_conv<32, 32, EPI_BWD_MASK_BF16>(dz_a, wb[2], nullptr, act2, dz_b, nullptr, W, H, err, st);
   if (e != cudaSuccess) return e;
   // layer 2
-  k_wgrad<32, 32><<<rows_grid, 256, 0, st>>>(act1, 32, dz_b, nullptr, 32, W, H, scale,
+  k_wgrad<32, 32><<<rows_grid, 256, 0, st>>>(act1, 32, dz_b, nullptr, W, H, scale,
                                               grads + kOffW[1], grads + kOffB[1]);
   e = launch_conv<32, 32, EPI_BWD_MASK_BF16>(dz_b, wb[1], nullptr, act1, dz_a, nullptr, W, H, err, st);
   if (e != cudaSuccess) return e;
   // layer 1 (no data gradient for the input features)
-  k_wgrad<16, 32><<<rows_grid, 256, 0, st>>>(feat16, 9, dz_a, nullptr, 32, W, H, scale,
+  k_wgrad<16, 32><<<rows_grid, 256, 0, st>>>(feat16, 9, dz_a, nullptr, W, H, scale,
                                               grads + kOffW[0], grads + kOffB[0]);
   return cudaGetLastError();
 }

@@ -49,7 +49,8 @@ constexpr int kMaxTopBytes = 85 * 7 * 16;
 #endif
 // binary traversal prefetches both children of every visited node into L1
 // (prefetch.global.L1) as soon as their indices are known, so a child's
-// fetch that misses L1 overlaps the current node's slab tests
+// fetch that misses L1 overlaps the current node's slab tests; measured 1.87
+// vs 1.53 ms per 1080p blob pair (and 2.00 with 12 blocks per SM): off
 #ifndef RT_PREFETCH
 #define RT_PREFETCH 0
 #endif

@@ -263,6 +263,138 @@ def icosphere(subdiv: int) -> tuple[np.ndarray, np.ndarray]:
     return np.array(verts), np.array(faces, np.int64)
 
 
+def splitmix64_at(seed: int, counter: np.ndarray) -> np.ndarray:
+    """Draw number ``counter`` (0-based) of the SplitMix64 stream seeded with
+    ``seed``, for an array of counters (random access into the stream)."""
+    c = np.asarray(counter, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z = np.uint64(int(seed) & _MASK) + (c + np.uint64(1)) * np.uint64(_GAMMA)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(_MIX1)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(_MIX2)
+        z = z ^ (z >> np.uint64(31))
+    return z
+
+
+def value_noise(seed: int, x: np.ndarray, z: np.ndarray) -> np.ndarray:
+    """2-D value noise in [-1, 1]: lattice values 2U - 1 with U = draw
+    (ix mod 2^20) * 2^20 + (iz mod 2^20) of SplitMix64(seed), blended
+    bilinearly with smoothstep weights 3t^2 - 2t^3."""
+    fx, fz = np.floor(x), np.floor(z)
+    tx, tz = x - fx, z - fz
+    ix, iz = fx.astype(np.int64), fz.astype(np.int64)
+
+    def lat(a, b):
+        k = ((a & 0xFFFFF) << 20) | (b & 0xFFFFF)
+        u = (splitmix64_at(seed, k) >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+        return 2.0 * u - 1.0
+
+    sx, sz = tx * tx * (3.0 - 2.0 * tx), tz * tz * (3.0 - 2.0 * tz)
+    a = lat(ix, iz) + (lat(ix + 1, iz) - lat(ix, iz)) * sx
+    b = lat(ix, iz + 1) + (lat(ix + 1, iz + 1) - lat(ix, iz + 1)) * sx
+    return a + (b - a) * sz
+
+
+def fbm(seed: int, x: np.ndarray, z: np.ndarray, octaves: int = 6, wavelength: float = 250.0):
+    """Fractional Brownian motion: sum over octaves o of 0.5^o times value
+    noise (seed + o) at frequency 2^o / wavelength."""
+    h = np.zeros(np.broadcast(x, z).shape)
+    for o in range(octaves):
+        f = (2.0 ** o) / wavelength
+        h += (0.5 ** o) * value_noise(seed + o, x * f, z * f)
+    return h
+
+
+def config_terrain(seed: int = 5, n_grid: int = 2236, n_spheres: int = 10000, n_lights: int = 8,
+                   W: int = 3840, H: int = 2160, max_depth: int = 4, size: float = 1000.0,
+                   amplitude: float = 60.0) -> Scene:
+    """Procedural terrain: an n_grid x n_grid height grid over [-size, size]^2
+    (2 (n_grid-1)^2 triangles; 9,990,450 for 2236), height amplitude * fbm
+    (6 octaves of value noise, base wavelength size/4, seed), plus n_spheres
+    spheres floating over it and n_lights point lights.
+
+    Cell (i, j) with corners v00 = (i, j), v10 = (i+1, j), v01 = (i, j+1),
+    v11 = (i+1, j+1) gives triangles (v00, v10, v11) and (v00, v11, v01);
+    material 0 (albedo (0.45, 0.5, 0.35), matte) is the terrain. Spheres
+    draw from SplitMix64(seed + 100), 8 uniforms each in this order: x, z
+    (U[-0.9 size, 0.9 size]), radius U[0.5, 4), lift U[0, 20) above the
+    terrain (centre y = height(x, z) + radius + lift), albedo r, g, b, mirror
+    coin (u < 0.3 -> reflectivity 0.7); sphere s has material 1 + s. Lights
+    draw x, z (U[-size, size]) and sit at y = 400 with intensity 1/n_lights.
+    The camera is frame 0 of ``terrain_cameras``.
+    """
+    g = np.linspace(-size, size, n_grid)
+    X, Z = np.meshgrid(g, g, indexing="ij")
+    Y = amplitude * fbm(seed, X, Z, wavelength=size / 4.0)
+    V = np.stack([X, Y, Z], -1).astype(np.float32)
+    i, j = np.meshgrid(np.arange(n_grid - 1), np.arange(n_grid - 1), indexing="ij")
+    i, j = i.ravel(), j.ravel()
+    v00, v10, v01, v11 = V[i, j], V[i + 1, j], V[i, j + 1], V[i + 1, j + 1]
+    tris = np.zeros(2 * len(i), TRIANGLE_DT)
+    tris["v0"][0::2], tris["v1"][0::2], tris["v2"][0::2] = v00, v10, v11
+    tris["v0"][1::2], tris["v1"][1::2], tris["v2"][1::2] = v00, v11, v01
+    tris["material"] = 0
+    mats = np.zeros(1 + n_spheres, MATERIAL_DT)
+    mats["albedo"][0] = (0.45, 0.5, 0.35)
+    sp = np.zeros(n_spheres, SPHERE_DT)
+    if n_spheres:
+        u = SplitMix64(seed + 100).uniform(8 * n_spheres).reshape(n_spheres, 8)
+        x = -0.9 * size + 1.8 * size * u[:, 0]
+        z = -0.9 * size + 1.8 * size * u[:, 1]
+        r = 0.5 + 3.5 * u[:, 2]
+        y = amplitude * fbm(seed, x, z, wavelength=size / 4.0) + r + 20.0 * u[:, 3]
+        sp["center"] = np.stack([x, y, z], -1)
+        sp["radius"] = r
+        sp["material"] = 1 + np.arange(n_spheres)
+        mats["albedo"][1:] = u[:, 4:7]
+        mats["reflectivity"][1:] = np.where(u[:, 7] < 0.3, 0.7, 0.0)
+    lights = np.zeros(n_lights, LIGHT_DT)
+    u = SplitMix64(seed + 200).uniform(2 * n_lights).reshape(n_lights, 2)
+    lights["position"] = np.stack([-size + 2 * size * u[:, 0], np.full(n_lights, 400.0),
+                                   -size + 2 * size * u[:, 1]], -1)
+    lights["intensity"] = 1.0 / n_lights
+    cams = terrain_cameras(seed, 1, size=size, amplitude=amplitude)
+    return Scene(name=f"terrain-{seed}", spheres=sp, triangles=tris, materials=mats, lights=lights,
+                 camera=cams[0], eye_sep=0.065, convergence=60.0, W=W, H=H, max_depth=max_depth)
+
+
+def terrain_cameras(seed: int = 5, n_frames: int = 120, n_keys: int = 8, size: float = 1000.0,
+                    amplitude: float = 60.0, frames_per_loop: int = 120) -> np.ndarray:
+    """Cameras of a flight over the terrain: a closed uniform Catmull-Rom
+    spline through n_keys control points drawn from SplitMix64(seed + 300)
+    (x, z in U[-0.6 size, 0.6 size], y = terrain height + 30 + U[0, 20), 3
+    uniforms per key in that order). Frame f sits at spline parameter
+    n_keys * f / frames_per_loop, raised where needed to 20 above the terrain;
+    it looks along the spline tangent tilted down by 0.3 (before
+    normalisation), up = +y, 60 degree field of view."""
+    u = SplitMix64(seed + 300).uniform(3 * n_keys).reshape(n_keys, 3)
+    kx = -0.6 * size + 1.2 * size * u[:, 0]
+    kz = -0.6 * size + 1.2 * size * u[:, 1]
+    ky = amplitude * fbm(seed, kx, kz, wavelength=size / 4.0) + 30.0 + 20.0 * u[:, 2]
+    K = np.stack([kx, ky, kz], -1)
+
+    def spline(t):
+        k = int(np.floor(t)) % n_keys
+        s_ = t - np.floor(t)
+        p0, p1, p2, p3 = K[(k - 1) % n_keys], K[k], K[(k + 1) % n_keys], K[(k + 2) % n_keys]
+        return 0.5 * ((2 * p1) + (-p0 + p2) * s_ + (2 * p0 - 5 * p1 + 4 * p2 - p3) * s_ ** 2
+                      + (-p0 + 3 * p1 - 3 * p2 + p3) * s_ ** 3)
+
+    cams = np.zeros(n_frames, CAMERA_DT)
+    for f in range(n_frames):
+        t = n_keys * f / frames_per_loop
+        e = spline(t)
+        d = spline(t + 1e-3) - e
+        ground = amplitude * fbm(seed, np.array([e[0]]), np.array([e[2]]), wavelength=size / 4.0)[0]
+        e[1] = max(e[1], ground + 20.0)
+        d = d / np.linalg.norm(d)
+        d[1] -= 0.3
+        cams["eye"][f] = e
+        cams["forward"][f] = d / np.linalg.norm(d)
+        cams["up"][f] = (0.0, 1.0, 0.0)
+        cams["vfov_deg"][f] = 60.0
+    return cams
+
+
 BATCH_RESOLUTIONS = ((640, 360), (1280, 720), (1920, 1080), (3840, 2160))
 
 
