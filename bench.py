@@ -65,6 +65,11 @@ def parse():
                     help="skip the batched-requests measurement")
     ap.add_argument("--batch-only", action="store_true",
                     help="print only the batched-requests measurement as one JSON object")
+    ap.add_argument("--no-sequence", action="store_true",
+                    help="skip the 4K terrain-sequence measurement")
+    ap.add_argument("--sequence-only", action="store_true",
+                    help="print only the 4K terrain-sequence measurement as one JSON object")
+    ap.add_argument("--sequence-frames", type=int, default=120)
     ap.add_argument("--study", action="store_true",
                     help="print one JSON object with the stage split of the small and blob "
                          "scenes, the polyhedra complexity sweep, the L2 / MUFU probes and the "
@@ -275,6 +280,124 @@ def batch_leg(stream, reps=5, warm=2):
             "sequential_images_identical": bool(same)}
 
 
+# ------------------------------------------------------ 4K terrain sequence
+def sequence_leg(stream, n_frames=120, per_launch=8):
+    """A flight over the procedural terrain (9,990,450 triangles + 10,000
+    spheres, 8 lights, depth 4) at 3840x2160 per eye: n_frames stereo frames
+    rendered 8 per launch through one autotuned batch (cameras updated between
+    launches), against the plain one-frame-at-a-time trace of the same frames;
+    learned reprojection on a few frames, with its PSNR against the full
+    trace."""
+    import torch
+
+    from paper_1702_01530_gb300 import capi, scenegen as sg, train_reproj as tr
+    t0 = time.perf_counter()
+    s = sg.config_terrain()
+    cams = sg.terrain_cameras(5, n_frames)
+    gen_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    g = capi.GpuScene(s)
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    W, H, D = s.W, s.H, s.max_depth
+    n_launch = (n_frames + per_launch - 1) // per_launch
+    outs = [torch.empty((2, H, W, 3), dtype=torch.float32, device="cuda") for _ in range(per_launch)]
+    items = [(g.handle, cams[i % n_frames], s.eye_sep, s.convergence, W, H, D, o[0], o[1])
+             for i, o in enumerate(outs)]
+    out = {"workload": f"terrain 2236x2236 grid ({len(s.triangles)} triangles) + "
+                       f"{len(s.spheres)} spheres, 8 lights, depth 4, 3840x2160 per eye, "
+                       f"{n_frames} spline frames, {per_launch} per launch",
+           "scene_generation_s": round(gen_s, 1), "upload_and_bvh_build_s": round(build_s, 3)}
+    b = capi.rt_batch_create(capi.make_requests(items))
+    try:
+        cfg, tuned = capi.rt_batch_autotune(b, reps=1, stream=stream)
+        out["autotune"] = {k: int(cfg[k][0]) for k in cfg.dtype.names}
+        rays = np.zeros(3, np.int64)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        wall0 = time.perf_counter()
+        e0.record(stream)
+        for k in range(n_launch):
+            for i in range(per_launch):
+                f = min(k * per_launch + i, n_frames - 1)
+                capi.rt_batch_set_camera(b, i, cams[f], s.eye_sep, s.convergence)
+            capi.rt_batch_launch(b, stream)
+            r, _, _ = capi.rt_batch_stats(b, per_launch)
+            rays += r.astype(np.int64)
+        e1.record(stream)
+        e1.synchronize()
+        wall = time.perf_counter() - wall0
+        ms = e0.elapsed_time(e1)
+        frames = n_launch * per_launch
+        out["batched"] = {"frames": frames, "ms_total": round(ms, 1), "wall_s": round(wall, 2),
+                          "ms_per_frame": round(ms / frames, 3),
+                          "stereo_frames_per_s": round(frames / (ms * 1e-3), 2),
+                          "rays": [int(x) for x in rays],
+                          "mrays_per_s": round(rays.sum() / (ms * 1e-3) / 1e6, 1)}
+        last = outs[(n_frames - 1) % per_launch].clone()
+    finally:
+        capi.rt_batch_destroy(b)
+    # the plain trace of the same frames, one rt_render_stereo per frame
+    n_plain = n_frames
+    img = torch.empty((2, H, W, 3), dtype=torch.float32, device="cuda")
+
+    def plain():
+        for f in range(n_plain):
+            capi.rt_render_stereo(g.handle, cams[f], s.eye_sep, s.convergence, W, H, D, img[0],
+                                  img[1], stream)
+    ms_plain = _event_ms(plain, stream, reps=1, warm=0)
+    capi.rt_render_stereo(g.handle, cams[n_frames - 1], s.eye_sep, s.convergence, W, H, D, img[0],
+                          img[1], stream)
+    capi.rt_sync_status(g.handle)
+    out["plain"] = {"frames": n_plain, "ms_per_frame": round(ms_plain / n_plain, 3),
+                    "last_frame_identical_to_batched": bool(torch.equal(img, last))}
+    out["batched_speedup_vs_plain"] = round((ms_plain / n_plain) / out["batched"]["ms_per_frame"], 3)
+    # learned reprojection (BF16 network) on every 10th frame, each retrace
+    # threshold; the threshold reported is the largest whose right-eye PSNR
+    # against the full trace is >= 40 dB on every evaluated frame
+    params, _ = tr.load_weights()
+    net = capi.Net(params)
+    try:
+        L = torch.empty((H, W, 3), dtype=torch.float32, device="cuda")
+        R = torch.empty_like(L)
+        n = torch.zeros(1, dtype=torch.int32, device="cuda")
+        rows = []
+        thresholds = (0.9, 0.5, 0.25, 0.1, 0.03, 0.0075)
+        for f in range(0, n_frames, 10):
+            cam = cams[f]
+            full = lambda: capi.rt_render_stereo(g.handle, cam, s.eye_sep, s.convergence, W, H, D,  # noqa: E731
+                                                 img[0], img[1], stream)
+            t_full = _event_ms(full, stream, reps=2, warm=1)
+            for thr in (None,) + thresholds:
+                h = net.handle if thr is not None else None
+                rep = lambda: capi.rt_render_stereo_reproj(g.handle, cam, s.eye_sep, s.convergence,  # noqa: E731
+                                                           W, H, D, h, thr or 0.5, L, R, n, stream)
+                t_rep = _event_ms(rep, stream, reps=2, warm=1)
+                capi.rt_sync_status(g.handle)
+                rows.append({"frame": f, "threshold": thr, "full_ms": t_full, "reproj_ms": t_rep,
+                             "psnr": tr.psnr(R, img[1]), "retraced": int(n.item()) / (W * H)})
+        capi.rt_net_status(net.handle)
+
+        def summary(thr):
+            rs = [r for r in rows if r["threshold"] == thr]
+            return {"threshold": thr, "frames": len(rs),
+                    "speedup": round(sum(r["full_ms"] for r in rs) / sum(r["reproj_ms"] for r in rs), 3),
+                    "right_psnr_db_min": round(min(r["psnr"] for r in rs), 2),
+                    "right_psnr_db_mean": round(float(np.mean([r["psnr"] for r in rs])), 2),
+                    "retraced_fraction_mean": round(float(np.mean([r["retraced"] for r in rs])), 5)}
+        ok = [t for t in thresholds if summary(t)["right_psnr_db_min"] >= 40.0]
+        out["reprojection"] = {
+            "full_ms_per_frame": round(float(np.mean([r["full_ms"] for r in rows if r["threshold"] is None])), 3),
+            "learned_at_40db": summary(max(ok)) if ok else None,
+            "holes_only": summary(None),
+            "per_threshold": [summary(t) for t in thresholds]}
+    finally:
+        net.close()
+        g.close()
+    return out
+
+
 # ---------------------------------------------------------------- our arm
 def run_ours(args, rank, world, local):
     import torch
@@ -440,6 +563,8 @@ def run_ours(args, rank, world, local):
         line["reproj"] = reproj_leg(s)
     if rank == 0 and not args.no_batch:
         line["batch"] = batch_leg(stream)
+    if rank == 0 and not args.no_sequence:
+        line["sequence"] = sequence_leg(stream, n_frames=args.sequence_frames)
     if rank == 0 and not args.no_cpu_baseline:
         cb = cpu_baseline(s, args.cpu_sample)
         line["cpu_baseline"] = {"value": round(cb["mrays_per_s"], 4), "unit": UNIT,
@@ -705,6 +830,14 @@ def main():
     if args.study:
         if rank == 0:
             run_study(args)
+        return
+    if args.sequence_only:
+        if rank == 0:
+            import torch
+
+            from paper_1702_01530_gb300 import build as rtbuild
+            rtbuild.build()
+            print(json.dumps(sequence_leg(torch.cuda.current_stream(), n_frames=args.sequence_frames)))
         return
     if args.batch_only:
         if rank == 0:

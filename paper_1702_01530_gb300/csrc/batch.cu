@@ -69,6 +69,12 @@ struct KBatch {
 
 constexpr uint32_t kNoReq = 0xFFFFFFFFu;
 
+// minimum resident blocks per SM requested from the register allocator for
+// k_render_batch (8: 64 registers, no spills)
+#ifndef RT_BATCH_MIN_BLOCKS
+#define RT_BATCH_MIN_BLOCKS 8
+#endif
+
 __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -112,7 +118,7 @@ __global__ void k_stamp(unsigned long long* t) {
 
 // Shadow queue entry: (origin | pixel) (direction | t_max) (contribution | request)
 // Mirror queue entry: (origin | pixel) (direction | depth) (weight | request)
-__global__ void __launch_bounds__(kThreads, 8) k_render_batch(KBatch kp) {
+__global__ void __launch_bounds__(kThreads, RT_BATCH_MIN_BLOCKS) k_render_batch(KBatch kp) {
   const uint32_t lane = lane_id();
   const uint32_t lt_mask = (1u << lane) - 1u;
   const size_t gwarp = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;

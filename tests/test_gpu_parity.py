@@ -230,6 +230,39 @@ def test_full_size_blob_scene_sampled_parity():
     assert (ref["hit_id"] != capi.RT_MISS_ID).mean() > 0.05
 
 
+def test_terrain_parity_small_grid():
+    # the terrain recipe on a 65 x 65 grid (8,192 triangles) with 40 spheres
+    s = sg.config_terrain(n_grid=65, n_spheres=40, W=96, H=54)
+    ref = oracle.render(s)
+    assert (ref["hit_id"] != capi.RT_MISS_ID).mean() > 0.5
+    check_parity(gpu_render(s), ref, 8, s.max_depth)
+
+
+def test_full_size_terrain_sampled_parity():
+    """9,990,450 triangles + 10,000 spheres at 3840x2160 per eye, depth 4, 8
+    lights: frame 0 of the terrain sequence, rendered as the sequence renders
+    it; the oracle traces a seeded sample of pixels one by one."""
+    s = sg.config_terrain()
+    g = capi.GpuScene(s)
+    try:
+        aux = g.render(aux=True)
+        capi.rt_sync_status(g.handle)
+        rgb = aux["rgb"].cpu().numpy().reshape(-1, 3)
+        hit = aux["hit_id"].cpu().numpy().view(np.uint32).reshape(-1)
+    finally:
+        g.close()
+    rng = np.random.default_rng(2025)
+    pix = rng.choice(2 * s.W * s.H, size=2000, replace=False)
+    ref = oracle.OracleScene(s).render(pixels=pix)
+    err = np.abs(rgb[pix] - ref["rgb"])
+    assert (err <= TOL).all(axis=-1).mean() >= FRAC
+    unfl = ref["flags"] == 0
+    assert unfl.mean() > 0.9 and err[unfl].max() <= MAXERR
+    prim = (ref["flags"] & 1) == 0
+    assert np.array_equal(hit[pix][prim], ref["hit_id"][prim])
+    assert (ref["hit_id"] != capi.RT_MISS_ID).mean() > 0.5
+
+
 # ------------------------------------------------------------ watchdog
 def test_bvh_cycle_stops_at_iteration_bound():
     s = sg.config_blobs(6, n_blobs=2, n_spheres=20, W=32, H=24, max_depth=1)

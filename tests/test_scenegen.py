@@ -63,3 +63,39 @@ def test_small_scene_ranges():
     assert (c[:, 2] >= -15).all() and (c[:, 2] <= -5).all()
     assert set(np.unique(s.materials["reflectivity"][:-1])) <= {0.0, 0.5}
     assert (s.W, s.H, s.max_depth, s.eye_sep, s.convergence) == (320, 240, 3, 0.065, 10.0)
+
+
+def test_value_noise_hits_lattice_values_and_stays_in_range():
+    ix = np.arange(-3, 4, dtype=np.float64)
+    iz = np.full_like(ix, 5.0)
+    v = sg.value_noise(9, ix, iz)
+    k = ((ix.astype(np.int64) & 0xFFFFF) << 20) | (5 & 0xFFFFF)
+    u = (sg.splitmix64_at(9, k) >> np.uint64(11)).astype(np.float64) * 2.0 ** -53
+    assert np.array_equal(v, 2.0 * u - 1.0)
+    x = np.linspace(-7.3, 7.9, 1001)
+    w = sg.value_noise(9, x, 0.37 * x)
+    assert np.abs(w).max() <= 1.0 and np.abs(np.diff(w)).max() < 0.1   # bounded and continuous
+
+
+def test_splitmix64_at_matches_the_stream():
+    a = sg.SplitMix64(77).u64(10)
+    b = sg.splitmix64_at(77, np.arange(10))
+    assert np.array_equal(a, b)
+
+
+def test_terrain_counts_heights_and_cameras():
+    s = sg.config_terrain(n_grid=33, n_spheres=25, W=16, H=9)
+    assert len(s.triangles) == 2 * 32 * 32 and len(s.spheres) == 25 and len(s.lights) == 8
+    y = s.triangles["v0"][:, 1]
+    assert np.abs(y).max() <= 60.0 * (2.0 - 2.0 ** -5)          # amplitude x sum of 0.5^o
+    assert (s.triangles["material"] == 0).all()
+    # spheres float above the terrain surface under their centre
+    c = s.spheres["center"].astype(np.float64)
+    ground = 60.0 * sg.fbm(5, c[:, 0], c[:, 2], wavelength=250.0)
+    assert (c[:, 1] - s.spheres["radius"] >= ground - 1e-3).all()
+    cams = sg.terrain_cameras(5, 12)
+    e = cams["eye"].astype(np.float64)
+    assert (e[:, 1] >= 60.0 * sg.fbm(5, e[:, 0], e[:, 2], wavelength=250.0) + 20.0 - 1e-3).all()
+    assert np.allclose(np.linalg.norm(cams["forward"], axis=1), 1.0, atol=1e-6)
+    again = sg.config_terrain(n_grid=33, n_spheres=25, W=16, H=9)
+    assert again.triangles.tobytes() == s.triangles.tobytes()
