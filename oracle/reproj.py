@@ -16,6 +16,14 @@ definitions in numpy (and PyTorch CPU float64 for the network):
   ReLU, sigmoid; mean binary cross-entropy; gradients by autograd in float64.
   `forward(..., bf16=True)` rounds inputs, weights and hidden activations to
   BF16 where the tensor-core kernels do, so the two can be compared closely.
+* FP8 inference (`forward_fp8`): the first layer as in the BF16 network; its
+  output and every later hidden activation is stored as OCP FP8 E4M3 of the
+  activation times a per-tensor power-of-two scale; layers 2-4 use E4M3
+  weights times a per-output-channel power-of-two scale (`weight_scales_fp8`),
+  undone (exactly) before the bias. E4M3 (`e4m3`): sign, 4 exponent bits
+  with bias 7, 3 mantissa bits, subnormals below 2^-6, largest finite 448,
+  no infinities; conversion rounds to nearest, ties to even mantissa, and
+  saturates to +-448.
 """
 from __future__ import annotations
 
@@ -122,6 +130,62 @@ def forward(params, feat, W, H, bf16=True):
             if bf16:
                 x = _bf16(x)
     return torch.sigmoid(x)[0, 0].numpy()
+
+
+E4M3_MAX = 448.0
+
+
+def e4m3(x):
+    """Round to the nearest OCP FP8 E4M3 value (ties to even), saturating at
+    +-448, in float64. Spacing 2^(e-3) in the binade [2^e, 2^(e+1)) for
+    e >= -6, and 2^-9 below 2^-6 (subnormals)."""
+    x = np.asarray(x, np.float64)
+    a = np.abs(x)
+    _, k = np.frexp(np.where(a > 0, a, 1.0))          # a = m 2^k, m in [0.5, 1)
+    e = np.maximum(k.astype(np.float64) - 1.0, -6.0)  # floor(log2 a), at least -6
+    q = np.exp2(e - 3.0)
+    r = np.minimum(np.round(a / q) * q, E4M3_MAX)      # np.round: half to even
+    return np.copysign(r, x)
+
+
+def pow2_scale(amax):
+    """Largest power of two s with amax * s <= 448 (1 when amax is 0): 2^(k-1)
+    for 448 / amax = m 2^k, m in [0.5, 1)."""
+    amax = np.asarray(amax, np.float64)
+    ratio = np.where(amax > 0, E4M3_MAX / np.where(amax > 0, amax, 1.0), 2.0)
+    _, k = np.frexp(ratio)
+    return np.where(amax > 0, np.ldexp(1.0, k - 1), 1.0)
+
+
+def weight_scales_fp8(params):
+    """Per-output-channel scales of layers 2-4: pow2_scale of the largest
+    |weight| of the channel, taken over the float32 parameters."""
+    layers = unpack(np.asarray(params, np.float32).astype(np.float64))
+    return [pow2_scale(np.abs(w).reshape(w.shape[0], -1).max(axis=1)) for w, _ in layers[1:]]
+
+
+def forward_fp8(params, feat, W, H, act_scales):
+    """Retrace probability (H, W) of the FP8 network, float64 arithmetic.
+    act_scales: scales of the three hidden activations (layer 1-3 outputs)."""
+    import torch
+    import torch.nn.functional as F
+    x = torch.tensor(np.asarray(feat, np.float64)[:, :9].reshape(H, W, 9)).permute(2, 0, 1)[None]
+    x = _bf16(x)
+    layers = unpack(params)
+    wsc = weight_scales_fp8(params)
+    w0, b0 = layers[0]
+    z = F.conv2d(x, _bf16(torch.tensor(w0)), torch.tensor(b0), padding=1)
+    q = torch.tensor(e4m3(torch.relu(z).numpy() * act_scales[0]))     # stored activation
+    for li in (1, 2, 3):
+        w, b = layers[li]
+        s_w = wsc[li - 1]
+        wq = torch.tensor(e4m3(np.asarray(w, np.float32).astype(np.float64) * s_w[:, None, None, None]))
+        acc = F.conv2d(q, wq, None, padding=1)
+        inv = torch.tensor(1.0 / (act_scales[li - 1] * s_w))[None, :, None, None]
+        z = acc * inv + torch.tensor(b)[None, :, None, None]
+        if li < 3:
+            q = torch.tensor(e4m3(torch.relu(z).numpy() * act_scales[li]))
+    return torch.sigmoid(z)[0, 0].numpy()
 
 
 def loss_and_grads(params, feat, label, W, H):

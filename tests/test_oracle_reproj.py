@@ -185,3 +185,91 @@ def test_composite_oracle_definitions():
     assert np.allclose(g[..., 0], 0.299 * 0.25) and np.allclose(g[..., 1:], 1.0, atol=1e-6)
     sbs = post.composite(L, R, 2)
     assert sbs.shape == (2, 6, 3) and (sbs[:, :3] == L).all() and (sbs[:, 3:] == R).all()
+
+
+# ------------------------------------------------------------------- FP8
+def _e4m3_table():
+    """Every finite E4M3 value from the bit layout: sign, 4 exponent bits
+    (bias 7), 3 mantissa bits; exponent 0 is subnormal (M * 2^-9); the
+    pattern S.1111.111 is NaN."""
+    vals = []
+    for b in range(256):
+        sgn, E, M = b >> 7, (b >> 3) & 15, b & 7
+        if E == 15 and M == 7:
+            continue
+        v = M * 2.0 ** -9 if E == 0 else (1 + M / 8) * 2.0 ** (E - 7)
+        vals.append((-v if sgn else v, M))
+    return vals
+
+
+def test_e4m3_table_limits():
+    t = sorted(v for v, _ in _e4m3_table())
+    assert max(t) == 448.0 and min(t) == -448.0
+    assert min(v for v in t if v > 0) == 2.0 ** -9
+    assert np.array_equal(orp.e4m3(np.array(t)), np.array(t))      # representable values are fixed
+
+
+def test_e4m3_rounding_matches_brute_force_nearest_even():
+    table = _e4m3_table()
+    vals = np.array([v for v, _ in table])
+    mant = np.array([m for _, m in table])
+    rng = np.random.default_rng(3)
+    x = np.concatenate([rng.uniform(-500, 500, 400),
+                        np.exp2(rng.uniform(-12, 9.5, 400)) * rng.choice([-1, 1], 400),
+                        (vals[:-1] + vals[1:]) / 2.0])                # exact ties
+    got = orp.e4m3(x)
+    for xi, gi in zip(x, got):
+        if abs(xi) >= 448.0:
+            assert gi == np.copysign(448.0, xi)
+            continue
+        d = np.abs(vals - xi)
+        cand = np.flatnonzero(d == d.min())
+        if len(cand) > 1:                                  # tie: the even mantissa wins
+            cand = [c for c in cand if mant[c] % 2 == 0]
+        assert gi == vals[cand[0]] or (gi == 0 and vals[cand[0]] == 0), (xi, gi, vals[cand])
+
+
+def test_pow2_scale():
+    s = orp.pow2_scale(np.array([1.0, 448.0, 449.0, 3.5, 0.0, 1e-3]))
+    assert s.tolist() == [256.0, 1.0, 0.5, 128.0, 1.0, 262144.0]
+    a = np.random.default_rng(4).uniform(1e-3, 1e3, 100)
+    sc = orp.pow2_scale(a)
+    assert (a * sc <= 448.0).all() and (a * sc * 2 > 448.0).all()
+
+
+def test_fp8_forward_identity_network_closed_form():
+    # layer 1 copies feature 0 to channel 0, layers 2 and 3 pass channel 0
+    # through, layer 4 reads it with bias b: p = sigmoid(x0 + b) exactly when
+    # x0 is representable after scaling, whatever the scales
+    W, H = 11, 7
+    params = np.zeros(sum(ci * co * 9 + co for ci, co in orp.LAYERS), np.float32)
+    k = 0
+    for li, (ci, co) in enumerate(orp.LAYERS):
+        w = np.zeros((co, ci, 3, 3), np.float32)
+        w[0, 0, 1, 1] = 1.0
+        params[k:k + w.size] = w.ravel()
+        k += w.size
+        if li == 3:
+            params[k] = -0.75
+        k += co
+    rng = np.random.default_rng(5)
+    feat = np.zeros((W * H, 16), np.float32)
+    feat[:, 0] = rng.integers(0, 16, W * H) / 8.0
+    feat[:, 1:9] = rng.uniform(-1, 1, (W * H, 8))
+    for scales in ((16.0, 16.0, 16.0), (1.0, 64.0, 0.5)):
+        p = orp.forward_fp8(params, feat, W, H, scales)
+        want = 1.0 / (1.0 + np.exp(-(feat[:, 0].astype(np.float64).reshape(H, W) - 0.75)))
+        assert np.allclose(p, want, rtol=0, atol=1e-15)
+    # dropping the weight scale (a plausible slip) would multiply x0 by 256
+    assert orp.weight_scales_fp8(params)[0][0] == 256.0
+
+
+def test_fp8_forward_close_to_float64_network():
+    W, H = 40, 12
+    params = sg.net_params_he(41)
+    feat = sg.bf16_features_synthetic(42, W, H)
+    ref = orp.forward(params, feat, W, H, bf16=False)
+    x = orp.forward(params, feat, W, H, bf16=True)            # hidden activations' range
+    p8 = orp.forward_fp8(params, feat, W, H, (8.0, 8.0, 8.0))
+    assert np.abs(p8 - ref).max() < 0.1 and np.abs(p8 - ref).mean() < 0.02
+    assert np.abs(x - ref).max() < np.abs(p8 - ref).max()     # FP8 loses more than BF16
