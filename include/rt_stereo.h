@@ -302,6 +302,33 @@ int rt_net_get_params(const rt_net* net, float* host_params);
 int rt_net_status(const rt_net* net, void* cuda_stream);
 
 /*
+ * rt_net_set_fp8 -- run the network's inference in FP8 from now on
+ * (rt_net_forward and rt_render_stereo_reproj; training stays BF16).
+ * Layer 1 keeps BF16 operands; its output and the later hidden activations
+ * are stored as OCP FP8 E4M3 of (activation * act_scales[i]), i = 0, 1, 2
+ * for the outputs of layers 1-3, rounded to nearest even and saturated at
+ * +-448. Layers 2-4 multiply E4M3 operands on the tensor cores
+ * (tcgen05 kind::f8f6f4, FP32 accumulation) with E4M3 weights scaled per
+ * output channel by the largest power of two s with max|w| * s <= 448; the
+ * epilogue undoes both scales exactly before the bias.
+ *   act_scales: host float[3], each a power of two in [2^-30, 2^30] (see
+ *     rt_net_activation_amax for choosing them), or NULL to return to BF16.
+ * Packs the current parameters (call it again after training); synchronises.
+ * Errors: RT_ERR_INVALID_ARG, RT_ERR_CUDA.
+ */
+int rt_net_set_fp8(rt_net* net, const float* act_scales);
+
+/*
+ * rt_net_activation_amax -- run the BF16 network on a feature map (layout as
+ * for rt_net_forward) and return the largest value of each of its three
+ * hidden activations (after ReLU) in host_amax[3]; synchronises cuda_stream.
+ * A natural FP8 scale for activation i is the largest power of two s with
+ * host_amax[i] * s <= 448.
+ */
+int rt_net_activation_amax(rt_net* net, const uint16_t* d_feat16, uint32_t W, uint32_t H,
+                           float* host_amax, void* cuda_stream);
+
+/*
  * rt_net_forward -- retrace probability of every pixel of a W x H feature map.
  *   d_feat16: DEVICE, W*H*16 BF16 (as uint16 bits), row-major pixels,
  *             16-byte aligned (it is read by the tensor-memory-access engine;

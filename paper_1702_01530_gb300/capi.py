@@ -63,6 +63,8 @@ _SIGS = {
     "rt_net_get_params": (ctypes.c_int, [_vp, _vp]),
     "rt_net_status": (ctypes.c_int, [_vp, _vp]),
     "rt_net_forward": (ctypes.c_int, [_vp, _vp, _u32, _u32, _vp, _vp]),
+    "rt_net_set_fp8": (ctypes.c_int, [_vp, _vp]),
+    "rt_net_activation_amax": (ctypes.c_int, [_vp, _vp, _u32, _u32, _vp, _vp]),
     "rt_net_train_step": (ctypes.c_int, [_vp, _vp, _vp, _u32, _u32, _f32, _vp, _vp, _vp]),
     "rt_reproj_warp": (ctypes.c_int, [_vp, _vp, _vp, _vp, _u32, _u32, _f32, _f32, _f32, _vp, _vp,
                                       _vp, _vp, _vp, _vp]),
@@ -383,6 +385,32 @@ def rt_net_status(net, stream=None):
 
 def rt_net_forward(net, feat16, W, H, prob, stream=None):
     _check(lib().rt_net_forward(net, _dptr(feat16), W, H, _dptr(prob), _stream(stream)))
+
+
+def rt_net_set_fp8(net, act_scales):
+    """act_scales: three powers of two, or None to return to BF16 inference."""
+    if act_scales is None:
+        _check(lib().rt_net_set_fp8(net, None))
+        return
+    a = np.ascontiguousarray(act_scales, np.float32)
+    _check(lib().rt_net_set_fp8(net, a.ctypes.data))
+
+
+def rt_net_activation_amax(net, feat16, W, H, stream=None) -> np.ndarray:
+    out = np.zeros(3, np.float32)
+    _check(lib().rt_net_activation_amax(net, _dptr(feat16), W, H, out.ctypes.data, _stream(stream)))
+    return out
+
+
+def fp8_scales(amax) -> np.ndarray:
+    """The largest power of two s with amax * s <= 448, per activation."""
+    amax = np.asarray(amax, np.float64)
+    out = np.ones(len(amax))
+    for i, a in enumerate(amax):
+        if a > 0:
+            _, k = np.frexp(448.0 / a)
+            out[i] = 2.0 ** (k - 1)
+    return out.astype(np.float32)
 
 
 def rt_net_train_step(net, feat16, label, W, H, lr, want_loss=True, grads=None, stream=None):

@@ -35,6 +35,7 @@
 // FP32 master weights.
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -74,7 +75,7 @@ constexpr int kHaloW = kTileM + 2;   // 130
 constexpr int kHaloRows = (kRows + 2) * kHaloW;  // halo pixels per tile
 constexpr uint32_t kWaitBound = 1u << 26;
 
-enum Epi : int { EPI_RELU_BF16 = 0, EPI_SIGMOID_F32 = 1, EPI_BWD_MASK_BF16 = 2 };
+enum Epi : int { EPI_RELU_BF16 = 0, EPI_SIGMOID_F32 = 1, EPI_BWD_MASK_BF16 = 2, EPI_RELU_FP8 = 3 };
 
 // ------------------------------------------------------------ PTX helpers
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -137,6 +138,20 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b
       "{\n\t.reg .pred p;\n\t"
       "setp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+
+// instruction descriptor: kind::f8f6f4, D = F32, A = B = E4M3 (format 0), both K-major
+__host__ __device__ constexpr uint32_t make_idesc_e4m3(int M, int N) {
+  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_e4m3(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
       "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
 }
 
@@ -206,13 +221,13 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
 }
 
 // All MMAs of one tile: per output row ry, D[128 px, COUT] (TMEM columns
-// dtmem + ry*COUT) = sum over taps (dy, dx) and 16-channel K steps of the halo
-// shifted by (ry+dy)*130 + dx pixels times the packed weights of the tap.
-// `plane` is the byte distance between 8-channel chunk planes of the halo.
-template <int CIN, int COUT, uint32_t kPlaneBytes>
+// dtmem + ry*COUT) = sum over taps (dy, dx) and 32-byte K steps (16 BF16 or
+// 32 E4M3 channels) of the halo shifted by (ry+dy)*130 + dx pixels times the
+// packed weights of the tap. kChunks = 16-byte channel chunks per pixel,
+// kPlaneBytes = the distance between chunk planes of the halo.
+template <int kChunks, int COUT, uint32_t kPlaneBytes, bool FP8>
 __device__ __forceinline__ void issue_tile_mmas(uint32_t hbase, uint32_t wbase, uint32_t dtmem,
                                                 uint32_t idesc) {
-  constexpr int kChunks = CIN / 8;
   const uint32_t a_lo = desc_lo(hbase, kPlaneBytes), b_lo = desc_lo(wbase, COUT * 16);
   constexpr uint32_t hi = desc_hi(128u);
 #pragma unroll
@@ -221,22 +236,29 @@ __device__ __forceinline__ void issue_tile_mmas(uint32_t hbase, uint32_t wbase, 
     for (int tap = 0; tap < 9; ++tap) {
       const int dy = tap / 3, dx = tap % 3;
 #pragma unroll
-      for (int ks = 0; ks < CIN / 16; ++ks) {
+      for (int ks = 0; ks < kChunks / 2; ++ks) {
         const uint32_t a_off = (2u * ks) * kPlaneBytes + (uint32_t)((ry + dy) * kHaloW + dx) * 16u;
         const uint32_t b_off = (uint32_t)((tap * kChunks + 2 * ks) * COUT) * 16u;
-        mma_bf16(dtmem + (uint32_t)(ry * COUT), desc_join(a_lo + (a_off >> 4), hi),
-                 desc_join(b_lo + (b_off >> 4), hi), idesc, (tap | ks) ? 1u : 0u);
+        const uint64_t da = desc_join(a_lo + (a_off >> 4), hi), db = desc_join(b_lo + (b_off >> 4), hi);
+        if (FP8) mma_e4m3(dtmem + (uint32_t)(ry * COUT), da, db, idesc, (tap | ks) ? 1u : 0u);
+        else mma_bf16(dtmem + (uint32_t)(ry * COUT), da, db, idesc, (tap | ks) ? 1u : 0u);
       }
     }
   }
 }
 
 // ------------------------------------------------------------ conv kernel
-// in:  BF16, [P][16] interleaved (CIN = 16) or [4][P][8] planar (CIN = 32)
-// wpk: BF16 packed weights, [tap][CIN/8][COUT][8]
-// EPI_RELU_BF16:     out16 (planar [4][P][8]) = relu(acc + bias)
+// in:  BF16 [P][16] interleaved (CIN = 16) or [4][P][8] planar (CIN = 32);
+//      with IN_FP8, E4M3 [2][P][16] planar (CIN = 32)
+// wpk: packed weights, [tap][16-byte chunk][COUT][chunk elements] (BF16 or E4M3)
+// With IN_FP8 the accumulator of channel co is first multiplied by inv[co]
+// (the product of the input's activation scale and the channel's weight
+// scale, inverted: a power of two).
+// EPI_RELU_BF16:     out (BF16 planar [4][P][8]) = relu(acc + bias)
 // EPI_SIGMOID_F32:   out32[P] = sigmoid(acc[0] + bias[0])
-// EPI_BWD_MASK_BF16: out16 (planar) = acc * (mask16 (planar) > 0)
+// EPI_BWD_MASK_BF16: out (BF16 planar) = acc * (mask16 (planar) > 0)
+// EPI_RELU_FP8:      out (E4M3 planar [2][P][16]) = e4m3(relu(acc + bias) * out_scale),
+//                    round to nearest even, saturating at +-448
 //
 // The last warp is the producer: its first lane loads each tile's halo as one
 // TMA box per 8-channel chunk (8 channels x 130 pixels x R+2 rows, zeros
@@ -254,34 +276,37 @@ __device__ __forceinline__ void issue_tile_mmas(uint32_t hbase, uint32_t wbase, 
 // Every wait is bounded; a wait that gives up sets the error word, and before
 // the CTA frees TMEM and exits the producer waits (bounded) for the copies and
 // MMAs it has issued.
-template <int CIN, int COUT>
+template <int CIN, int COUT, bool IN_FP8>
 struct ConvTmaLayout {
-  static constexpr int kChunks = CIN / 8;
+  static constexpr int kElem = IN_FP8 ? 1 : 2;                           // bytes per channel
+  static constexpr int kChunks = CIN * kElem / 16;                       // 16-byte chunks per pixel
   static constexpr uint32_t kBox = (uint32_t)kHaloRows * 16u;          // bytes of one TMA box
   static constexpr uint32_t kPlane = (kBox + 127u) & ~127u;            // chunk plane stride
   static constexpr uint32_t kHalo = ((kChunks * kPlane) + 1023u) & ~1023u;
-  static constexpr uint32_t kW = ((9u * COUT * CIN * 2u) + 127u) & ~127u;
+  static constexpr uint32_t kWBytes = 9u * COUT * CIN * kElem;
+  static constexpr uint32_t kW = (kWBytes + 127u) & ~127u;
   static constexpr uint32_t kAcc = (uint32_t)kRows * COUT;
   static constexpr uint32_t kSet = kAcc <= 32 ? 32 : (kAcc <= 64 ? 64 : (kAcc <= 128 ? 128 : 256));
   static constexpr uint32_t kTmemCols = 2 * kSet;
-  static constexpr size_t kSmem = kStages * (size_t)kHalo + kW + 32 * 4 + 16 * 8 + 16;
+  static constexpr size_t kSmem = kStages * (size_t)kHalo + kW + 64 * 4 + 16 * 8 + 16;
 };
 
-template <int CIN, int COUT, int EPI, bool PLANAR_IN>
+template <int CIN, int COUT, int EPI, bool PLANAR_IN, bool IN_FP8>
 __global__ void __launch_bounds__(kConvTmaThreads, 1)
-    k_conv_tma(const __grid_constant__ CUtensorMap tmap, const __nv_bfloat16* __restrict__ wpk,
-               const float* __restrict__ bias, const __nv_bfloat16* __restrict__ mask16,
-               __nv_bfloat16* __restrict__ out16, float* __restrict__ out32, uint32_t W, uint32_t H,
-               uint32_t* err) {
-  using Lt = ConvTmaLayout<CIN, COUT>;
+    k_conv_tma(const __grid_constant__ CUtensorMap tmap, const void* __restrict__ wpk,
+               const float* __restrict__ bias, const float* __restrict__ inv,
+               float out_scale, const __nv_bfloat16* __restrict__ mask16, void* __restrict__ out,
+               float* __restrict__ out32, uint32_t W, uint32_t H, uint32_t* err) {
+  using Lt = ConvTmaLayout<CIN, COUT, IN_FP8>;
   static_assert(CIN % 16 == 0 && (COUT == 16 || COUT == 32), "shape");
   static_assert(Lt::kTmemCols <= 512, "two accumulator sets must fit in TMEM");
   extern __shared__ __align__(1024) unsigned char smem[];
   static_assert(kStages >= 2 && kStages <= 8, "halo stages");
   unsigned char* halo0 = smem;
   unsigned char* wsm = smem + kStages * Lt::kHalo;
-  float* bsm = reinterpret_cast<float*>(wsm + Lt::kW);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(bsm + 32);
+  float* bsm = reinterpret_cast<float*>(wsm + Lt::kW);    // bias[32], then inv[32]
+  float* ism = bsm + 32;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(bsm + 64);
   uint64_t* halo_full = bars;        // [kStages]
   uint64_t* acc_full = bars + 8;     // [2]
   uint64_t* acc_empty = bars + 10;   // [2]
@@ -293,8 +318,11 @@ __global__ void __launch_bounds__(kConvTmaThreads, 1)
   {
     const uint4* src = reinterpret_cast<const uint4*>(wpk);
     uint4* dst = reinterpret_cast<uint4*>(wsm);
-    for (uint32_t i = tid; i < 9u * COUT * CIN * 2u / 16u; i += blockDim.x) dst[i] = src[i];
-    if (tid < COUT) bsm[tid] = bias ? bias[tid] : 0.f;
+    for (uint32_t i = tid; i < Lt::kWBytes / 16u; i += blockDim.x) dst[i] = src[i];
+    if (tid < COUT) {
+      bsm[tid] = bias ? bias[tid] : 0.f;
+      ism[tid] = inv ? inv[tid] : 1.f;
+    }
   }
   if (tid == 0) {
     for (int b = 0; b < kStages; ++b) mbar_init(halo_full + b, 1);
@@ -314,7 +342,7 @@ __global__ void __launch_bounds__(kConvTmaThreads, 1)
 
   if (warp == kEpiWarps) {
     if (lane == 0) {
-      const uint32_t idesc = make_idesc(kTileM, COUT);
+      const uint32_t idesc = IN_FP8 ? make_idesc_e4m3(kTileM, COUT) : make_idesc(kTileM, COUT);
       const uint32_t wbase = smem_u32(wsm);
       bool issued_halo[kStages], issued_acc[2] = {false, false};
       uint32_t halo_par[kStages], acc_par[2] = {0, 0};     // parity of the last issued use
@@ -330,10 +358,10 @@ __global__ void __launch_bounds__(kConvTmaThreads, 1)
         mbar_arrive_expect_tx(halo_full + b, (uint32_t)Lt::kChunks * Lt::kBox);
 #pragma unroll
         for (int c = 0; c < Lt::kChunks; ++c)
-          if (PLANAR_IN)   // tensor {8, W, H, CIN/8}
+          if (PLANAR_IN)   // tensor {16 B of channels, W, H, chunks}
             tma_load_4d(halo0 + (size_t)b * Lt::kHalo + (size_t)c * Lt::kPlane, &tmap, 0, x0 - 1,
                         y - 1, c, halo_full + b);
-          else             // tensor {8, CIN/8, W, H}
+          else             // tensor {16 B of channels, chunks, W, H}
             tma_load_4d(halo0 + (size_t)b * Lt::kHalo + (size_t)c * Lt::kPlane, &tmap, 0, c, x0 - 1,
                         y - 1, halo_full + b);
         issued_halo[b] = true;
@@ -347,8 +375,8 @@ __global__ void __launch_bounds__(kConvTmaThreads, 1)
         issued_halo[b] = false;
         if (it >= 2 && !mbar_wait(acc_empty + sa, ((it >> 1) - 1) & 1u)) { ok = false; break; }
         fence_after();
-        issue_tile_mmas<CIN, COUT, Lt::kPlane>(smem_u32(halo0 + (size_t)b * Lt::kHalo), wbase,
-                                               tmem + (uint32_t)sa * Lt::kSet, idesc);
+        issue_tile_mmas<Lt::kChunks, COUT, Lt::kPlane, IN_FP8>(
+            smem_u32(halo0 + (size_t)b * Lt::kHalo), wbase, tmem + (uint32_t)sa * Lt::kSet, idesc);
         mma_commit(acc_full + sa);
         issued_acc[sa] = true;
         acc_par[sa] = (it >> 1) & 1u;
@@ -393,8 +421,33 @@ __global__ void __launch_bounds__(kConvTmaThreads, 1)
         if (EPI == EPI_SIGMOID_F32) {
           float v[16];
           tmem_ld16(lane_addr, v);
-          if (valid) out32[p] = 1.f / (1.f + __expf(-(v[0] + bsm[0])));
+          const float z = IN_FP8 ? fmaf(v[0], ism[0], bsm[0]) : v[0] + bsm[0];
+          if (valid) out32[p] = 1.f / (1.f + __expf(-z));
+        } else if (EPI == EPI_RELU_FP8) {
+          uint32_t r[COUT / 16][16];
+#pragma unroll
+          for (int half = 0; half < COUT / 16; ++half) tmem_ld16_nowait(lane_addr + half * 16, r[half]);
+          tmem_wait_ld();
+#pragma unroll
+          for (int half = 0; half < COUT / 16; ++half) {
+            uint32_t packed[4];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              const int c0 = half * 16 + 2 * i, c1 = c0 + 1;
+              const float a0 = __uint_as_float(r[half][2 * i]), a1 = __uint_as_float(r[half][2 * i + 1]);
+              const float y0 = fmaxf(IN_FP8 ? fmaf(a0, ism[c0], bsm[c0]) : a0 + bsm[c0], 0.f);
+              const float y1 = fmaxf(IN_FP8 ? fmaf(a1, ism[c1], bsm[c1]) : a1 + bsm[c1], 0.f);
+              const uint32_t q = __nv_cvt_float2_to_fp8x2(make_float2(y0 * out_scale, y1 * out_scale),
+                                                          __NV_SATFINITE, __NV_E4M3);
+              if (i & 1) packed[i >> 1] |= q << 16; else packed[i >> 1] = q;
+            }
+            // E4M3 planar: plane `half` holds channels 16 half .. 16 half + 15
+            if (valid)
+              *reinterpret_cast<uint4*>(static_cast<uint8_t*>(out) + (half * P + p) * 16) =
+                  make_uint4(packed[0], packed[1], packed[2], packed[3]);
+          }
         } else {
+          __nv_bfloat16* out16 = static_cast<__nv_bfloat16*>(out);
           uint32_t r[COUT / 16][16];                 // all columns of the row, one wait
 #pragma unroll
           for (int half = 0; half < COUT / 16; ++half) tmem_ld16_nowait(lane_addr + half * 16, r[half]);
@@ -474,6 +527,32 @@ __global__ void k_pack_bwd(const float* __restrict__ Wt, int cout, int cin, int 
     if (co < cout && ci < cin) v = Wt[((size_t)co * cin + ci) * 9 + (8 - tap)];
     out[i] = __float2bfloat16_rn(v);
   }
+}
+
+// FP8 forward pack of layers 2-4: [tap][ci/16][co][ci%16] E4M3 of
+// W[co][ci][tap] * scale[co] (round to nearest even, saturating), zero fill
+__global__ void k_pack_fwd_fp8(const float* __restrict__ Wt, int cout, int cin, int cout_pad,
+                               int cin_pad, const float* __restrict__ scale, uint8_t* __restrict__ out) {
+  const int n = 9 * cin_pad * cout_pad;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int e = i % 16, rest = i / 16;
+    const int co = rest % cout_pad, rest2 = rest / cout_pad;
+    const int chunk = rest2 % (cin_pad / 16), tap = rest2 / (cin_pad / 16);
+    const int ci = chunk * 16 + e;
+    float v = 0.f;
+    if (co < cout && ci < cin) v = Wt[((size_t)co * cin + ci) * 9 + tap] * scale[co];
+    out[i] = (uint8_t)__nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
+  }
+}
+
+// largest element of a non-negative BF16 map (ReLU outputs): float bits of
+// non-negative values order like unsigned integers
+__global__ void k_amax(const __nv_bfloat16* __restrict__ a, size_t n, unsigned* __restrict__ out) {
+  float m = 0.f;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    m = fmaxf(m, __bfloat162float(a[i]));
+  for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_down_sync(0xFFFFFFFFu, m, off));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
 }
 
 // ------------------------------------------------------- BCE + d(logit)
@@ -636,58 +715,63 @@ EncodeTiledFn encode_tiled() {
   return fn;
 }
 
-// Tensor map of a BF16 map for the halo boxes of k_conv_tma. Interleaved
-// [H][W][CIN] is viewed as {8, CIN/8, W, H} with box {8, 1, 130, R+2};
-// planar [CIN/8][H][W][8] as {8, W, H, CIN/8} with box {8, 130, R+2, 1}.
-template <int CIN, bool PLANAR>
-cudaError_t make_halo_map(CUtensorMap* map, const __nv_bfloat16* in, uint32_t W, uint32_t H) {
+// Tensor map of a BF16 or E4M3 map for the halo boxes of k_conv_tma; a box
+// is one 16-byte channel chunk of 130 pixels x R+2 rows. Interleaved
+// [H][W][C] is viewed as {chunk elements, chunks, W, H} with box
+// {chunk elements, 1, 130, R+2}; planar [chunks][H][W][chunk elements] as
+// {chunk elements, W, H, chunks} with box {chunk elements, 130, R+2, 1}.
+template <int CIN, bool PLANAR, bool FP8>
+cudaError_t make_halo_map(CUtensorMap* map, const void* in, uint32_t W, uint32_t H) {
   const EncodeTiledFn fn = encode_tiled();
   if (!fn) return cudaErrorNotSupported;
   if (reinterpret_cast<uintptr_t>(in) & 15u) return cudaErrorInvalidValue;
+  constexpr int kElem = FP8 ? 1 : 2, kPer = 16 / kElem, kChunks = CIN / kPer;
   const cuuint64_t P = (cuuint64_t)W * H;
   cuuint64_t dims[4], strides[3];
   cuuint32_t box[4];
   if (PLANAR) {
-    const cuuint64_t d[4] = {8, W, H, (cuuint64_t)(CIN / 8)};
+    const cuuint64_t d[4] = {kPer, W, H, kChunks};
     const cuuint64_t st[3] = {16, (cuuint64_t)W * 16, P * 16};
-    const cuuint32_t bx[4] = {8, (cuuint32_t)kHaloW, (cuuint32_t)(kRows + 2), 1};
+    const cuuint32_t bx[4] = {kPer, (cuuint32_t)kHaloW, (cuuint32_t)(kRows + 2), 1};
     for (int i = 0; i < 4; ++i) { dims[i] = d[i]; box[i] = bx[i]; }
     for (int i = 0; i < 3; ++i) strides[i] = st[i];
   } else {
-    const cuuint64_t d[4] = {8, (cuuint64_t)(CIN / 8), W, H};
-    const cuuint64_t st[3] = {16, (cuuint64_t)CIN * 2, (cuuint64_t)W * CIN * 2};
-    const cuuint32_t bx[4] = {8, 1, (cuuint32_t)kHaloW, (cuuint32_t)(kRows + 2)};
+    const cuuint64_t d[4] = {kPer, kChunks, W, H};
+    const cuuint64_t st[3] = {16, (cuuint64_t)CIN * kElem, (cuuint64_t)W * CIN * kElem};
+    const cuuint32_t bx[4] = {kPer, 1, (cuuint32_t)kHaloW, (cuuint32_t)(kRows + 2)};
     for (int i = 0; i < 4; ++i) { dims[i] = d[i]; box[i] = bx[i]; }
     for (int i = 0; i < 3; ++i) strides[i] = st[i];
   }
   const cuuint32_t estr[4] = {1, 1, 1, 1};
-  const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<__nv_bfloat16*>(in), dims,
-                        strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                        CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  const CUresult r = fn(map, FP8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4,
+                        const_cast<void*>(in), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-// in: interleaved [P][16] when CIN = 16, planar [4][P][8] when CIN = 32
-template <int CIN, int COUT, int EPI>
-cudaError_t launch_conv(const __nv_bfloat16* in, const __nv_bfloat16* wpk, const float* bias,
-                        const __nv_bfloat16* mask16, __nv_bfloat16* out16, float* out32,
+// in: BF16 interleaved [P][16] when CIN = 16, BF16 planar [4][P][8] when
+// CIN = 32, E4M3 planar [2][P][16] with IN_FP8
+template <int CIN, int COUT, int EPI, bool IN_FP8 = false>
+cudaError_t launch_conv(const void* in, const void* wpk, const float* bias, const float* inv,
+                        float out_scale, const __nv_bfloat16* mask16, void* out, float* out32,
                         uint32_t W, uint32_t H, uint32_t* err, cudaStream_t st) {
-  constexpr bool kPlanarIn = CIN == 32;
+  constexpr bool kPlanarIn = IN_FP8 || CIN == 32;
   const uint32_t tiles = ((W + kTileM - 1) / kTileM) * ((H + kRows - 1) / kRows);
-  using Lt = ConvTmaLayout<CIN, COUT>;
+  using Lt = ConvTmaLayout<CIN, COUT, IN_FP8>;
   size_t smem = Lt::kSmem + (size_t)(g_conv_smem_pad + conv_smem_pad());
   // a CTA that takes all 512 TMEM columns must be alone on its SM: ask for
   // more than half of the SM's shared memory so a second one cannot be placed
   if (Lt::kTmemCols == 512 && smem < 116u * 1024u) smem = 116u * 1024u;
   static size_t configured = 0;
   if (configured < smem) {
-    cudaError_t e = cudaFuncSetAttribute(k_conv_tma<CIN, COUT, EPI, kPlanarIn>,
+    cudaError_t e = cudaFuncSetAttribute(k_conv_tma<CIN, COUT, EPI, kPlanarIn, IN_FP8>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     configured = smem;
   }
   CUtensorMap map;
-  cudaError_t e = make_halo_map<CIN, kPlanarIn>(&map, in, W, H);
+  cudaError_t e = make_halo_map<CIN, kPlanarIn, IN_FP8>(&map, in, W, H);
   if (e != cudaSuccess) return e;
   // resident CTAs per SM from the shared-memory footprint (227 KB usable,
   // 1 KB reserved per CTA) and the TMEM columns (512 per SM) each CTA takes
@@ -696,8 +780,8 @@ cudaError_t launch_conv(const __nv_bfloat16* in, const __nv_bfloat16* wpk, const
   if (per_sm < 1) per_sm = 1;
   uint32_t grid = (uint32_t)(num_sms() * per_sm);
   if (grid > tiles) grid = tiles;
-  k_conv_tma<CIN, COUT, EPI, kPlanarIn><<<grid, kConvTmaThreads, smem, st>>>(
-      map, wpk, bias, mask16, out16, out32, W, H, err);
+  k_conv_tma<CIN, COUT, EPI, kPlanarIn, IN_FP8><<<grid, kConvTmaThreads, smem, st>>>(
+      map, wpk, bias, inv, out_scale, mask16, out, out32, W, H, err);
   return cudaGetLastError();
 }
 }  // namespace
@@ -729,13 +813,54 @@ cudaError_t forward(const __nv_bfloat16* feat16, const float* params, __nv_bfloa
                     __nv_bfloat16* act1, __nv_bfloat16* act2, __nv_bfloat16* act3, float* prob,
                     uint32_t W, uint32_t H, uint32_t* err, cudaStream_t st) {
   cudaError_t e;
-  e = launch_conv<16, 32, EPI_RELU_BF16>(feat16, wf[0], params + kOffB[0], nullptr, act1, nullptr, W, H, err, st);
+  e = launch_conv<16, 32, EPI_RELU_BF16>(feat16, wf[0], params + kOffB[0], nullptr, 1.f, nullptr, act1,
+                                         nullptr, W, H, err, st);
   if (e != cudaSuccess) return e;
-  e = launch_conv<32, 32, EPI_RELU_BF16>(act1, wf[1], params + kOffB[1], nullptr, act2, nullptr, W, H, err, st);
+  e = launch_conv<32, 32, EPI_RELU_BF16>(act1, wf[1], params + kOffB[1], nullptr, 1.f, nullptr, act2,
+                                         nullptr, W, H, err, st);
   if (e != cudaSuccess) return e;
-  e = launch_conv<32, 32, EPI_RELU_BF16>(act2, wf[2], params + kOffB[2], nullptr, act3, nullptr, W, H, err, st);
+  e = launch_conv<32, 32, EPI_RELU_BF16>(act2, wf[2], params + kOffB[2], nullptr, 1.f, nullptr, act3,
+                                         nullptr, W, H, err, st);
   if (e != cudaSuccess) return e;
-  return launch_conv<32, 16, EPI_SIGMOID_F32>(act3, wf[3], params + kOffB[3], nullptr, nullptr, prob, W, H, err, st);
+  return launch_conv<32, 16, EPI_SIGMOID_F32>(act3, wf[3], params + kOffB[3], nullptr, 1.f, nullptr,
+                                             nullptr, prob, W, H, err, st);
+}
+
+cudaError_t pack_weights_fp8(const float* params, const float* const scale[3], uint8_t* const w8[3],
+                             cudaStream_t st) {
+  for (int l = 1; l < 4; ++l)
+    k_pack_fwd_fp8<<<64, 256, 0, st>>>(params + kOffW[l], kCout[l], kCin[l], kCoutPad[l], kCinPad[l],
+                                       scale[l - 1], w8[l - 1]);
+  return cudaGetLastError();
+}
+
+size_t packed_fp8_bytes(int l) { return 9ull * kCinPad[l] * kCoutPad[l]; }
+
+// the FP8 network: layer 1 in BF16 with E4M3 output, layers 2-4 on E4M3
+// operands (kind::f8f6f4); act8 buffers hold E4M3 planar [2][P][16]
+cudaError_t forward_fp8(const __nv_bfloat16* feat16, const float* params, __nv_bfloat16* const wf[4],
+                        uint8_t* const w8[3], const float* const inv[3], const float act_scale[3],
+                        uint8_t* act8_1, uint8_t* act8_2, uint8_t* act8_3, float* prob, uint32_t W,
+                        uint32_t H, uint32_t* err, cudaStream_t st) {
+  cudaError_t e;
+  e = launch_conv<16, 32, EPI_RELU_FP8>(feat16, wf[0], params + kOffB[0], nullptr, act_scale[0], nullptr,
+                                        act8_1, nullptr, W, H, err, st);
+  if (e != cudaSuccess) return e;
+  e = launch_conv<32, 32, EPI_RELU_FP8, true>(act8_1, w8[0], params + kOffB[1], inv[0], act_scale[1],
+                                              nullptr, act8_2, nullptr, W, H, err, st);
+  if (e != cudaSuccess) return e;
+  e = launch_conv<32, 32, EPI_RELU_FP8, true>(act8_2, w8[1], params + kOffB[2], inv[1], act_scale[2],
+                                              nullptr, act8_3, nullptr, W, H, err, st);
+  if (e != cudaSuccess) return e;
+  return launch_conv<32, 16, EPI_SIGMOID_F32, true>(act8_3, w8[2], params + kOffB[3], inv[2], 1.f, nullptr,
+                                                    nullptr, prob, W, H, err, st);
+}
+
+cudaError_t activation_amax(const __nv_bfloat16* const act[3], uint64_t P, unsigned* amax3,
+                            cudaStream_t st) {
+  cudaMemsetAsync(amax3, 0, 3 * sizeof(unsigned), st);
+  for (int l = 0; l < 3; ++l) k_amax<<<num_sms() * 4, 256, 0, st>>>(act[l], P * 32, amax3 + l);
+  return cudaGetLastError();
 }
 
 // gradients of the mean BCE loss into grads (same layout as params); the
@@ -754,17 +879,20 @@ cudaError_t backward(const __nv_bfloat16* feat16, const float* label, __nv_bfloa
   // layer 4: dW from g32 (one channel), data gradient into dz_a (masked by act3 > 0)
   k_wgrad<32, 1><<<rows_grid, 256, 0, st>>>(act3, 32, nullptr, g32, W, H, scale,
                                              grads + kOffW[3], grads + kOffB[3]);
-  cudaError_t e = launch_conv<16, 32, EPI_BWD_MASK_BF16>(g16, wb[3], nullptr, act3, dz_a, nullptr, W, H, err, st);
+  cudaError_t e = launch_conv<16, 32, EPI_BWD_MASK_BF16>(g16, wb[3], nullptr, nullptr, 1.f, act3, dz_a,
+                                                         nullptr, W, H, err, st);
   if (e != cudaSuccess) return e;
   // layer 3
   k_wgrad<32, 32><<<rows_grid, 256, 0, st>>>(act2, 32, dz_a, nullptr, W, H, scale,
                                               grads + kOffW[2], grads + kOffB[2]);
-  e = launch_conv<32, 32, EPI_BWD_MASK_BF16>(dz_a, wb[2], nullptr, act2, dz_b, nullptr, W, H, err, st);
+  e = launch_conv<32, 32, EPI_BWD_MASK_BF16>(dz_a, wb[2], nullptr, nullptr, 1.f, act2, dz_b, nullptr,
+                                             W, H, err, st);
   if (e != cudaSuccess) return e;
   // layer 2
   k_wgrad<32, 32><<<rows_grid, 256, 0, st>>>(act1, 32, dz_b, nullptr, W, H, scale,
                                               grads + kOffW[1], grads + kOffB[1]);
-  e = launch_conv<32, 32, EPI_BWD_MASK_BF16>(dz_b, wb[1], nullptr, act1, dz_a, nullptr, W, H, err, st);
+  e = launch_conv<32, 32, EPI_BWD_MASK_BF16>(dz_b, wb[1], nullptr, nullptr, 1.f, act1, dz_a, nullptr,
+                                             W, H, err, st);
   if (e != cudaSuccess) return e;
   // layer 1 (no data gradient for the input features)
   k_wgrad<16, 32><<<rows_grid, 256, 0, st>>>(feat16, 9, dz_a, nullptr, W, H, scale,

@@ -10,6 +10,8 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
+#include <algorithm>
 
 #include "rt_internal.cuh"
 
@@ -35,11 +37,30 @@ struct rt_net {
   __nv_bfloat16* g16 = nullptr;
   float* g32 = nullptr;
   __nv_bfloat16* dz[2] = {};
+  // FP8 inference (rt_net_set_fp8): E4M3 weights of layers 2-4, their
+  // per-output-channel scales and the inverse scales the epilogues apply
+  bool fp8 = false;
+  float act_scale[3] = {1.f, 1.f, 1.f};
+  uint8_t* w8[3] = {};
+  float* wscale[3] = {};
+  float* inv[3] = {};
+  unsigned* amax = nullptr;
 };
 
 namespace {
 
 size_t a256(size_t b) { return (b + 255) & ~size_t(255); }
+
+// the network's forward pass in the precision it is set to (BF16, or FP8
+// after rt_net_set_fp8); act: three scratch maps of W*H*32 BF16 each
+cudaError_t net_forward(rt_net* net, const __nv_bfloat16* feat16, __nv_bfloat16* const act[3],
+                        float* prob, uint32_t W, uint32_t H, cudaStream_t st) {
+  if (!net->fp8)
+    return rt::nn::forward(feat16, net->params, net->wf, act[0], act[1], act[2], prob, W, H, net->err, st);
+  return rt::nn::forward_fp8(feat16, net->params, net->wf, net->w8, net->inv, net->act_scale,
+                             reinterpret_cast<uint8_t*>(act[0]), reinterpret_cast<uint8_t*>(act[1]),
+                             reinterpret_cast<uint8_t*>(act[2]), prob, W, H, net->err, st);
+}
 
 int net_buffers(rt_net* net, uint64_t P) {
   if (net->tb && net->tcap >= P) return RT_OK;
@@ -109,7 +130,9 @@ int rt_net_create(const float* host_params, uint32_t n_params, rt_net** out) {
   const size_t bp = a256((size_t)rt::nn::kParams * 4);
   size_t bw = 0;
   for (int l = 0; l < 4; ++l) bw += a256(rt::nn::packed_fwd_elems(l) * 2) + a256(rt::nn::packed_bwd_elems(l) * 2);
-  cudaError_t e = cudaMalloc(&net->block, 4 * bp + bw + 512);
+  size_t b8 = 256;                                          // amax
+  for (int l = 1; l < 4; ++l) b8 += a256(rt::nn::packed_fp8_bytes(l)) + 2 * 256;
+  cudaError_t e = cudaMalloc(&net->block, 4 * bp + bw + 512 + b8);
   if (e != cudaSuccess) { cudaGetLastError(); delete net; return cuda_fail(e, "network allocation"); }
   char* p = static_cast<char*>(net->block);
   net->params = reinterpret_cast<float*>(p); p += bp;
@@ -121,7 +144,13 @@ int rt_net_create(const float* host_params, uint32_t n_params, rt_net** out) {
     net->wb[l] = reinterpret_cast<__nv_bfloat16*>(p); p += a256(rt::nn::packed_bwd_elems(l) * 2);
   }
   net->loss = reinterpret_cast<float*>(p); p += 256;
-  net->err = reinterpret_cast<uint32_t*>(p);
+  net->err = reinterpret_cast<uint32_t*>(p); p += 256;
+  for (int l = 1; l < 4; ++l) {
+    net->w8[l - 1] = reinterpret_cast<uint8_t*>(p); p += a256(rt::nn::packed_fp8_bytes(l));
+    net->wscale[l - 1] = reinterpret_cast<float*>(p); p += 256;
+    net->inv[l - 1] = reinterpret_cast<float*>(p); p += 256;
+  }
+  net->amax = reinterpret_cast<unsigned*>(p);
   e = cudaMemcpy(net->params, host_params, (size_t)n_params * 4, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(net->m, 0, (size_t)n_params * 4);
   if (e == cudaSuccess) e = cudaMemset(net->v, 0, (size_t)n_params * 4);
@@ -161,15 +190,77 @@ int rt_net_status(const rt_net* net, void* cuda_stream) {
   return fail(RT_ERR_TIMEOUT, "a tensor-core wait reached its bound (bits " + std::to_string(bits) + ")");
 }
 
+int rt_net_set_fp8(rt_net* net, const float* act_scales) {
+  if (!net) return fail(RT_ERR_INVALID_ARG, "net is NULL");
+  if (!act_scales) { net->fp8 = false; return RT_OK; }
+  for (int i = 0; i < 3; ++i) {
+    int k = 0;
+    const double m = std::frexp((double)act_scales[i], &k);
+    if (!(act_scales[i] > 0.f) || !std::isfinite(act_scales[i]) || m != 0.5 || k < -29 || k > 31)
+      return fail(RT_ERR_INVALID_ARG, "activation scales must be powers of two in [2^-30, 2^30]");
+  }
+  std::vector<float> h(rt::nn::kParams);
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(h.data(), net->params, h.size() * 4, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "rt_net_set_fp8: parameter download");
+  // per output channel of layers 2-4: the largest power of two s with
+  // max |w| * s <= 448 (1 for an all-zero channel); inverse scale 1/(a s)
+  static const uint32_t off_w[4] = {0, 2624, 11872, 21120};
+  static const int cout[4] = {32, 32, 32, 1}, cin[4] = {9, 32, 32, 32};
+  for (int l = 1; l < 4; ++l) {
+    float sc[32], iv[32];
+    for (int co = 0; co < 32; ++co) {
+      double amax = 0.0;
+      if (co < cout[l])
+        for (int j = 0; j < cin[l] * 9; ++j)
+          amax = std::max(amax, (double)std::fabs(h[off_w[l] + (size_t)co * cin[l] * 9 + j]));
+      double s = 1.0;
+      if (amax > 0.0) {
+        int k = 0;
+        std::frexp(448.0 / amax, &k);
+        s = std::ldexp(1.0, k - 1);
+      }
+      sc[co] = (float)s;
+      iv[co] = (float)(1.0 / ((double)act_scales[l - 1] * s));
+    }
+    e = cudaMemcpy(net->wscale[l - 1], sc, sizeof sc, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(net->inv[l - 1], iv, sizeof iv, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "rt_net_set_fp8: scale upload");
+  }
+  e = rt::nn::pack_weights_fp8(net->params, net->wscale, net->w8, 0);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(e, "rt_net_set_fp8: weight packing");
+  for (int i = 0; i < 3; ++i) net->act_scale[i] = act_scales[i];
+  net->fp8 = true;
+  return RT_OK;
+}
+
+int rt_net_activation_amax(rt_net* net, const uint16_t* d_feat16, uint32_t W, uint32_t H,
+                           float* host_amax, void* cuda_stream) {
+  if (!net || !d_feat16 || !host_amax || W < 1 || H < 1) return fail(RT_ERR_INVALID_ARG, "bad argument");
+  if ((uint64_t)W * H > (1ull << 30)) return fail(RT_ERR_INVALID_ARG, "image too large");
+  int rc = net_buffers(net, (uint64_t)W * H);
+  if (rc) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  cudaError_t e = rt::nn::forward(reinterpret_cast<const __nv_bfloat16*>(d_feat16), net->params, net->wf,
+                                  net->act[0], net->act[1], net->act[2], net->prob, W, H, net->err, st);
+  if (e == cudaSuccess) e = rt::nn::activation_amax(net->act, (uint64_t)W * H, net->amax, st);
+  unsigned bits[3] = {0, 0, 0};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(bits, net->amax, sizeof bits, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "rt_net_activation_amax");
+  for (int i = 0; i < 3; ++i) std::memcpy(&host_amax[i], &bits[i], 4);
+  return RT_OK;
+}
+
 int rt_net_forward(rt_net* net, const uint16_t* d_feat16, uint32_t W, uint32_t H, float* d_prob,
                    void* cuda_stream) {
   if (!net || !d_feat16 || !d_prob || W < 1 || H < 1) return fail(RT_ERR_INVALID_ARG, "bad argument");
   if ((uint64_t)W * H > (1ull << 30)) return fail(RT_ERR_INVALID_ARG, "image too large");
   int rc = net_buffers(net, (uint64_t)W * H);
   if (rc) return rc;
-  cudaError_t e = rt::nn::forward(reinterpret_cast<const __nv_bfloat16*>(d_feat16), net->params,
-                                  net->wf, net->act[0], net->act[1], net->act[2], d_prob, W, H,
-                                  net->err, static_cast<cudaStream_t>(cuda_stream));
+  cudaError_t e = net_forward(net, reinterpret_cast<const __nv_bfloat16*>(d_feat16), net->act, d_prob,
+                              W, H, static_cast<cudaStream_t>(cuda_stream));
   if (e != cudaSuccess) return cuda_fail(e, "network forward");
   return RT_OK;
 }
@@ -283,8 +374,7 @@ int rt_render_stereo_reproj(const rt_scene* scene, const rt_camera* cam, float e
   rt::profile_mark(sc->ws, rt::ST_WARP, st);
   // 3. retrace probability
   if (e == cudaSuccess && net) {
-    e = rt::nn::forward(rp.feat16, net->params, net->wf, rp.act[0], rp.act[1], rp.act[2], rp.prob,
-                        W, H, net->err, st);
+    e = net_forward(net, rp.feat16, rp.act, rp.prob, W, H, st);
     rt::profile_mark(sc->ws, rt::ST_NET, st);
   }
   // 4. mask = hole or p > threshold, compacted

@@ -189,6 +189,15 @@ cudaError_t backward(const __nv_bfloat16* feat16, const float* label, __nv_bfloa
                      uint32_t W, uint32_t H, uint32_t* err, cudaStream_t st);
 cudaError_t adam(float* params, const float* grads, float* m, float* v, uint32_t n, float lr,
                  uint32_t step, cudaStream_t st);
+size_t packed_fp8_bytes(int l);
+cudaError_t pack_weights_fp8(const float* params, const float* const scale[3], uint8_t* const w8[3],
+                             cudaStream_t st);
+cudaError_t forward_fp8(const __nv_bfloat16* feat16, const float* params, __nv_bfloat16* const wf[4],
+                        uint8_t* const w8[3], const float* const inv[3], const float act_scale[3],
+                        uint8_t* act8_1, uint8_t* act8_2, uint8_t* act8_3, float* prob, uint32_t W,
+                        uint32_t H, uint32_t* err, cudaStream_t st);
+cudaError_t activation_amax(const __nv_bfloat16* const act[3], uint64_t P, unsigned* amax3,
+                            cudaStream_t st);
 }  // namespace nn
 
 }  // namespace rt

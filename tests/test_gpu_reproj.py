@@ -194,3 +194,105 @@ def test_training_pair_labels_cover_holes():
         assert 0.0 < lab.mean().item() < 0.5
     finally:
         g.close()
+
+
+# ------------------------------------------------------------------- FP8
+FP8_SCALES = (16.0, 16.0, 16.0)
+
+
+@pytest.mark.parametrize("W,H", [(300, 7), (1, 3), (333, 20)])
+def test_fp8_forward_matches_fp8_oracle(W, H):
+    """E4M3 activations and weights on kind::f8f6f4 against the float64
+    oracle that rounds to E4M3 at the same points; what remains is FP32 vs
+    FP64 accumulation, which can move a value across an E4M3 rounding
+    boundary (one E4M3 step, 1/16 relative) now and then."""
+    import torch
+    params = sg.net_params_he(11)
+    rng = np.random.default_rng(5)
+    params[2592:2624] = rng.normal(0, 0.1, 32)
+    params[21408] = -0.5
+    feat = sg.bf16_features_synthetic(12, W, H)
+    net = capi.Net(params)
+    try:
+        prob = torch.empty(W * H, dtype=torch.float32, device="cuda")
+        f = _t(feat, torch.bfloat16)
+        capi.rt_net_forward(net.handle, f, W, H, prob)
+        bf16 = prob.clone()
+        capi.rt_net_set_fp8(net.handle, FP8_SCALES)
+        capi.rt_net_forward(net.handle, f, W, H, prob)
+        got = prob.cpu().numpy().reshape(H, W)
+        capi.rt_net_set_fp8(net.handle, None)                 # back to BF16, bit for bit
+        capi.rt_net_forward(net.handle, f, W, H, prob)
+        capi.rt_net_status(net.handle)
+        assert torch.equal(prob, bf16)
+    finally:
+        net.close()
+    ref = orp.forward_fp8(params, feat, W, H, FP8_SCALES)
+    err = np.abs(got - ref)
+    assert err.max() <= 3e-2 and err.mean() <= 1e-3 and (err <= 1e-3).mean() >= 0.98, (err.max(), err.mean())
+    # and its distance from the unrounded float64 network (reported, loose bound)
+    f64 = orp.forward(params, feat, W, H, bf16=False)
+    assert np.abs(got - f64).mean() < 0.02
+
+
+def test_fp8_scales_rejected_unless_powers_of_two():
+    params = sg.net_params_he(3)
+    net = capi.Net(params)
+    try:
+        for bad in ((3.0, 16.0, 16.0), (0.0, 1.0, 1.0), (2.0 ** 40, 1.0, 1.0)):
+            with pytest.raises(capi.RtError):
+                capi.rt_net_set_fp8(net.handle, bad)
+    finally:
+        net.close()
+
+
+def test_activation_amax_matches_bf16_oracle_activations():
+    import torch
+    W, H = 64, 9
+    params = sg.net_params_he(21)
+    feat = sg.bf16_features_synthetic(22, W, H)
+    net = capi.Net(params)
+    try:
+        amax = capi.rt_net_activation_amax(net.handle, _t(feat, torch.bfloat16), W, H)
+    finally:
+        net.close()
+    # the oracle's BF16-emulated hidden activations, layer by layer
+    import torch.nn.functional as F
+    x = torch.tensor(np.asarray(feat, np.float64)[:, :9].reshape(H, W, 9)).permute(2, 0, 1)[None]
+    x = orp._bf16(x)
+    want = []
+    for w, b in orp.unpack(params)[:3]:
+        x = orp._bf16(torch.relu(F.conv2d(x, orp._bf16(torch.tensor(w)), torch.tensor(b), padding=1)))
+        want.append(float(x.max()))
+    assert np.allclose(amax, want, rtol=2e-2), (amax, want)
+    assert (capi.fp8_scales(amax) * amax <= 448).all()
+
+
+def test_reprojection_with_fp8_network_runs_and_matches_bf16_closely():
+    import torch
+    from paper_1702_01530_gb300 import train_reproj as tr
+    s = sg.config_small(4, W=320, H=240)
+    params, thr = tr.load_weights()
+    g = capi.GpuScene(s)
+    net = capi.Net(params)
+    try:
+        full = g.render()["rgb"]
+        outs = {}
+        for mode in ("bf16", "fp8"):
+            if mode == "fp8":
+                capi.rt_net_set_fp8(net.handle, FP8_SCALES)
+            L = torch.empty((s.H, s.W, 3), dtype=torch.float32, device="cuda")
+            R = torch.empty_like(L)
+            n = torch.zeros(1, dtype=torch.int32, device="cuda")
+            capi.rt_render_stereo_reproj(g.handle, s.camera, s.eye_sep, s.convergence, s.W, s.H,
+                                         s.max_depth, net.handle, thr, L, R, n)
+            capi.rt_sync_status(g.handle)
+            capi.rt_net_status(net.handle)
+            outs[mode] = (L, R, int(n.item()))
+        assert torch.equal(outs["fp8"][0], full[0])
+        p = {m: tr.psnr(outs[m][1], full[1]) for m in outs}
+        assert p["fp8"] > p["bf16"] - 1.0, p
+        assert abs(outs["fp8"][2] - outs["bf16"][2]) <= 0.2 * max(outs["bf16"][2], 100)
+    finally:
+        net.close()
+        g.close()
