@@ -199,22 +199,26 @@ def reproj_leg(blob_scene):
     params, thr = tr.load_weights()
     net = capi.Net(params)
     try:
-        out = {"weights": "paper_1702_01530_gb300/weights/reproj_net.bin", "threshold": thr}
+        scales = tr.fp8_calibration_scales(net.handle)
+        out = {"weights": "paper_1702_01530_gb300/weights/reproj_net.bin", "threshold": thr,
+               "fp8_act_scales": [float(x) for x in scales]}
+
+        def entry(a):
+            return {"pair_ms": round(a["ms_reproj"], 4), "speedup": round(a["speedup"], 3),
+                    "right_psnr_db_min": round(a["psnr_min"], 2),
+                    "retraced_fraction": round(a["retraced_mean"], 5)}
         for name, seeds, make in (
                 ("small_scenes_1080p", range(2000, 2003),
                  lambda seed: sg.config_small(seed, W=1920, H=1080)),
                 ("blob_scene_1080p", (blob_scene.name,), lambda _: blob_scene)):
+            capi.rt_net_set_fp8(net.handle, None)
             rows = tr.evaluate(net.handle, seeds, 1920, 1080, thresholds=(thr,), make_scene=make)
+            capi.rt_net_set_fp8(net.handle, scales)
+            rows8 = tr.evaluate(net.handle, seeds, 1920, 1080, thresholds=(thr,), make_scene=make)
             base = tr.evaluate(None, seeds, 1920, 1080, make_scene=make)
             a, b = tr.summarise(rows, thr), tr.summarise(base, None)
-            out[name] = {
-                "full_pair_ms": round(a["ms_full"], 4),
-                "learned": {"pair_ms": round(a["ms_reproj"], 4), "speedup": round(a["speedup"], 3),
-                            "right_psnr_db_min": round(a["psnr_min"], 2),
-                            "retraced_fraction": round(a["retraced_mean"], 5)},
-                "holes_only": {"pair_ms": round(b["ms_reproj"], 4), "speedup": round(b["speedup"], 3),
-                               "right_psnr_db_min": round(b["psnr_min"], 2),
-                               "retraced_fraction": round(b["retraced_mean"], 5)}}
+            out[name] = {"full_pair_ms": round(a["ms_full"], 4), "learned": entry(a),
+                         "learned_fp8": entry(tr.summarise(rows8, thr)), "holes_only": entry(b)}
         return out
     finally:
         net.close()
@@ -387,9 +391,30 @@ def sequence_leg(stream, n_frames=120, per_launch=8):
                     "right_psnr_db_mean": round(float(np.mean([r["psnr"] for r in rs])), 2),
                     "retraced_fraction_mean": round(float(np.mean([r["retraced"] for r in rs])), 5)}
         ok = [t for t in thresholds if summary(t)["right_psnr_db_min"] >= 40.0]
+        best = max(ok) if ok else min(thresholds)
+        # the same network with FP8 inference at that threshold
+        scales = tr.fp8_calibration_scales(net.handle)
+        capi.rt_net_set_fp8(net.handle, scales)
+        for f in range(0, n_frames, 10):
+            cam = cams[f]
+            capi.rt_render_stereo(g.handle, cam, s.eye_sep, s.convergence, W, H, D, img[0], img[1],
+                                  stream)
+            full_ms = next(r["full_ms"] for r in rows if r["frame"] == f and r["threshold"] is None)
+            rep = lambda: capi.rt_render_stereo_reproj(g.handle, cam, s.eye_sep, s.convergence,  # noqa: E731
+                                                       W, H, D, net.handle, best, L, R, n, stream)
+            t_rep = _event_ms(rep, stream, reps=2, warm=1)
+            capi.rt_sync_status(g.handle)
+            rows.append({"frame": f, "threshold": ("fp8", best), "full_ms": full_ms,
+                         "reproj_ms": t_rep, "psnr": tr.psnr(R, img[1]),
+                         "retraced": int(n.item()) / (W * H)})
+        capi.rt_net_status(net.handle)
+        fp8 = summary(("fp8", best))
+        fp8["threshold"] = best
+        fp8["act_scales"] = [float(x) for x in scales]
         out["reprojection"] = {
             "full_ms_per_frame": round(float(np.mean([r["full_ms"] for r in rows if r["threshold"] is None])), 3),
-            "learned_at_40db": summary(max(ok)) if ok else None,
+            "learned_at_40db": summary(best) if ok else None,
+            "learned_fp8_same_threshold": fp8,
             "holes_only": summary(None),
             "per_threshold": [summary(t) for t in thresholds]}
     finally:
