@@ -61,6 +61,8 @@ def parse():
                     help="profiling mode: build the scene, render twice, exit")
     ap.add_argument("--ncu-net", action="store_true",
                     help="profiling mode: run the retrace network on 1080p features twice, exit")
+    ap.add_argument("--fp8", action="store_true",
+                    help="with --ncu-net: FP8 inference (activation scales 128, 64, 32)")
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the batched-requests measurement")
     ap.add_argument("--batch-only", action="store_true",
@@ -663,6 +665,8 @@ def run_ncu_net(args):
     f = torch.from_numpy(sg_features(W, H)).to(torch.bfloat16).cuda()
     prob = torch.empty(W * H, dtype=torch.float32, device="cuda")
     net = capi.Net(params)
+    if args.fp8:
+        capi.rt_net_set_fp8(net.handle, (128.0, 64.0, 32.0))
     for _ in range(2):
         capi.rt_net_forward(net.handle, f, W, H, prob)
     capi.rt_net_status(net.handle)
