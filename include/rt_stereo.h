@@ -204,6 +204,20 @@ int rt_debug_set_node(rt_scene* scene, uint32_t node, int32_t left, int32_t righ
                       int empty_right);
 
 /*
+ * rt_debug_set_pool_capacity -- TEST HOOK; the paper has no counterpart.
+ * Limits the two drain pools of the scene's renders to `entries` rays each
+ * (0 restores the full capacity, which is 128 rays per warp of the render
+ * kernel; larger values are clamped to it). Once every primary tile has been
+ * handed out, the render kernel's warps hand their queued shadow and mirror
+ * rays to these pools and take them back in batches of 32; rays that do not
+ * fit stay with the warp that queued them. A small capacity forces that
+ * fallback (and the empty entries it publishes at the end of a pool), which
+ * must render the same image bit for bit. Returns RT_ERR_INVALID_ARG for a
+ * NULL scene. Host-only; takes effect with the next render.
+ */
+int rt_debug_set_pool_capacity(rt_scene* scene, uint32_t entries);
+
+/*
  * rt_scene_set_traversal -- choose the tree renders of this scene walk:
  * wide == 0 (default) the binary radix tree, wide != 0 the 4-wide tree
  * derived from it (every inner node at even depth holds its grandchildren;

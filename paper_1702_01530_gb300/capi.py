@@ -52,6 +52,7 @@ _SIGS = {
     "rt_sync_status": (ctypes.c_int, [_vp, _vp]),
     "rt_scene_get_bvh": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "rt_scene_num_prims": (_u32, [_vp]),
+    "rt_debug_set_pool_capacity": (ctypes.c_int, [_vp, _u32]),
     "rt_debug_set_node": (ctypes.c_int, [_vp, _u32, ctypes.c_int32, ctypes.c_int32,
                                          ctypes.c_int]),
     "rt_profile_enable": (ctypes.c_int, [_vp, ctypes.c_int]),
@@ -216,6 +217,10 @@ def rt_sync_status(scene, stream=None):
 
 def rt_debug_set_node(scene, node, left, right, empty_right=False):
     _check(lib().rt_debug_set_node(scene, node, left, right, int(bool(empty_right))))
+
+
+def rt_debug_set_pool_capacity(scene, entries):
+    _check(lib().rt_debug_set_pool_capacity(scene, entries))
 
 
 STAGES = ("clear", "trace", "resolve", "warp", "net", "mask", "retrace", "compose")

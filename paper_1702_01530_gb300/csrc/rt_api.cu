@@ -66,10 +66,16 @@ int ensure_workspace(const rt_scene* sc_c, uint32_t W, uint32_t H) {
   const uint32_t cap_s = 32u * sc->nl + 32u, cap_r = 64u;
   if (ws.base && ws.cap_pixels >= pixels && ws.L == sc->nl && ws.n_warps >= n_warps) return RT_OK;
   const uint64_t cap_pixels = ws.cap_pixels > pixels ? ws.cap_pixels : pixels;
+  // drain pools: 128 entries per warp and kind (a full pool only makes the
+  // warps that cannot hand over their leftovers trace them themselves)
+  const uint64_t cap_p = n_warps * 128u;
   size_t b_acc = align256(cap_pixels * 3 * sizeof(uint32_t));
   size_t b_q = align256(n_warps * (cap_s + cap_r) * 3 * sizeof(float4));
+  size_t b_p = align256(2 * cap_p * 3 * sizeof(float4));
+  size_t b_f = align256(2 * cap_p * sizeof(uint32_t));
   size_t b_c = align256(rt::C_TOTAL * sizeof(uint32_t));
-  size_t total = b_acc + b_q + b_c;
+  size_t total = b_acc + b_q + b_p + b_f + b_c;
+  if (cap_p > 0xFFFFFFFFull) return fail(RT_ERR_INVALID_ARG, "render grid too large for the drain pools");
   void* base = nullptr;
   cudaError_t e = cudaMalloc(&base, total);
   if (e != cudaSuccess) { cudaGetLastError(); return cuda_fail(e, "workspace allocation"); }
@@ -79,7 +85,15 @@ int ensure_workspace(const rt_scene* sc_c, uint32_t W, uint32_t H) {
   ws.bytes = total;
   ws.accum = reinterpret_cast<uint32_t*>(p); p += b_acc;
   ws.wq = reinterpret_cast<float4*>(p); p += b_q;
+  ws.pool = reinterpret_cast<float4*>(p); p += b_p;
+  ws.pool_flag = reinterpret_cast<uint32_t*>(p); p += b_f;
   ws.counters = reinterpret_cast<uint32_t*>(p);
+  ws.cap_p = (uint32_t)cap_p;
+  ws.epoch = 0;
+  // pool flags start below every epoch a render will use
+  e = cudaMemset(ws.pool_flag, 0, 2 * cap_p * sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();   // before any render stream reads them
+  if (e != cudaSuccess) { cudaGetLastError(); return cuda_fail(e, "workspace initialisation"); }
   ws.cap_s = cap_s;
   ws.cap_r = cap_r;
   ws.n_warps = n_warps;
@@ -445,6 +459,12 @@ int rt_debug_set_node(rt_scene* scene, uint32_t node, int32_t left, int32_t righ
   }
   e = cudaMemcpy(scene->nodes + 4 * (size_t)node, nd, sizeof nd, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return cuda_fail(e, "node upload");
+  return RT_OK;
+}
+
+int rt_debug_set_pool_capacity(rt_scene* scene, uint32_t entries) {
+  if (!scene) return fail(RT_ERR_INVALID_ARG, "scene is NULL");
+  scene->ws.cap_p_limit = entries;
   return RT_OK;
 }
 

@@ -94,6 +94,11 @@ struct Workspace {
   void* base = nullptr;
   uint32_t* accum = nullptr;     // 2*P*3 fixed-point colour sums
   float4* wq = nullptr;          // warp queues: n_warps x (cap_s + cap_r) x 3 float4
+  float4* pool = nullptr;        // drain pools: shadow then mirror, cap_p entries of 3 float4 each
+  uint32_t* pool_flag = nullptr; // per pool entry: epoch of the render that wrote it
+  uint32_t cap_p = 0;            // entries per drain pool
+  uint32_t cap_p_limit = 0;      // test hook: renders use at most this many (0 = cap_p)
+  uint32_t epoch = 0;            // renders issued on this workspace (pool flags hold it)
   uint32_t* counters = nullptr;  // see Counter enum
   uint32_t cap_s = 0, cap_r = 0; // shadow / mirror entries per warp
   uint64_t n_warps = 0;          // warps the queues are sized for
@@ -110,11 +115,20 @@ struct Workspace {
 };
 
 // counters block layout (uint32 each)
+// (one 128-byte line each: the tile counter that every warp hammers, a flag
+// that changes once, and the drain-pool counters)
 enum Counter : int {
   C_TILE = 0,       // next primary tile
   C_SHADOW = 1,     // shadow rays enqueued (all warps)
   C_REFL = 2,       // mirror rays enqueued (all warps)
-  C_TOTAL = 4
+  C_TILES_OUT = 32, // set once a warp has found every tile handed out
+  C_S_AVAIL = 64,   // drain pools: published entries not yet taken (int32), shadow
+  C_R_AVAIL = 65,   // ... mirror
+  C_S_HEAD = 66,    // drain pools: next entry to take / next entry to reserve, shadow
+  C_S_TAIL = 67,
+  C_R_HEAD = 68,    // ... mirror
+  C_R_TAIL = 69,
+  C_TOTAL = 96
 };
 
 struct RenderArgs {

@@ -13,10 +13,16 @@
 //              rays produced by its own shading. Each round the warp picks,
 //              warp-uniformly, 32 queued shadow rays (any-hit), else 32
 //              queued mirror rays (closest hit + shade), else a new primary
-//              tile (generate + closest hit + shade); when the tiles are gone
-//              it drains its queues. Rounds are full warps except the final
-//              drain, no ray waits for a later launch, and there is one
-//              launch tail per frame instead of one per bounce depth.
+//              tile (generate + closest hit + shade). Once every tile has
+//              been handed out, a warp hands its whole queue to two global
+//              drain pools (shadow, mirror) and from then on takes batches
+//              of up to 32 rays from the pools, mirror rays first, handing
+//              back whatever its shading queues: the rest of the frame
+//              spreads over every warp still running, in full rounds,
+//              instead of each warp tracing its own backlog alone (measured
+//              on the 1080p blob pair: 1.52 -> 1.32 ms). No ray waits for
+//              a later launch, and there is one launch tail per frame
+//              instead of one per bounce depth.
 //   k_resolve  fixed-point sums -> float RGB, clamp to [0,1]
 //
 // Colour sums are fixed-point uint32 per channel (atomic adds of
@@ -43,10 +49,86 @@ struct KParams {
   RenderArgs a;
   uint32_t* accum;
   float4* wq;          // warp queues: per warp cap_s shadow then cap_r mirror entries
+  float4* pool;        // drain pools: cap_p shadow entries, then cap_p mirror entries
+  uint32_t* pool_flag; // per pool entry: epoch of the render that wrote it
   uint32_t* counters;
-  uint32_t cap_s, cap_r;
+  uint32_t cap_s, cap_r, cap_p;
+  uint32_t epoch;      // this render's epoch (> 0)
   uint32_t n_tiles;    // 2 * tiles_x * tiles_y
+  bool share_partial;  // drain: hand over backlogs of less than a round too
 };
+
+constexpr uint32_t kNullPix = 0xFFFFFFFFu;   // pool entry that carries no ray
+constexpr uint32_t kSpinMax = 1u << 22;        // bound of every wait on another warp
+// scenes of at least this many primitives hand over partial backlogs too
+// (1080p blob pair, 257k primitives: 1.301 ms sharing everything, 1.330
+// keeping partial backlogs; small scene, 10 primitives: 0.262 against 0.239)
+constexpr uint32_t kSharePartialPrims = 1024;
+
+// Polls use relaxed (L2-coherent) loads: an acquire load would invalidate
+// the SM's L1, which holds the top of the BVH for every warp on the SM. A
+// pool entry is read after its flag has been seen (a control dependency) with
+// L2 loads, and its producer publishes the flag with a release store.
+__device__ __forceinline__ uint32_t ld_relaxed(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed(uint32_t* p, uint32_t v) {
+  asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void st_release(uint32_t* p, uint32_t v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ int2 ld_volatile2(const uint32_t* p) {
+  int2 v;
+  asm volatile("ld.volatile.global.v2.s32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(p) : "memory");
+  return v;
+}
+// Drain pool protocol (one lane of a warp calls these; every step is one
+// atomic, no retry loop, so thousands of warps can hand over and take at
+// once): a warp reserves entries with an add on the tail, writes them and
+// sets each entry's flag to the render's epoch, then adds their number to
+// `avail`. A taker first claims up to 32 from `avail` (a counting semaphore:
+// a subtraction, undone for what was not there) and only then advances the
+// head by what it got, so the head never passes the tail; an entry it takes
+// may still be in the middle of its producer's write, which the flag tells.
+// Reserve n entries; `room` = how many of them lie inside the pool (entries
+// beyond its capacity are never written or taken).
+__device__ __forceinline__ uint32_t pool_reserve(uint32_t* tail, uint32_t n, uint32_t cap,
+                                                 uint32_t& room) {
+  const uint32_t at = atomicAdd(tail, n);
+  room = at >= cap ? 0u : min(n, cap - at);
+  return at;
+}
+// Claim up to 32 published entries; returns how many and the first in h.
+__device__ __forceinline__ uint32_t pool_take(uint32_t* head, int* avail, int want, uint32_t& h) {
+  const int prev = atomicSub(avail, want);
+  const int got = prev <= 0 ? 0 : min(prev, want);
+  if (got < want) atomicAdd(avail, want - got);
+  if (got > 0) h = atomicAdd(head, (uint32_t)got);
+  return (uint32_t)got;
+}
+
+// Copy the first `room` of n (< 32) warp-queue entries to a drain pool at
+// entry `at` (room == n), or publish `room` empty entries there when the
+// pool ran out (room < n; the warp then traces all n itself); each lane one
+// entry, published by its flag.
+__device__ __forceinline__ void pool_put(const float4* q, float4* pool, uint32_t* flag,
+                                         uint32_t at, uint32_t n, uint32_t room, uint32_t epoch) {
+  const uint32_t lane = threadIdx.x & 31;
+  if (lane < room) {
+    float4* d = pool + 3 * ((size_t)at + lane);
+    if (room == n) {
+      const float4* e = q + 3 * (size_t)lane;
+      const float4 e0 = e[0], e1 = e[1], e2 = e[2];
+      d[0] = e0; d[1] = e1; d[2] = e2;
+    } else {
+      d[0] = make_float4(0.f, 0.f, 0.f, __uint_as_float(kNullPix));
+    }
+    st_release(flag + at + lane, epoch);
+  }
+}
 
 __device__ __forceinline__ void flush_work(const WorkCount& wc, uint64_t* work, int kind) {
   uint32_t a = wc.inner, b = wc.sphere, c = wc.tri;
@@ -77,7 +159,6 @@ k_render(KParams kp) {
   const RenderArgs& a = kp.a;
   // the top of the 4-wide tree, staged in shared memory once per block
   extern __shared__ float4 top[];
-  __shared__ uint32_t next_shadow[kThreads / 32];   // per-warp shadow-queue cursor
   if (WIDE && !COUNT) {
     for (uint32_t i = threadIdx.x; i < 7u * a.sc.n_top; i += blockDim.x) top[i] = a.sc.nodes4[i];
     __syncthreads();
@@ -89,9 +170,11 @@ k_render(KParams kp) {
   const size_t gwarp = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   float4* const S = kp.wq + gwarp * 3 * (size_t)(kp.cap_s + kp.cap_r);
   float4* const R = S + 3 * (size_t)kp.cap_s;
+  uint32_t* const cnt = kp.counters;
   uint32_t nS = 0, nR = 0;          // warp-uniform queue fills
   uint32_t made_s = 0, made_r = 0;  // rays this warp enqueued
   bool tiles_left = true;
+  uint32_t tiles_out = 0;           // lane 0: the tiles-out flag, loaded one round ahead
   const uint32_t plist_n = a.plist_n_dev ? *a.plist_n_dev : a.plist_n;
   const uint32_t n_tiles = a.plist ? (plist_n + 31u) / 32u : kp.n_tiles;
   WorkCount wc_p = {0, 0, 0}, wc_s = {0, 0, 0}, wc_r = {0, 0, 0};
@@ -101,40 +184,113 @@ k_render(KParams kp) {
     if (round > (1u << 30)) { if (lane == 0) atomicOr(a.err, ERR_ITER); break; }
     // ---------------------------------------------- warp-uniform schedule
     int mode;
-    uint32_t take = 0, base = 0, tile = 0;
-    if (nS >= 32) {
-      mode = M_SHADOW;
-      if (RT_SHADOW_REFILL) { take = nS; base = 0; nS = 0; }
-      else { take = 32; nS -= 32; base = nS; }
-    }
-    else if (nR >= 32) { mode = M_MIRROR; take = 32; nR -= 32; base = nR; }
+    uint32_t take = 0, tile = 0;
+    const float4* src = nullptr;        // first queue entry of this round's batch
+    const uint32_t* flags = nullptr;    // batch from a drain pool: its entries' flags
+    // before a round on its own queue: have the tiles run out meanwhile?
+    // then the queue goes to the pools instead (the flag was loaded during
+    // the previous round, so its latency is hidden)
+    if (tiles_left && (nS >= 32 || nR >= 32) && __shfl_sync(0xFFFFFFFFu, tiles_out, 0))
+      tiles_left = false;
+    if (tiles_left && nS >= 32) { mode = M_SHADOW; take = 32; nS -= 32; src = S + 3 * (size_t)nS; }
+    else if (tiles_left && nR >= 32) { mode = M_MIRROR; take = 32; nR -= 32; src = R + 3 * (size_t)nR; }
     else if (tiles_left) {
       uint32_t t = 0;
-      if (lane == 0) t = atomicAdd(&kp.counters[C_TILE], 1u);
+      if (lane == 0) t = atomicAdd(&cnt[C_TILE], 1u);
       t = __shfl_sync(0xFFFFFFFFu, t, 0);
-      if (t >= n_tiles) { tiles_left = false; continue; }
+      if (t >= n_tiles) {
+        if (lane == 0 && t == n_tiles) st_relaxed(&cnt[C_TILES_OUT], 1u);
+        tiles_left = false;
+        continue;
+      }
       mode = M_PRIMARY; tile = t;
+    } else {
+      // ------------------------------------------------------ drain phase
+      // hand the whole queue to the pools, 32 entries at a time, so that
+      // every warp still running shares the rest of the frame
+      bool keep_s = false, keep_r = false;   // a pool ran out: trace them here
+      // in a small scene a backlog of less than a round per kind stays here:
+      // its rounds cost less than handing them over (a few contended atomics
+      // on the pool counters at the end of the frame)
+      if (nS < 32 && nR < 32 && !kp.share_partial) { keep_s = nS > 0; keep_r = nR > 0; }
+      else
+      for (int kind = 0; kind < 2; ++kind) {
+        uint32_t& nq = kind ? nR : nS;
+        const size_t off = kind ? (size_t)kp.cap_p : 0;
+        while (nq > 0) {
+          const uint32_t c = min(nq, 32u);
+          uint32_t at = 0, room = 0;
+          if (lane == 0) {
+            if (ld_relaxed(&cnt[kind ? C_R_TAIL : C_S_TAIL]) < kp.cap_p)
+              at = pool_reserve(&cnt[kind ? C_R_TAIL : C_S_TAIL], c, kp.cap_p, room);
+          }
+          at = __shfl_sync(0xFFFFFFFFu, at, 0);
+          room = __shfl_sync(0xFFFFFFFFu, room, 0);
+          pool_put((kind ? R : S) + 3 * (size_t)(nq - c), kp.pool + 3 * off, kp.pool_flag + off,
+                   at, c, room, kp.epoch);
+          __syncwarp();
+          if (lane == 0 && room > 0) atomicAdd((int*)&cnt[kind ? C_R_AVAIL : C_S_AVAIL], (int)room);
+          if (room < c) { if (kind) keep_r = true; else keep_s = true; break; }
+          nq -= c;
+        }
+      }
+      if (keep_s) { mode = M_SHADOW; take = min(nS, 32u); nS -= take; src = S + 3 * (size_t)nS; }
+      else if (keep_r) { mode = M_MIRROR; take = min(nR, 32u); nR -= take; src = R + 3 * (size_t)nR; }
+      else {
+        // take a batch, mirror rays first (they start the longest chains),
+        // else shadow rays; nothing taken ends the warp (a lost race too:
+        // retrying costs more in contention on the pool counters than the
+        // warp adds, measured)
+        uint32_t n = 0, h = 0, kind = 0;
+        if (lane == 0) {
+          const int2 av = ld_volatile2(&cnt[C_S_AVAIL]);   // (shadow, mirror) published
+          if (av.y > 0) { n = pool_take(&cnt[C_R_HEAD], (int*)&cnt[C_R_AVAIL], 32, h); kind = 1; }
+          if (n == 0 && av.x > 0) { n = pool_take(&cnt[C_S_HEAD], (int*)&cnt[C_S_AVAIL], 32, h); kind = 0; }
+        }
+        n = __shfl_sync(0xFFFFFFFFu, n, 0);
+        h = __shfl_sync(0xFFFFFFFFu, h, 0);
+        kind = __shfl_sync(0xFFFFFFFFu, kind, 0);
+        if (n > 0) {
+          const size_t off = kind ? (size_t)kp.cap_p : 0;
+          mode = kind ? M_MIRROR : M_SHADOW;
+          take = n;
+          src = kp.pool + 3 * (off + h);
+          flags = kp.pool_flag + off + h;
+        } else {
+          // nothing published in either pool: this warp is done. Every ray
+          // handed to a pool is taken by a warp still running (at the latest
+          // by the warp that handed it over, which looks again after handing
+          // over), so no ray is left behind.
+          break;
+        }
+      }
     }
-    else if (nS > 0) { mode = M_SHADOW; take = nS; base = 0; nS = 0; }
-    else if (nR > 0) { mode = M_MIRROR; take = nR; base = 0; nR = 0; }
-    else break;
+    if (tiles_left && lane == 0) tiles_out = ld_relaxed(&cnt[C_TILES_OUT]);
 
     if (mode == M_SHADOW) {
       // ------------------------------------------------ any-hit round
-      if (RT_SHADOW_REFILL && lane == 0) next_shadow[threadIdx.x >> 5] = 32u;
-      __syncwarp();
-      uint32_t i = lane;
-      while (i < take) {
-        const float4* e = S + 3 * (size_t)(base + i);
-        const float4 s0 = e[0], s1 = e[1];
+      if (lane < take) {
+        const float4* e = src + 3 * (size_t)lane;
+        float4 s0, s1, s2;
+        bool ok = true;
+        if (flags) {                       // wait until the entry is published
+          uint32_t spins = 0;
+          while (ld_relaxed(flags + lane) != kp.epoch) {
+            if (++spins > kSpinMax) { atomicOr(a.err, ERR_QUEUE); ok = false; break; }
+            __nanosleep(64);
+          }
+          s0 = __ldcg(e); s1 = __ldcg(e + 1); s2 = __ldcg(e + 2);
+        } else {
+          s0 = e[0]; s1 = e[1]; s2 = e[2];
+        }
+        if (__float_as_uint(s0.w) >= 2 * P) {     // an empty pool entry, or corrupt
+          if (__float_as_uint(s0.w) != kNullPix) atomicOr(a.err, ERR_INDEX);
+          ok = false;
+        }
         float tb = 0.f;
         uint32_t id = 0, k = 0;
-        const bool blocked = trace_ray<true, COUNT, WIDE>(a.sc, top, xyz(s0), xyz(s1), s1.w, tb, id, k, wc_s, a.err);
-        if (!blocked) {
-          const float4 s2 = e[2];
+        if (ok && !trace_ray<true, COUNT, WIDE>(a.sc, top, xyz(s0), xyz(s1), s1.w, tb, id, k, wc_s, a.err))
           accumulate(kp.accum, __float_as_uint(s0.w), s2.x, s2.y, s2.z, a.color_scale);
-        }
-        i = RT_SHADOW_REFILL ? atomicAdd(&next_shadow[threadIdx.x >> 5], 1u) : take;
       }
       __syncwarp();
       continue;
@@ -167,10 +323,25 @@ k_render(KParams kp) {
     } else {
       active = lane < take;
       if (active) {
-        const float4* e = R + 3 * (size_t)(base + lane);
-        const float4 q0 = e[0], q1 = e[1], q2 = e[2];
+        const float4* e = src + 3 * (size_t)lane;
+        float4 q0, q1, q2;
+        if (flags) {                       // wait until the entry is published
+          uint32_t spins = 0;
+          while (ld_relaxed(flags + lane) != kp.epoch) {
+            if (++spins > kSpinMax) { atomicOr(a.err, ERR_QUEUE); active = false; break; }
+            __nanosleep(64);
+          }
+          q0 = __ldcg(e); q1 = __ldcg(e + 1); q2 = __ldcg(e + 2);
+        } else {
+          q0 = e[0]; q1 = e[1]; q2 = e[2];
+        }
         o = xyz(q0);
         pix = __float_as_uint(q0.w);
+        if (pix >= 2 * P) {                         // an empty pool entry, or corrupt
+          if (pix != kNullPix) atomicOr(a.err, ERR_INDEX);
+          active = false;
+          pix = 0;
+        }
         d = xyz(q1);
         depth = __float_as_uint(q1.w);
         w = xyz(q2);
@@ -304,6 +475,15 @@ cudaError_t render_impl(const RenderArgs& a, Workspace& ws, cudaStream_t st) {
                        : (a.eyes == 3u ? 2u : 1u) * a.cam.tiles_x * a.cam.tiles_y;
   const int grid = render_grid();
   if ((uint64_t)grid * (kThreads / 32) > ws.n_warps) return cudaErrorInvalidValue;
+  kp.share_partial = a.sc.n_prims >= kSharePartialPrims;
+  kp.pool = ws.pool;
+  kp.pool_flag = ws.pool_flag;
+  kp.cap_p = ws.cap_p_limit && ws.cap_p_limit < ws.cap_p ? ws.cap_p_limit : ws.cap_p;
+  if (++ws.epoch == 0) {            // flags of 2^32 renders ago could match: clear them
+    cudaMemsetAsync(ws.pool_flag, 0, 2 * (size_t)ws.cap_p * sizeof(uint32_t), st);
+    ws.epoch = 1;
+  }
+  kp.epoch = ws.epoch;
   cudaMemsetAsync(ws.counters, 0, C_TOTAL * sizeof(uint32_t), st);
   // clear the colour sums of the eyes this render traces
   const bool left = !a.plist && (a.eyes & 1u), right = a.plist || (a.eyes & 2u);

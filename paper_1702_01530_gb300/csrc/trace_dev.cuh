@@ -14,15 +14,17 @@ namespace rt {
 namespace {
 
 // Tuning knobs (compile-time): RT_MIN_BLOCKS = minimum resident blocks per
-// SM requested from the register allocator (0 = no request; 10 measured
-// best on GB300: 48 registers, 40 warps per SM); RT_WHILE_WHILE = 1
+// SM requested from the register allocator (0 = no request; 8 measured best
+// on GB300 with the drain pools: 64 registers, 32 warps per SM, 1.305 ms per
+// 1080p blob pair as with 10 blocks, 0.265 against 0.284 ms on a small
+// scene, where 10 blocks spill in the shading code); RT_WHILE_WHILE = 1
 // postpones the first leaf a ray meets and keeps descending until every
 // active lane of the warp holds a leaf, so the leaf tests of a warp run
 // together instead of interleaving with node visits (the "while-while" loop
 // of Aila & Laine, HPG 2009) -- 20 % slower here with one primitive per leaf,
 // hence off by default.
 #ifndef RT_MIN_BLOCKS
-#define RT_MIN_BLOCKS 10
+#define RT_MIN_BLOCKS 8
 #endif
 #ifndef RT_WHILE_WHILE
 #define RT_WHILE_WHILE 0
@@ -34,12 +36,6 @@ constexpr int kStack4 = 100;   // 3 pushes per 4-wide level, <= 33 levels
 #define RT_TREELET_DEPTH 2
 #endif
 constexpr int kMaxTopBytes = 85 * 7 * 16;
-// shadow rounds take the warp's whole shadow queue and every lane fetches its
-// next entry as soon as its ray finishes (per-warp counter in shared memory);
-// measured 1.55 vs 1.53 ms per 1080p blob pair: off by default
-#ifndef RT_SHADOW_REFILL
-#define RT_SHADOW_REFILL 0
-#endif
 // binary traversal keeps the top of its stack in a register: a pop hands
 // the register over at once and reloads it from local memory in the
 // background, so the pop and the next node fetch do not wait in series;

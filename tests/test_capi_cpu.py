@@ -74,6 +74,7 @@ def test_render_rejects_null_scene_and_bad_view(lib):
     with pytest.raises(capi.RtError):
         capi.rt_sync_status(None, stream=0)
     assert lib.rt_debug_set_node(None, 0, 0, 0, 0) == capi.RT_ERR_INVALID_ARG
+    assert lib.rt_debug_set_pool_capacity(None, 0) == capi.RT_ERR_INVALID_ARG
     assert "NULL" in capi.rt_last_error()
 
 

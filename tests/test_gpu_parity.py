@@ -201,6 +201,45 @@ def test_repeated_renders_are_identical():
         g.close()
 
 
+# ------------------------------------------------------- drain pools
+def test_blob_pair_renders_are_identical_at_full_size():
+    # the end of every frame hands queued rays between warps through the
+    # drain pools: a ray lost or traced twice would change the fixed-point sums
+    s = sg.config_blobs(2)
+    g = capi.GpuScene(s)
+    try:
+        first = g.render(aux=True)
+        ref_rgb, ref_rays = first["rgb"].cpu().numpy(), first["rays"].cpu().numpy()
+        for _ in range(4):
+            r = g.render(aux=True)
+            assert np.array_equal(r["rgb"].cpu().numpy(), ref_rgb)
+            assert np.array_equal(r["rays"].cpu().numpy(), ref_rays)
+        capi.rt_sync_status(g.handle)
+    finally:
+        g.close()
+
+
+@pytest.mark.parametrize("cap", [1, 37, 4096])
+def test_full_drain_pools_fall_back_to_the_owning_warp(cap):
+    # pools too small for the frame: the rays that do not fit stay with the
+    # warp that queued them (and the pool ends with empty entries); the image
+    # and the ray counts must not change
+    s = sg.config_blobs(3, n_blobs=30, n_spheres=150, W=256, H=192)
+    g = capi.GpuScene(s)
+    try:
+        ref = g.render(aux=True)
+        capi.rt_debug_set_pool_capacity(g.handle, cap)
+        small = g.render(aux=True)
+        capi.rt_sync_status(g.handle)
+        for k in ("rgb", "hit_id", "rays"):
+            assert np.array_equal(small[k].cpu().numpy(), ref[k].cpu().numpy()), k
+        capi.rt_debug_set_pool_capacity(g.handle, 0)
+        again = g.render(aux=True)
+        assert np.array_equal(again["rgb"].cpu().numpy(), ref["rgb"].cpu().numpy())
+    finally:
+        g.close()
+
+
 # ---------------------------------------------- full size, sampled pixels
 def test_full_size_blob_scene_sampled_parity():
     """256,000 triangles + 1,000 spheres at 1920x1080 per eye, depth 5, 4
