@@ -224,7 +224,7 @@ int rt_debug_set_pool_capacity(rt_scene* scene, uint32_t entries);
  * its top two levels are staged in shared memory). Both hold the same leaves
  * and boxes and give the same images bit for bit (Table 1 of the paper: BVH
  * trees). On the 256k-triangle blob scene at 1080p the binary walk is faster
- * on GB300 (1.52 vs 1.63 ms per pair), hence the default. The instrumented
+ * on GB300 (1.29 vs 1.41 ms per pair), hence the default. The instrumented
  * work counts of rt_render_stereo_aux always follow the binary tree.
  */
 int rt_scene_set_traversal(rt_scene* scene, int wide);

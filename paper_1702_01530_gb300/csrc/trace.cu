@@ -20,7 +20,7 @@
 //              back whatever its shading queues: the rest of the frame
 //              spreads over every warp still running, in full rounds,
 //              instead of each warp tracing its own backlog alone (measured
-//              on the 1080p blob pair: 1.52 -> 1.32 ms). No ray waits for
+//              on the 1080p blob pair: 1.52 -> 1.30 ms). No ray waits for
 //              a later launch, and there is one launch tail per frame
 //              instead of one per bounce depth.
 //   k_resolve  fixed-point sums -> float RGB, clamp to [0,1]
@@ -442,6 +442,20 @@ __global__ void k_resolve(const uint32_t* __restrict__ acc, float* __restrict__ 
   }
 }
 
+// The same, 4 values per thread with 16-byte loads and stores, when n3 is a
+// multiple of 4 and both images are 16-byte aligned: the images may be
+// pinned host memory mapped into the device (the host-output render), where
+// wide stores make fuller transfers over the CPU-GPU link.
+__global__ void k_resolve4(const uint4* __restrict__ acc, float4* __restrict__ out_L,
+                           float4* __restrict__ out_R, uint32_t n3_4, float inv_scale) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < 2 * n3_4; i += gridDim.x * blockDim.x) {
+    const uint4 a = acc[i];
+    const float4 v = make_float4(fminf(1.f, (float)a.x * inv_scale), fminf(1.f, (float)a.y * inv_scale),
+                                 fminf(1.f, (float)a.z * inv_scale), fminf(1.f, (float)a.w * inv_scale));
+    if (i < n3_4) out_L[i] = v; else out_R[i - n3_4] = v;
+  }
+}
+
 __global__ void k_counts(const uint32_t* counters, uint64_t primary, uint64_t* out) {
   if (threadIdx.x != 0) return;
   out[0] = primary;
@@ -497,7 +511,14 @@ cudaError_t render_impl(const RenderArgs& a, Workspace& ws, cudaStream_t st) {
   profile_mark(ws, a.trace_stage, st);
   const uint32_t n3 = (uint32_t)(P * 3);
   if (a.resolve) {
-    k_resolve<<<num_sms() * 8, 256, 0, st>>>(ws.accum, a.out_L, a.out_R, n3, 1.f / a.color_scale);
+    const bool wide = n3 % 4 == 0 && ((uintptr_t)a.out_L % 16) == 0 && ((uintptr_t)a.out_R % 16) == 0;
+    if (wide)
+      k_resolve4<<<num_sms() * 8, 256, 0, st>>>(reinterpret_cast<const uint4*>(ws.accum),
+                                                 reinterpret_cast<float4*>(a.out_L),
+                                                 reinterpret_cast<float4*>(a.out_R), n3 / 4,
+                                                 1.f / a.color_scale);
+    else
+      k_resolve<<<num_sms() * 8, 256, 0, st>>>(ws.accum, a.out_L, a.out_R, n3, 1.f / a.color_scale);
     profile_mark(ws, ST_RESOLVE, st);
   }
   const uint64_t primary = a.plist ? a.plist_n : (a.eyes == 3u ? 2 * P : P);

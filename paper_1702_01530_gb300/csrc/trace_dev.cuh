@@ -13,16 +13,17 @@
 namespace rt {
 namespace {
 
-// Tuning knobs (compile-time): RT_MIN_BLOCKS = minimum resident blocks per
-// SM requested from the register allocator (0 = no request; 8 measured best
-// on GB300 with the drain pools: 64 registers, 32 warps per SM, 1.305 ms per
-// 1080p blob pair as with 10 blocks, 0.265 against 0.284 ms on a small
-// scene, where 10 blocks spill in the shading code); RT_WHILE_WHILE = 1
+// Tuning knobs (compile-time; times are means of 100 1080p blob pairs on
+// GB300 with the drain pools of the render kernel, 1.299 ms by default):
+// RT_MIN_BLOCKS = minimum resident blocks per SM requested from the register
+// allocator (0 = no request; 8 measured best: 64 registers, 32 warps per SM;
+// 10 blocks (48 registers) give the same blob pair but spill in the shading
+// code, 0.30 against 0.24 ms on a 10-primitive scene); RT_WHILE_WHILE = 1
 // postpones the first leaf a ray meets and keeps descending until every
 // active lane of the warp holds a leaf, so the leaf tests of a warp run
 // together instead of interleaving with node visits (the "while-while" loop
-// of Aila & Laine, HPG 2009) -- 20 % slower here with one primitive per leaf,
-// hence off by default.
+// of Aila & Laine, HPG 2009) -- 1.549 ms with one primitive per leaf, hence
+// off by default.
 #ifndef RT_MIN_BLOCKS
 #define RT_MIN_BLOCKS 8
 #endif
@@ -39,14 +40,14 @@ constexpr int kMaxTopBytes = 85 * 7 * 16;
 // binary traversal keeps the top of its stack in a register: a pop hands
 // the register over at once and reloads it from local memory in the
 // background, so the pop and the next node fetch do not wait in series;
-// measured 1.60 vs 1.53 ms per 1080p blob pair: off by default
+// 1.370 ms: off by default
 #ifndef RT_STACK_TOP_REG
 #define RT_STACK_TOP_REG 0
 #endif
 // binary traversal prefetches both children of every visited node into L1
 // (prefetch.global.L1) as soon as their indices are known, so a child's
-// fetch that misses L1 overlaps the current node's slab tests; measured 1.87
-// vs 1.53 ms per 1080p blob pair (and 2.00 with 12 blocks per SM): off
+// fetch that misses L1 overlaps the current node's slab tests; 1.583 ms:
+// off
 #ifndef RT_PREFETCH
 #define RT_PREFETCH 0
 #endif
