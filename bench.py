@@ -508,25 +508,41 @@ def run_ours(args, rank, world, local):
     mrays = world * total_rays / (ms * 1e-3) / 1e6
     pairs = world / (ms * 1e-3)
 
-    # e2e: camera in, both images out to pinned host memory, through the C-ABI
-    hl = torch.empty((s.H, s.W, 3), dtype=torch.float32).pin_memory()
-    hr = torch.empty((s.H, s.W, 3), dtype=torch.float32).pin_memory()
+    # e2e: camera in, both images out to pinned host memory, through the C-ABI.
+    # (1) the stream of K pairs through rt_render_stereo_sequence, each pair's
+    # copy to the host overlapped with the next render (two pinned buffers
+    # used in turn); (2) one synchronous rt_render_stereo_host call per pair.
+    hl = [torch.empty((s.H, s.W, 3), dtype=torch.float32).pin_memory() for _ in range(2)]
+    hr = [torch.empty((s.H, s.W, 3), dtype=torch.float32).pin_memory() for _ in range(2)]
+    cams = [s.camera] * args.steps
+    seq_l = [hl[i % 2] for i in range(args.steps)]
+    seq_r = [hr[i % 2] for i in range(args.steps)]
+    capi.rt_render_stereo_sequence(g.handle, cams[:max(1, args.warmup)], s.eye_sep, s.convergence,
+                                   s.W, s.H, s.max_depth, seq_l[:max(1, args.warmup)],
+                                   seq_r[:max(1, args.warmup)], stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    capi.rt_render_stereo_sequence(g.handle, cams, s.eye_sep, s.convergence, s.W, s.H,
+                                   s.max_depth, seq_l, seq_r, stream)
+    e2e = (time.perf_counter() - t0) * 1e3 / args.steps
     for _ in range(max(1, args.warmup // 2)):
         capi.rt_render_stereo_host(g.handle, s.camera, s.eye_sep, s.convergence, s.W, s.H,
-                                   s.max_depth, hl, hr, stream)
+                                   s.max_depth, hl[0], hr[0], stream)
     e2e_ms = []
     for _ in range(args.steps):
         flush.fill_(1.0)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         capi.rt_render_stereo_host(g.handle, s.camera, s.eye_sep, s.convergence, s.W, s.H,
-                                   s.max_depth, hl, hr, stream)
+                                   s.max_depth, hl[0], hr[0], stream)
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
-    e2e = float(np.mean(e2e_ms))
+    e2e_one = float(np.mean(e2e_ms))
     if world > 1:
-        t = torch.tensor([e2e], device=dev)
+        t = torch.tensor([e2e, e2e_one], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e = float(t.item())
+        e2e, e2e_one = (float(x) for x in t.tolist())
 
     # roofline of the dominant kernel (FP32 issue bound): the persistent
     # render kernel traces every ray of the pair; achieved = its algorithmic
@@ -570,7 +586,14 @@ def run_ours(args, rank, world, local):
                 "stereo_pairs_per_s": round(world / (e2e * 1e-3), 2), "ms_per_step": round(e2e, 3),
                 "h2d_bytes_per_step": int(s.camera.nbytes),
                 "d2h_bytes_per_step": int(2 * s.W * s.H * 3 * 4),
-                "call": "rt_render_stereo_host"},
+                "call": f"rt_render_stereo_sequence ({args.steps} pairs in one call, host wall time; "
+                        "each pair copied to pinned host memory while the next renders; no L2 "
+                        "flush between the pairs of the call, whose working set per pair "
+                        "(accumulators, images, queues, pools: ~250 MB) exceeds the 129 MB L2)",
+                "one_call_per_pair": {
+                    "value": round(world * total_rays / (e2e_one * 1e-3) / 1e6, 2),
+                    "ms_per_step": round(e2e_one, 3),
+                    "call": "rt_render_stereo_host (synchronous, L2 flushed before each call)"}},
         "roofline": {"bound": "alu", "kernel": kern,
                      "algorithmic_ops_per_step": int(ops_all),
                      "kernel_ms_per_step": round(kern_ms, 4),

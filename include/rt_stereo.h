@@ -166,6 +166,33 @@ int rt_render_stereo_host(const rt_scene* scene, const rt_camera* cam,
                           float* host_L, float* host_R, void* cuda_stream);
 
 /*
+ * rt_render_stereo_sequence -- n_frames stereo pairs of one scene into HOST
+ * buffers, the device-to-host copy of each pair overlapped with the
+ * rendering of the next. Paper: Sec. 4-5 (a frame's synthesis time splits
+ * into GPU computation and CPU-GPU transfer; Figure 7); overlapping the two
+ * hides the transfer behind the computation of the following frame.
+ *   cams[n_frames]:  one camera per frame (host array); eye_sep,
+ *                    convergence, W, H and max_depth as in rt_render_stereo
+ *                    and shared by all frames
+ *   host_L[f], host_R[f]: frame f's images, H*W*3 float32 each (host
+ *                    memory; pinned memory lets the copies run
+ *                    asynchronously). The same buffer may be named for
+ *                    several frames: copies run in frame order, so it ends
+ *                    up holding the last of them.
+ * Each pair is rendered on cuda_stream into one of two scene-owned device
+ * frame slots and copied out on a scene-owned copy stream (the slot is not
+ * reused before its copy has finished). Returns when every image is in host
+ * memory. Every camera is validated before any work is queued.
+ * Errors: RT_ERR_INVALID_ARG (as rt_render_stereo, or a NULL camera array,
+ * pointer array or buffer), RT_ERR_OOM, RT_ERR_CUDA.
+ */
+int rt_render_stereo_sequence(const rt_scene* scene, const rt_camera* cams, uint32_t n_frames,
+                              float eye_sep, float convergence,
+                              uint32_t W, uint32_t H, uint32_t max_depth,
+                              float* const* host_L, float* const* host_R,
+                              void* cuda_stream);
+
+/*
  * rt_sync_status -- synchronise cuda_stream and report device-side checks
  * raised by earlier work on the scene (then clear them).
  * Returns RT_OK, RT_ERR_TIMEOUT (a traversal or queue loop reached its

@@ -47,6 +47,8 @@ _SIGS = {
     "rt_render_stereo": (ctypes.c_int, [_vp, _vp, _f32, _f32, _u32, _u32, _u32, _vp, _vp, _vp]),
     "rt_render_stereo_aux": (ctypes.c_int, [_vp, _vp, _f32, _f32, _u32, _u32, _u32, _vp, _vp,
                                             _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "rt_render_stereo_sequence": (ctypes.c_int, [_vp, _vp, _u32, _f32, _f32, _u32, _u32, _u32,
+                                                 _vp, _vp, _vp]),
     "rt_render_stereo_host": (ctypes.c_int, [_vp, _vp, _f32, _f32, _u32, _u32, _u32, _vp, _vp,
                                              _vp]),
     "rt_sync_status": (ctypes.c_int, [_vp, _vp]),
@@ -209,6 +211,22 @@ def rt_render_stereo_host(scene, camera, eye_sep, convergence, W, H, max_depth, 
     c, pc = _cam(camera)
     _check(lib().rt_render_stereo_host(scene, pc, eye_sep, convergence, W, H, max_depth,
                                        _hptr(host_L), _hptr(host_R), _stream(stream)))
+
+
+def rt_render_stereo_sequence(scene, cameras, eye_sep, convergence, W, H, max_depth, hosts_L,
+                              hosts_R, stream=None):
+    """One stereo pair per camera into host buffers hosts_L[f], hosts_R[f]
+    (H*W*3 float32 each; a buffer may repeat), copies overlapped with the
+    next frame's render."""
+    cams = np.ascontiguousarray(np.asarray(cameras, dtype=scenegen.CAMERA_DT).reshape(-1))
+    n = cams.shape[0]
+    if len(hosts_L) != n or len(hosts_R) != n:
+        raise ValueError("one left and one right host buffer per camera")
+    pl = (ctypes.c_void_p * max(1, n))(*[_hptr(x) for x in hosts_L])
+    pr = (ctypes.c_void_p * max(1, n))(*[_hptr(x) for x in hosts_R])
+    _check(lib().rt_render_stereo_sequence(scene, cams.ctypes.data, n, eye_sep, convergence, W, H,
+                                           max_depth, ctypes.cast(pl, ctypes.c_void_p),
+                                           ctypes.cast(pr, ctypes.c_void_p), _stream(stream)))
 
 
 def rt_sync_status(scene, stream=None):

@@ -43,8 +43,15 @@ bool finite3(const float* v) { return std::isfinite(v[0]) && std::isfinite(v[1])
 size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
 void free_workspace(rt::Workspace& ws) {
+  if (ws.seq_copy) cudaStreamSynchronize(ws.seq_copy);
   if (ws.base) cudaFree(ws.base);
   if (ws.frame) cudaFree(ws.frame);
+  if (ws.seq_frame) cudaFree(ws.seq_frame);
+  for (int k = 0; k < 2; ++k) {
+    if (ws.seq_rendered[k]) cudaEventDestroy(ws.seq_rendered[k]);
+    if (ws.seq_copied[k]) cudaEventDestroy(ws.seq_copied[k]);
+  }
+  if (ws.seq_copy) cudaStreamDestroy(ws.seq_copy);
   if (ws.rp.base) cudaFree(ws.rp.base);
   for (cudaEvent_t& e : ws.ev)
     if (e) cudaEventDestroy(e);
@@ -375,6 +382,72 @@ int rt_render_stereo_host(const rt_scene* scene, const rt_camera* cam, float eye
   if (e == cudaSuccess) e = cudaMemcpyAsync(host_R, dR, bytes / 2, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(e, "device-to-host copy");
+  return RT_OK;
+}
+
+int rt_render_stereo_sequence(const rt_scene* scene, const rt_camera* cams, uint32_t n_frames,
+                              float eye_sep, float convergence, uint32_t W, uint32_t H,
+                              uint32_t max_depth, float* const* host_L, float* const* host_R,
+                              void* cuda_stream) {
+  if (!scene) return fail(RT_ERR_INVALID_ARG, "scene is NULL");
+  if (n_frames == 0) return RT_OK;
+  if (!cams || !host_L || !host_R) return fail(RT_ERR_INVALID_ARG, "camera or host pointer array is NULL");
+  for (uint32_t f = 0; f < n_frames; ++f)
+    if (!host_L[f] || !host_R[f]) return fail(RT_ERR_INVALID_ARG, "host output buffer of frame " + std::to_string(f) + " is NULL");
+  rt::RenderArgs a;
+  for (uint32_t f = 0; f < n_frames; ++f) {        // validate every camera before any work
+    const int rc = make_render_args(scene, &cams[f], eye_sep, convergence, W, H, max_depth, a);
+    if (rc) return rc;
+  }
+  int rc = ensure_workspace(scene, W, H);
+  if (rc) return rc;
+  rt_scene* sc = const_cast<rt_scene*>(scene);
+  rt::Workspace& ws = sc->ws;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  const size_t img = (size_t)W * H * 3;            // floats per image
+  const size_t slot = 2 * img * sizeof(float);     // both images
+  cudaError_t e = cudaSuccess;
+  if (!ws.seq_copy) {
+    e = cudaStreamCreateWithFlags(&ws.seq_copy, cudaStreamNonBlocking);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+      e = cudaEventCreateWithFlags(&ws.seq_rendered[k], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ws.seq_copied[k], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) { cudaGetLastError(); return cuda_fail(e, "sequence stream and events"); }
+  }
+  if (ws.seq_frame_bytes < slot) {
+    cudaStreamSynchronize(ws.seq_copy);            // no copy may still read the old slots
+    if (ws.seq_frame) cudaFree(ws.seq_frame);
+    ws.seq_frame = nullptr;
+    ws.seq_frame_bytes = 0;
+    e = cudaMalloc(&ws.seq_frame, 2 * slot);
+    if (e != cudaSuccess) { cudaGetLastError(); return cuda_fail(e, "sequence frame allocation"); }
+    ws.seq_frame_bytes = slot;
+  }
+  for (uint32_t f = 0; f < n_frames && e == cudaSuccess; ++f) {
+    const int k = (int)(f & 1u);
+    float* dL = ws.seq_frame + (size_t)k * 2 * img;
+    float* dR = dL + img;
+    // the slot's previous copy (frame f - 2) has to finish before it is overwritten
+    if (f >= 2) e = cudaStreamWaitEvent(st, ws.seq_copied[k], 0);
+    if (e != cudaSuccess) break;
+    rc = make_render_args(scene, &cams[f], eye_sep, convergence, W, H, max_depth, a);
+    if (rc) { cudaStreamSynchronize(ws.seq_copy); return rc; }
+    a.out_L = dL;
+    a.out_R = dR;
+    rt::profile_begin(ws, st);
+    e = rt::render(a, ws, st);
+    if (e == cudaSuccess) e = cudaEventRecord(ws.seq_rendered[k], st);
+    // the copy engine reads the finished pair while the next frame renders
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ws.seq_copy, ws.seq_rendered[k], 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host_L[f], dL, img * sizeof(float), cudaMemcpyDeviceToHost, ws.seq_copy);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host_R[f], dR, img * sizeof(float), cudaMemcpyDeviceToHost, ws.seq_copy);
+    if (e == cudaSuccess) e = cudaEventRecord(ws.seq_copied[k], ws.seq_copy);
+  }
+  const cudaError_t e2 = cudaStreamSynchronize(ws.seq_copy);
+  if (e == cudaSuccess) e = e2;
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) { cudaGetLastError(); return cuda_fail(e, "sequence render"); }
   return RT_OK;
 }
 

@@ -105,6 +105,12 @@ struct Workspace {
   uint64_t cap_pixels = 0;       // 2*P the accumulators are sized for
   float4* frame = nullptr;       // frame buffers for rt_render_stereo_host
   size_t frame_bytes = 0;
+  // rt_render_stereo_sequence: two device frame slots (each both images),
+  // a copy stream and per slot the events "rendered" and "copied"
+  float* seq_frame = nullptr;
+  size_t seq_frame_bytes = 0;    // bytes of one slot
+  cudaStream_t seq_copy = nullptr;
+  cudaEvent_t seq_rendered[2] = {}, seq_copied[2] = {};
   uint32_t L = 0;
   ReprojBuffers rp;
   // stage timing (CUDA events on the render stream), see Stage

@@ -201,6 +201,54 @@ def test_repeated_renders_are_identical():
         g.close()
 
 
+# ------------------------------------------------ sequences to the host
+def test_sequence_to_host_equals_single_renders():
+    # one pair per camera, copies overlapped with the next render; a host
+    # buffer named for several frames ends up with the last of them
+    import torch
+    s = sg.config_blobs(3, n_blobs=12, n_spheres=60, W=160, H=96)
+    cams = []
+    for dx in (0.0, 1.5, -2.0, 0.5, 3.0):
+        c = s.camera.copy()
+        c["eye"][0] += dx
+        cams.append(c)
+    g = capi.GpuScene(s)
+    try:
+        ref = []
+        for c in cams:
+            out = torch.empty((2, s.H, s.W, 3), dtype=torch.float32, device="cuda")
+            capi.rt_render_stereo(g.handle, c, s.eye_sep, s.convergence, s.W, s.H, s.max_depth,
+                                  out[0], out[1])
+            ref.append(out.cpu().numpy())
+        capi.rt_sync_status(g.handle)
+        own = [torch.empty((2, s.H, s.W, 3), dtype=torch.float32).pin_memory() for _ in cams]
+        capi.rt_render_stereo_sequence(g.handle, cams, s.eye_sep, s.convergence, s.W, s.H,
+                                       s.max_depth, [o[0] for o in own], [o[1] for o in own])
+        for f in range(len(cams)):
+            assert np.array_equal(own[f].numpy(), ref[f]), f
+        ring = [torch.empty((2, s.H, s.W, 3), dtype=torch.float32).pin_memory() for _ in range(2)]
+        capi.rt_render_stereo_sequence(g.handle, cams, s.eye_sep, s.convergence, s.W, s.H,
+                                       s.max_depth, [ring[f % 2][0] for f in range(len(cams))],
+                                       [ring[f % 2][1] for f in range(len(cams))])
+        assert np.array_equal(ring[0].numpy(), ref[4]) and np.array_equal(ring[1].numpy(), ref[3])
+        unpinned = [np.zeros((2, s.H, s.W, 3), np.float32) for _ in range(2)]
+        capi.rt_render_stereo_sequence(g.handle, cams[:2], s.eye_sep, s.convergence, s.W, s.H,
+                                       s.max_depth, [u[0] for u in unpinned],
+                                       [u[1] for u in unpinned])
+        assert np.array_equal(unpinned[1], ref[1])
+        bad = cams[:2]
+        bad[1] = bad[1].copy()
+        bad[1]["vfov_deg"] = 0.0
+        with pytest.raises(capi.RtError) as e:
+            capi.rt_render_stereo_sequence(g.handle, bad, s.eye_sep, s.convergence, s.W, s.H,
+                                           s.max_depth, [u[0] for u in unpinned],
+                                           [u[1] for u in unpinned])
+        assert e.value.code == capi.RT_ERR_INVALID_ARG
+        capi.rt_sync_status(g.handle)
+    finally:
+        g.close()
+
+
 # ------------------------------------------------------- drain pools
 def test_blob_pair_renders_are_identical_at_full_size():
     # the end of every frame hands queued rays between warps through the
