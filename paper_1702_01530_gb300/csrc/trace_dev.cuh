@@ -143,9 +143,13 @@ __device__ __forceinline__ bool traverse(const DeviceScene& sc, V3 o, V3 d, floa
   float tcur = ANY ? tmax : t_best;
   bool any = false;
   for (uint32_t it = 0;; ++it) {
-    if (it >= it_max) { atomicOr(err, ERR_ITER); break; }
     if (node >= 0) {
-      if ((uint32_t)node >= n - 1) { atomicOr(err, ERR_INDEX); break; }
+      // the iteration bound is checked on node visits only: a leaf visit
+      // pushes nothing, so a run of them ends with the (bounded) stack
+      if (it >= it_max || (uint32_t)node >= n - 1) {
+        atomicOr(err, it >= it_max ? ERR_ITER : ERR_INDEX);
+        break;
+      }
       const float4* np = sc.nodes + 4 * (size_t)node;
       const float4 a = __ldg(np), b = __ldg(np + 1), c = __ldg(np + 2), e = __ldg(np + 3);
       if (COUNT) wc.inner++;
