@@ -224,8 +224,8 @@ int rt_scene_get_bvh(const rt_scene* scene, uint64_t* keys, int32_t* left, int32
  * its own left child with an empty right child) to check that traversal
  * stops at its iteration bound and rt_sync_status reports RT_ERR_TIMEOUT;
  * every index stays in range, so no memory outside the scene is touched.
- * It edits the binary tree (renders walk it after
- * rt_scene_set_traversal(scene, 0)). Synchronises the device.
+ * It edits the LBVH (renders walk it after
+ * rt_scene_set_traversal(scene, RT_TREE_LBVH)). Synchronises the device.
  */
 int rt_debug_set_node(rt_scene* scene, uint32_t node, int32_t left, int32_t right,
                       int empty_right);
@@ -245,16 +245,27 @@ int rt_debug_set_node(rt_scene* scene, uint32_t node, int32_t left, int32_t righ
 int rt_debug_set_pool_capacity(rt_scene* scene, uint32_t entries);
 
 /*
- * rt_scene_set_traversal -- choose the tree renders of this scene walk:
- * wide == 0 (default) the binary radix tree, wide != 0 the 4-wide tree
- * derived from it (every inner node at even depth holds its grandchildren;
- * its top two levels are staged in shared memory). Both hold the same leaves
- * and boxes and give the same images bit for bit (Table 1 of the paper: BVH
- * trees). On the 256k-triangle blob scene at 1080p the binary walk is faster
- * on GB300 (1.29 vs 1.41 ms per pair), hence the default. The instrumented
- * work counts of rt_render_stereo_aux always follow the binary tree.
+ * rt_scene_set_traversal -- choose the tree renders of this scene walk
+ * (Table 1 of the paper: BVH trees). Every scene holds three over the same
+ * leaves (one primitive each) and the same conservative leaf boxes, so all
+ * three give the same images bit for bit:
+ *   RT_TREE_SAH  (0, default) a binary tree rebuilt on the GPU from the
+ *                LBVH's leaves with the surface area heuristic over binned
+ *                centroids; on the 256k-triangle blob scene at 1080p it needs
+ *                15 % fewer node visits for shadow and mirror rays than the
+ *                LBVH and is the fastest walk on GB300;
+ *   RT_TREE_WIDE (1) the 4-wide tree derived from the LBVH (every inner node
+ *                at even depth holds its grandchildren; its top two levels
+ *                staged in shared memory);
+ *   RT_TREE_LBVH (2) the Morton-code binary radix tree itself, the tree
+ *                rt_scene_get_bvh returns and rt_debug_set_node edits.
+ * The instrumented work counts of rt_render_stereo_aux follow the binary
+ * tree in use (the LBVH for RT_TREE_WIDE). Other values: RT_ERR_INVALID_ARG.
  */
-int rt_scene_set_traversal(rt_scene* scene, int wide);
+#define RT_TREE_SAH 0
+#define RT_TREE_WIDE 1
+#define RT_TREE_LBVH 2
+int rt_scene_set_traversal(rt_scene* scene, int tree);
 
 /*
  * rt_profile_enable / rt_profile_read -- per-stage GPU time of the last

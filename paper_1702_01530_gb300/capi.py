@@ -244,8 +244,15 @@ def rt_debug_set_pool_capacity(scene, entries):
 STAGES = ("clear", "trace", "resolve", "warp", "net", "mask", "retrace", "compose")
 
 
-def rt_scene_set_traversal(scene, wide=True):
-    _check(lib().rt_scene_set_traversal(scene, int(bool(wide))))
+RT_TREE_SAH, RT_TREE_WIDE, RT_TREE_LBVH = 0, 1, 2
+
+
+def rt_scene_set_traversal(scene, tree=RT_TREE_WIDE):
+    """Tree the scene's renders walk: RT_TREE_SAH (default), RT_TREE_WIDE
+    or RT_TREE_LBVH (booleans map True -> RT_TREE_WIDE, False -> RT_TREE_SAH)."""
+    if isinstance(tree, bool):
+        tree = RT_TREE_WIDE if tree else RT_TREE_SAH
+    _check(lib().rt_scene_set_traversal(scene, int(tree)))
 
 
 def rt_profile_enable(scene, on=True):

@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -146,11 +147,13 @@ int make_render_args(const rt_scene* scene, const rt_camera* cam, float eye_sep,
   a.cam.H = H;
   a.cam.tiles_x = (W + 7) / 8;
   a.cam.tiles_y = (H + 3) / 4;
-  a.sc.nodes = scene->nodes;
+  // binary renders walk the SAH tree unless the LBVH is asked for; the
+  // 4-wide tree (and the work counts of a 4-wide scene) derive from the LBVH
+  a.sc.nodes = scene->tree == RT_TREE_SAH ? scene->nodes_sah : scene->nodes;
   a.sc.nodes4 = scene->nodes4;
   a.sc.n4 = scene->n4;
   a.sc.n_top = scene->n_top;
-  a.binary = scene->binary;
+  a.binary = scene->tree != RT_TREE_WIDE;
   a.sc.prims = scene->prims;
   a.sc.mats = scene->mats;
   a.sc.lights = scene->lights;
@@ -237,7 +240,7 @@ int rt_scene_create(const rt_sphere* spheres, uint32_t n_spheres, const rt_trian
   const size_t b_parent = align256((2 * n - 1) * sizeof(int32_t));
   const size_t b_nodes4 = align256((n > 1 ? n - 1 : 1) * 7 * sizeof(float4));
   const size_t b_err = 256;
-  const size_t total = b_nodes + b_prims + b_mats + b_lights + b_keys + b_parent + b_nodes4 + b_err;
+  const size_t total = 2 * b_nodes + b_prims + b_mats + b_lights + b_keys + b_parent + b_nodes4 + b_err;
   cudaError_t e = cudaMalloc(&sc->block, total);
   if (e != cudaSuccess) { cudaGetLastError(); delete sc; return cuda_fail(e, "scene allocation"); }
   char* p = static_cast<char*>(sc->block);
@@ -248,6 +251,7 @@ int rt_scene_create(const rt_sphere* spheres, uint32_t n_spheres, const rt_trian
   sc->keys = reinterpret_cast<uint64_t*>(p); p += b_keys;
   sc->parent = reinterpret_cast<int32_t*>(p); p += b_parent;
   sc->nodes4 = reinterpret_cast<float4*>(p); p += b_nodes4;
+  sc->nodes_sah = reinterpret_cast<float4*>(p); p += b_nodes;
   sc->err = reinterpret_cast<uint32_t*>(p);
   e = cudaMallocHost(&sc->h_err, sizeof(uint32_t));
   if (e != cudaSuccess) { cudaGetLastError(); cudaFree(sc->block); delete sc; return cuda_fail(e, "pinned allocation"); }
@@ -257,9 +261,9 @@ int rt_scene_create(const rt_sphere* spheres, uint32_t n_spheres, const rt_trian
   const size_t b_sph = align256((size_t)n_spheres * sizeof(rt_sphere) + 16);
   const size_t b_tri = align256((size_t)n_tris * sizeof(rt_triangle) + 16);
   // 256-byte multiple: the two uint32 counts of the 4-wide build follow it
-  const size_t b_tmp = align256(rt::lbvh_tmp_bytes((uint32_t)n) > rt::bvh4_tmp_bytes((uint32_t)n)
-                                    ? rt::lbvh_tmp_bytes((uint32_t)n)
-                                    : rt::bvh4_tmp_bytes((uint32_t)n));
+  const size_t b_tmp = align256(std::max(rt::lbvh_tmp_bytes((uint32_t)n),
+                                         std::max(rt::bvh4_tmp_bytes((uint32_t)n),
+                                                  rt::sah_tmp_bytes((uint32_t)n))));
   void* tmp = nullptr;
   e = cudaMalloc(&tmp, b_sph + b_tri + b_tmp + 256);
   if (e != cudaSuccess) { cudaGetLastError(); rt_scene_destroy(sc); return cuda_fail(e, "build scratch allocation"); }
@@ -283,6 +287,9 @@ int rt_scene_create(const rt_sphere* spheres, uint32_t n_spheres, const rt_trian
                        d_lbvh, st);
   uint32_t counts[2] = {0, 0};
   if (e == cudaSuccess) e = cudaMemcpyAsync(counts, d_counts, sizeof counts, cudaMemcpyDeviceToHost, st);
+  // the render tree: SAH splits over the LBVH's leaves
+  if (e == cudaSuccess)
+    e = rt::build_sah_tree(sc->nodes, sc->parent, (uint32_t)n, sc->nodes_sah, d_lbvh, sc->err, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(sc->h_err, sc->err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   sc->n_top = counts[0];
@@ -541,9 +548,11 @@ int rt_debug_set_pool_capacity(rt_scene* scene, uint32_t entries) {
   return RT_OK;
 }
 
-int rt_scene_set_traversal(rt_scene* scene, int wide) {
+int rt_scene_set_traversal(rt_scene* scene, int tree) {
   if (!scene) return fail(RT_ERR_INVALID_ARG, "scene is NULL");
-  scene->binary = wide == 0;
+  if (tree != RT_TREE_SAH && tree != RT_TREE_WIDE && tree != RT_TREE_LBVH)
+    return fail(RT_ERR_INVALID_ARG, "tree must be RT_TREE_SAH, RT_TREE_WIDE or RT_TREE_LBVH");
+  scene->tree = tree;
   return RT_OK;
 }
 

@@ -167,6 +167,11 @@ cudaError_t build_lbvh(const float4* d_sph_in, const float* d_tri_in, uint32_t n
                        float4* d_nodes, float4* d_prims, uint64_t* d_keys, int32_t* d_parent,
                        void* d_tmp, size_t tmp_bytes, uint32_t* d_err, cudaStream_t st);
 size_t lbvh_tmp_bytes(uint32_t n);
+size_t sah_tmp_bytes(uint32_t n);
+// binned-SAH binary tree over the leaves of the LBVH (nodes, parent): same
+// node layout and leaf slots, root 0; synchronises st once per tree level
+cudaError_t build_sah_tree(const float4* lbvh_nodes, const int32_t* parent, uint32_t n,
+                           float4* out, void* tmp, uint32_t* err, cudaStream_t st);
 size_t bvh4_tmp_bytes(uint32_t n);
 cudaError_t build_bvh4(const float4* nodes, const int32_t* parent, uint32_t n, int top_depth,
                        float4* nodes4, uint32_t* counts_dev, void* tmp, cudaStream_t st);
@@ -229,8 +234,9 @@ struct rt_scene {
   void* block = nullptr;       // persistent device allocation
   float4* nodes = nullptr;
   float4* nodes4 = nullptr;
+  float4* nodes_sah = nullptr; // binary tree rebuilt with the SAH over the same leaves (sah.cu)
   uint32_t n4 = 0, n_top = 0;
-  bool binary = true;          // render with the binary tree (default) or the 4-wide one
+  int tree = RT_TREE_SAH;      // the tree renders walk (rt_scene_set_traversal)
   float4* prims = nullptr;
   float4* mats = nullptr;
   float4* lights = nullptr;

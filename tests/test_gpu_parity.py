@@ -29,9 +29,11 @@ def _lib():
     torch.cuda.init()
 
 
-def gpu_render(s, **kw):
+def gpu_render(s, tree=None, **kw):
     g = capi.GpuScene(s)
     try:
+        if tree is not None:
+            capi.rt_scene_set_traversal(g.handle, tree)
         r = g.render(aux=True, **kw)
         capi.rt_sync_status(g.handle)
         out = {"rgb": r["rgb"].cpu().numpy(),
@@ -141,13 +143,29 @@ def test_single_primitive_scene():
 
 
 def test_work_counts_match_oracle_bvh_traversal():
+    # the oracle walks its own LBVH (bit-identical to the GPU's) in the same
+    # near-child-first order
     s = sg.config_blobs(5, n_blobs=10, n_spheres=50, W=96, H=64)
-    gpu = gpu_render(s, count_work=True)
+    gpu = gpu_render(s, count_work=True, tree=capi.RT_TREE_LBVH)
     ref = oracle.OracleScene(s).render(mode=oracle.OracleScene.MODE_BVH)
     g, r = gpu["work"].astype(np.float64), ref["work"].astype(np.float64)
     assert r[0, 0] > 1000
     rel = np.abs(g - r) / np.maximum(r, 1.0)
     assert rel.max() < 0.02, (g, r)
+
+
+def test_sah_tree_is_another_tree_with_the_same_results():
+    # the render tree (SAH splits over the LBVH's leaves) is a different
+    # binary tree -- its walks visit other nodes -- with the same hits, depths,
+    # images and ray counts (every other parity test runs on it as well)
+    s = sg.config_blobs(3, n_blobs=30, n_spheres=150, W=160, H=120)
+    lbvh = gpu_render(s, count_work=True, tree=capi.RT_TREE_LBVH)
+    sah = gpu_render(s, count_work=True, tree=capi.RT_TREE_SAH)
+    for k in ("rgb", "hit_id", "depth", "rays"):
+        assert np.array_equal(lbvh[k], sah[k]), k
+    assert not np.array_equal(sah["work"][:, 0], lbvh["work"][:, 0])
+    # primitive tests: the same leaves behind conservative boxes
+    assert 0.5 < sah["work"][:, 1:].sum() / lbvh["work"][:, 1:].sum() < 2.0
 
 
 def test_host_render_matches_device_render():
@@ -175,16 +193,21 @@ def test_host_render_matches_device_render():
                                   lambda: sg.config_small(4, W=97, H=61),
                                   lambda: scene(spheres=[((0, 0, -5), 1.0, 0)], W=16, H=9),
                                   lambda: sg.config_polyhedra(6, n_lights=2, ground=True, W=80, H=60)])
-def test_wide_and_binary_traversal_give_identical_images(make):
+def test_all_trees_give_identical_images(make):
     s = make()
     g = capi.GpuScene(s)
     try:
-        binary = g.render(aux=True)
-        capi.rt_scene_set_traversal(g.handle, True)
-        wide = g.render(aux=True)
+        sah = g.render(aux=True)                          # the default tree
+        out = {}
+        for tree in (capi.RT_TREE_WIDE, capi.RT_TREE_LBVH, capi.RT_TREE_SAH):
+            capi.rt_scene_set_traversal(g.handle, tree)
+            out[tree] = g.render(aux=True)
         capi.rt_sync_status(g.handle)
-        for k in ("rgb", "hit_id", "depth", "rays"):
-            assert np.array_equal(wide[k].cpu().numpy(), binary[k].cpu().numpy()), k
+        for tree, r in out.items():
+            for k in ("rgb", "hit_id", "depth", "rays"):
+                assert np.array_equal(r[k].cpu().numpy(), sah[k].cpu().numpy()), (tree, k)
+        with pytest.raises(capi.RtError):
+            capi.rt_scene_set_traversal(g.handle, 3)
     finally:
         g.close()
 
@@ -359,7 +382,8 @@ def test_bvh_cycle_stops_at_iteration_bound():
         # node 0 becomes its own left child; its right child gets an empty
         # box: every ray entering the root loops until the iteration bound
         capi.rt_debug_set_node(g.handle, 0, 0, int(bvh["right"][0]), empty_right=True)
-        g.render()                                       # the hook edits the binary tree
+        capi.rt_scene_set_traversal(g.handle, capi.RT_TREE_LBVH)   # the hook edits the LBVH
+        g.render()
         with pytest.raises(capi.RtError) as e:
             capi.rt_sync_status(g.handle)
         assert e.value.code == capi.RT_ERR_TIMEOUT
