@@ -15,7 +15,8 @@
 // One level of the tree per launch, one block per node of the level:
 //   1. centroid bounds of the node's leaves (block reduction);
 //   2. kBins bins per axis: leaf count and the union of the leaf boxes
-//      (shared-memory atomics on order-preserving integer images of floats);
+//      (shared-memory atomics on order-preserving integer images of floats,
+//      one set of bins per warp, merged);
 //   3. the split of least SAH cost, area(L) n(L) + area(R) n(R), over the
 //      3 (kBins - 1) bin boundaries; an object-median split when the centroids
 //      coincide or the depth budget is low, so that no leaf lies deeper than
@@ -37,7 +38,14 @@
 namespace rt {
 namespace {
 
-constexpr int kSahThreads = 256;
+#ifndef RT_SAH_THREADS
+#define RT_SAH_THREADS 256
+#endif
+// threads per node (block): 256 measured best (blob scene 12.2 ms, 10M-triangle terrain 485 ms
+// for the whole tree; 512: 15.0 / 531 ms, 1024: 22.8 / 778 ms -- the many small nodes of the
+// lower levels pay for every thread of their block)
+constexpr int kSahThreads = RT_SAH_THREADS;
+constexpr int kSahWarps = kSahThreads / 32;
 constexpr int kBins = 16;
 constexpr int kMaxDepth = 60;        // median splits keep every leaf at or above this depth
 
@@ -87,8 +95,9 @@ k_sah_level(const float4* __restrict__ leaf_lo, const float4* __restrict__ leaf_
             const Job* __restrict__ jobs, uint32_t n_jobs, Job* __restrict__ next,
             uint32_t* __restrict__ next_count, float4* __restrict__ out, uint32_t* __restrict__ root_split,
             uint32_t n, uint32_t* __restrict__ err) {
-  __shared__ int s_cnt[3][kBins];
-  __shared__ int s_box[3][kBins][6];         // lo xyz, hi xyz as order-preserving ints
+  // bins per warp (fewer shared-memory atomics on one address), merged into warp 0's
+  __shared__ int s_cnt[kSahWarps][3][kBins];
+  __shared__ int s_box[kSahWarps][3][kBins][6];   // lo xyz, hi xyz as order-preserving ints
   __shared__ int s_red[12];                  // centroid bounds, then child boxes of a median split
   __shared__ uint32_t s_scan[kSahThreads / 32];
   __shared__ float s_cost[3 * (kBins - 1)];
@@ -100,9 +109,10 @@ k_sah_level(const float4* __restrict__ leaf_lo, const float4* __restrict__ leaf_
 
   // 1. centroid bounds
   if (tid < 6) s_red[tid] = tid < 3 ? f2o(INFINITY) : f2o(-INFINITY);
-  for (int i = tid; i < 3 * kBins; i += kSahThreads) {
-    s_cnt[i / kBins][i % kBins] = 0;
-    for (int c = 0; c < 6; ++c) s_box[i / kBins][i % kBins][c] = c < 3 ? f2o(INFINITY) : f2o(-INFINITY);
+  for (int i = tid; i < kSahWarps * 3 * kBins; i += kSahThreads) {
+    const int w = i / (3 * kBins), a = (i / kBins) % 3, q = i % kBins;
+    s_cnt[w][a][q] = 0;
+    for (int c = 0; c < 6; ++c) s_box[w][a][q][c] = c < 3 ? f2o(INFINITY) : f2o(-INFINITY);
   }
   __syncthreads();
   float clo[3] = {INFINITY, INFINITY, INFINITY}, chi[3] = {-INFINITY, -INFINITY, -INFINITY};
@@ -135,11 +145,26 @@ k_sah_level(const float4* __restrict__ leaf_lo, const float4* __restrict__ leaf_
       for (int a = 0; a < 3; ++a) {
         if (!(cext[a] > 0.f)) continue;
         const int bin = min(kBins - 1, (int)((c[a] - cmin[a]) * ((float)kBins / cext[a])));
-        atomicAdd(&s_cnt[a][bin], 1);
+        const int w = tid >> 5;
+        atomicAdd(&s_cnt[w][a][bin], 1);
         for (int q = 0; q < 3; ++q) {
-          atomicMin(&s_box[a][bin][q], f2o(l3[q]));
-          atomicMax(&s_box[a][bin][3 + q], f2o(h3[q]));
+          atomicMin(&s_box[w][a][bin][q], f2o(l3[q]));
+          atomicMax(&s_box[w][a][bin][3 + q], f2o(h3[q]));
         }
+      }
+    }
+    __syncthreads();
+    // merge the warps' bins into warp 0's
+    for (int i = tid; i < 3 * kBins * 7; i += kSahThreads) {
+      const int a = i / (kBins * 7), q = (i / 7) % kBins, f = i % 7;
+      if (f == 6) {
+        int t = 0;
+        for (int w = 0; w < kSahWarps; ++w) t += s_cnt[w][a][q];
+        s_cnt[0][a][q] = t;
+      } else {
+        int v = s_box[0][a][q][f];
+        for (int w = 1; w < kSahWarps; ++w) v = f < 3 ? min(v, s_box[w][a][q][f]) : max(v, s_box[w][a][q][f]);
+        s_box[0][a][q][f] = v;
       }
     }
     __syncthreads();
@@ -149,13 +174,13 @@ k_sah_level(const float4* __restrict__ leaf_lo, const float4* __restrict__ leaf_
       float rlo[3] = {INFINITY, INFINITY, INFINITY}, rhi[3] = {-INFINITY, -INFINITY, -INFINITY};
       int nl = 0, nr = 0;
       for (int q = 0; q < kBins; ++q) {
-        const int c = s_cnt[a][q];
+        const int c = s_cnt[0][a][q];
         if (!c) continue;
         float* blo = q <= s ? llo : rlo;
         float* bhi = q <= s ? lhi : rhi;
         for (int x = 0; x < 3; ++x) {
-          blo[x] = fminf(blo[x], o2f(s_box[a][q][x]));
-          bhi[x] = fmaxf(bhi[x], o2f(s_box[a][q][3 + x]));
+          blo[x] = fminf(blo[x], o2f(s_box[0][a][q][x]));
+          bhi[x] = fmaxf(bhi[x], o2f(s_box[0][a][q][3 + x]));
         }
         if (q <= s) nl += c; else nr += c;
       }
@@ -246,11 +271,11 @@ k_sah_level(const float4* __restrict__ leaf_lo, const float4* __restrict__ leaf_
     for (int c = 0; c < 2; ++c)
       for (int x = 0; x < 3; ++x) { cl[c][x] = INFINITY; ch[c][x] = -INFINITY; }
     for (int q = 0; q < kBins; ++q) {
-      if (!s_cnt[axis][q]) continue;
+      if (!s_cnt[0][axis][q]) continue;
       const int c = q <= split_bin ? 0 : 1;
       for (int x = 0; x < 3; ++x) {
-        cl[c][x] = fminf(cl[c][x], o2f(s_box[axis][q][x]));
-        ch[c][x] = fmaxf(ch[c][x], o2f(s_box[axis][q][3 + x]));
+        cl[c][x] = fminf(cl[c][x], o2f(s_box[0][axis][q][x]));
+        ch[c][x] = fmaxf(ch[c][x], o2f(s_box[0][axis][q][3 + x]));
       }
     }
   } else {
