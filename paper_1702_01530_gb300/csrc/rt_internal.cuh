@@ -33,7 +33,7 @@ enum : uint32_t {
   ERR_BUILD = 16u,     // BVH refit did not reach the root
 };
 
-constexpr int kStackSize = 64;   // radix-tree depth over unique 64-bit keys <= 64
+constexpr int kStackSize = 64;   // >= the depth of the LBVH (64-bit keys) and of the SAH tree (60)
 constexpr int32_t kEmptyChild = 0x7FFFFFFF;  // unused slot of a 4-wide node
 constexpr float kAmbient = 0.1f;
 constexpr float kBgR = 0.2f, kBgG = 0.3f, kBgB = 0.5f;

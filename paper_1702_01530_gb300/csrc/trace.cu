@@ -33,9 +33,11 @@
 // Traversal (Table 1 of the paper: BVH trees): BVH2 nodes of 64 B with both
 // child boxes, read as four 16-byte vector loads through the read-only path;
 // slab tests in FP32 with fused multiply-adds and three-input min/max; the
-// far child is pushed on a per-thread stack (depth <= 64 by construction of
-// the radix tree over unique 64-bit keys), the near child is visited first.
-// Each loop has an iteration bound; hitting it sets the error word.
+// far child is pushed on a per-thread stack of 64 entries, the near child is
+// visited first. The tree is the SAH rebuild of the scene's LBVH (sah.cu,
+// depth <= 60 by its depth budget) or the LBVH itself (depth <= 64: a radix
+// tree over unique 64-bit keys). Each loop has an iteration bound and the
+// stack a size check; hitting either sets the error word.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
