@@ -12,11 +12,17 @@
 // same image 11 % faster. Any binary tree over the same conservative leaf
 // boxes yields the same closest hit and the same any-hit answer.
 //
-// One level of the tree per launch, one block per node of the level:
+// Build time (GB300): the blob scene's 257k leaves 6.3 ms, the 10M-triangle
+// terrain 0.18 s (with 256 threads for every level and no bin combining:
+// 12.2 ms and 0.49 s).
+// One level of the tree per launch, one block per node of the level (nodes
+// of at most kSmallLeaves leaves: their whole subtree in one warp):
 //   1. centroid bounds of the node's leaves (block reduction);
 //   2. kBins bins per axis: leaf count and the union of the leaf boxes
 //      (shared-memory atomics on order-preserving integer images of floats,
-//      one set of bins per warp, merged);
+//      one set of bins per warp, merged; the lanes of a warp that fall in one
+//      bin combine their values first, as neighbouring leaves in Morton order
+//      usually do);
 //   3. the split of least SAH cost, area(L) n(L) + area(R) n(R), over the
 //      3 (kBins - 1) bin boundaries; an object-median split when the centroids
 //      coincide or the depth budget is low, so that no leaf lies deeper than
@@ -41,13 +47,19 @@ namespace {
 #ifndef RT_SAH_THREADS
 #define RT_SAH_THREADS 256
 #endif
-// threads per node (block): 256 measured best (blob scene 12.2 ms, 10M-triangle terrain 485 ms
-// for the whole tree; 512: 15.0 / 531 ms, 1024: 22.8 / 778 ms -- the many small nodes of the
-// lower levels pay for every thread of their block)
+#ifndef RT_SAH_THREADS_TOP
+#define RT_SAH_THREADS_TOP 1024
+#endif
+// threads per node (block): 256 for the many nodes of the lower levels, 1024 for the levels of
+// fewer than kTopJobs nodes, whose blocks each cover many leaves
 constexpr int kSahThreads = RT_SAH_THREADS;
-constexpr int kSahWarps = kSahThreads / 32;
+// levels with fewer nodes than kTopJobs run kSahThreadsTop threads per node:
+// their few blocks cover many leaves each
+constexpr int kSahThreadsTop = RT_SAH_THREADS_TOP;
+constexpr uint32_t kTopJobs = 1024;
 constexpr int kBins = 16;
 constexpr int kMaxDepth = 60;        // median splits keep every leaf at or above this depth
+constexpr int kSmallLeaves = 32;     // subtrees of at most this many leaves: one warp each (k_sah_small)
 
 struct Job {
   uint32_t begin, end;               // leaf slots idx[begin, end) of this node (end - begin >= 2)
@@ -89,12 +101,15 @@ __global__ void k_iota(uint32_t* idx, uint32_t n) {
   if (k < n) idx[k] = k;
 }
 
+template <int kSahThreads>
 __global__ void __launch_bounds__(kSahThreads)
 k_sah_level(const float4* __restrict__ leaf_lo, const float4* __restrict__ leaf_hi,
             const uint32_t* __restrict__ idx_in, uint32_t* __restrict__ idx_out,
             const Job* __restrict__ jobs, uint32_t n_jobs, Job* __restrict__ next,
-            uint32_t* __restrict__ next_count, float4* __restrict__ out, uint32_t* __restrict__ root_split,
+            uint32_t* __restrict__ next_count, Job* __restrict__ small, uint32_t* __restrict__ small_count,
+            uint32_t out_buf, float4* __restrict__ out, uint32_t* __restrict__ root_split,
             uint32_t n, uint32_t* __restrict__ err) {
+  constexpr int kSahWarps = kSahThreads / 32;
   // bins per warp (fewer shared-memory atomics on one address), merged into warp 0's
   __shared__ int s_cnt[kSahWarps][3][kBins];
   __shared__ int s_box[kSahWarps][3][kBins][6];   // lo xyz, hi xyz as order-preserving ints
@@ -142,14 +157,25 @@ k_sah_level(const float4* __restrict__ leaf_lo, const float4* __restrict__ leaf_
       const float4 lo = leaf_lo[k], hi = leaf_hi[k];
       const float c[3] = {0.5f * (lo.x + hi.x), 0.5f * (lo.y + hi.y), 0.5f * (lo.z + hi.z)};
       const float l3[3] = {lo.x, lo.y, lo.z}, h3[3] = {hi.x, hi.y, hi.z};
+      // neighbouring leaves (Morton order) mostly share a bin: the lanes of a
+      // bin combine their values first and one of them updates the bin
+      const uint32_t active = __activemask();
       for (int a = 0; a < 3; ++a) {
-        if (!(cext[a] > 0.f)) continue;
+        if (!(cext[a] > 0.f)) continue;          // uniform over the block
         const int bin = min(kBins - 1, (int)((c[a] - cmin[a]) * ((float)kBins / cext[a])));
-        const int w = tid >> 5;
-        atomicAdd(&s_cnt[w][a][bin], 1);
+        const uint32_t grp = __match_any_sync(active, bin);
+        int v[6];
         for (int q = 0; q < 3; ++q) {
-          atomicMin(&s_box[w][a][bin][q], f2o(l3[q]));
-          atomicMax(&s_box[w][a][bin][3 + q], f2o(h3[q]));
+          v[q] = __reduce_min_sync(grp, f2o(l3[q]));
+          v[3 + q] = __reduce_max_sync(grp, f2o(h3[q]));
+        }
+        if ((uint32_t)(__ffs(grp) - 1) == (tid & 31)) {
+          const int w = tid >> 5;
+          atomicAdd(&s_cnt[w][a][bin], __popc(grp));
+          for (int q = 0; q < 3; ++q) {
+            atomicMin(&s_box[w][a][bin][q], v[q]);
+            atomicMax(&s_box[w][a][bin][3 + q], v[3 + q]);
+          }
         }
       }
     }
@@ -326,9 +352,13 @@ k_sah_level(const float4* __restrict__ leaf_lo, const float4* __restrict__ leaf_
       if (re[c] - rb[c] == 1) {
         child[c] = ~(int32_t)idx_out[rb[c]];
       } else {
-        const uint32_t at = atomicAdd(next_count, 1u);
+        const bool is_small = re[c] - rb[c] <= (uint32_t)kSmallLeaves;
+        const uint32_t at = atomicAdd(is_small ? small_count : next_count, 1u);
         if (at >= n / 2 + 1) { atomicOr(err, ERR_BUILD); continue; }
-        next[at] = Job{rb[c], re[c], id << 1 | (uint32_t)c, job.depth + 1};
+        // a small subtree is built later by one warp from the leaf slots this
+        // level wrote (idx buffer out_buf, kept in the depth field's top bit)
+        (is_small ? small : next)[at] =
+            Job{rb[c], re[c], id << 1 | (uint32_t)c, (job.depth + 1) | (is_small ? out_buf << 31 : 0u)};
         child[c] = 0;                                 // filled in by the child
       }
     }
@@ -336,11 +366,180 @@ k_sah_level(const float4* __restrict__ leaf_lo, const float4* __restrict__ leaf_
   }
 }
 
+// warp-wide inclusive scan of a box (lanes in order), forward or backward
+__device__ __forceinline__ void box_scan(float lo[3], float hi[3], bool backward) {
+  const uint32_t lane = threadIdx.x & 31;
+  for (int o = 1; o < 32; o <<= 1) {
+    float l[3], h[3];
+    for (int x = 0; x < 3; ++x) {
+      l[x] = backward ? __shfl_down_sync(0xFFFFFFFFu, lo[x], o) : __shfl_up_sync(0xFFFFFFFFu, lo[x], o);
+      h[x] = backward ? __shfl_down_sync(0xFFFFFFFFu, hi[x], o) : __shfl_up_sync(0xFFFFFFFFu, hi[x], o);
+    }
+    const bool ok = backward ? lane + o < 32 : lane >= (uint32_t)o;
+    if (ok)
+      for (int x = 0; x < 3; ++x) { lo[x] = fminf(lo[x], l[x]); hi[x] = fmaxf(hi[x], h[x]); }
+  }
+}
+
+// Subtrees of at most kSmallLeaves leaves, one warp each: every node takes
+// the split of least SAH cost over all positions of its leaves sorted by
+// centroid on each axis (a warp bitonic sort, ties by leaf order, then box
+// prefix and suffix scans), or the median of the current order when the
+// depth budget is short. Node ids follow the split positions as in
+// k_sah_level.
+constexpr int kSmallWarps = 4;
+__global__ void __launch_bounds__(32 * kSmallWarps)
+k_sah_small(const float4* __restrict__ leaf_lo, const float4* __restrict__ leaf_hi,
+            uint32_t* const* __restrict__ idx_bufs, const Job* __restrict__ jobs, uint32_t n_jobs,
+            float4* __restrict__ out, const uint32_t* __restrict__ root_split, uint32_t n,
+            uint32_t* __restrict__ err) {
+  __shared__ uint32_t s_slot[kSmallWarps][kSmallLeaves];     // leaf slots in the current order
+  __shared__ float s_box[kSmallWarps][kSmallLeaves][6];
+  __shared__ uint32_t s_tmp[kSmallWarps][kSmallLeaves];
+  __shared__ float s_tbox[kSmallWarps][kSmallLeaves][6];
+  __shared__ Job s_stack[kSmallWarps][kSmallLeaves];
+  const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t j = blockIdx.x * kSmallWarps + warp;
+  if (j >= n_jobs) return;
+  const Job job = jobs[j];
+  const uint32_t base = job.begin, m = job.end - job.begin;
+  const uint32_t* idx = idx_bufs[job.depth >> 31];
+  if (m < 2 || m > (uint32_t)kSmallLeaves) { if (lane == 0) atomicOr(err, ERR_BUILD); return; }
+  const uint32_t rs = *root_split;
+  if (lane < m) {
+    const uint32_t k = idx[base + lane];
+    s_slot[warp][lane] = k;
+    const float4 lo = leaf_lo[k], hi = leaf_hi[k];
+    s_box[warp][lane][0] = lo.x; s_box[warp][lane][1] = lo.y; s_box[warp][lane][2] = lo.z;
+    s_box[warp][lane][3] = hi.x; s_box[warp][lane][4] = hi.y; s_box[warp][lane][5] = hi.z;
+  }
+  int sp = 0;
+  if (lane == 0) s_stack[warp][0] = Job{0, m, job.parent_slot, job.depth & 0x7FFFFFFFu};
+  sp = 1;
+  __syncwarp();
+  for (uint32_t guard = 0; sp > 0 && guard < 2 * kSmallLeaves; ++guard) {
+    const Job t = s_stack[warp][--sp];
+    __syncwarp();
+    const uint32_t b = t.begin, s = t.end - t.begin;
+    const bool in = lane < s;
+    float blo[3] = {INFINITY, INFINITY, INFINITY}, bhi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    if (in)
+      for (int x = 0; x < 3; ++x) { blo[x] = s_box[warp][b + lane][x]; bhi[x] = s_box[warp][b + lane][3 + x]; }
+    uint32_t k_split = s / 2;                 // median of the current order unless the SAH wins
+    int best_axis = -1;
+    float best_cost = INFINITY;
+    if (t.depth + s - 1 <= (uint32_t)kMaxDepth) {
+      for (int axis = 0; axis < 3; ++axis) {
+        // sort (centroid, position) ascending over the lanes; out-of-range lanes last
+        float key = in ? 0.5f * (blo[axis] + bhi[axis]) : INFINITY;
+        uint32_t val = in ? lane : 0xFFFFFFFFu;
+        for (uint32_t kk = 2; kk <= 32; kk <<= 1)
+          for (uint32_t jj = kk >> 1; jj > 0; jj >>= 1) {
+            const float ok = __shfl_xor_sync(0xFFFFFFFFu, key, jj);
+            const uint32_t ov = __shfl_xor_sync(0xFFFFFFFFu, val, jj);
+            const bool up = (lane & kk) == 0, lower = (lane & jj) == 0;
+            const bool other_less = ok < key || (ok == key && ov < val);
+            const bool take = (lower == up) ? other_less : !other_less && !(ok == key && ov == val);
+            if (take) { key = ok; val = ov; }
+          }
+        // boxes in sorted order; prefix and suffix unions
+        float plo[3], phi[3], qlo[3], qhi[3];
+        for (int x = 0; x < 3; ++x) {
+          const float vlo = val < s ? s_box[warp][b + val][x] : INFINITY;
+          const float vhi = val < s ? s_box[warp][b + val][3 + x] : -INFINITY;
+          plo[x] = qlo[x] = vlo; phi[x] = qhi[x] = vhi;
+        }
+        box_scan(plo, phi, false);
+        box_scan(qlo, qhi, true);
+        // split after sorted position lane (left lane+1 leaves)
+        float q2lo[3], q2hi[3];
+        for (int x = 0; x < 3; ++x) {
+          q2lo[x] = __shfl_down_sync(0xFFFFFFFFu, qlo[x], 1);
+          q2hi[x] = __shfl_down_sync(0xFFFFFFFFu, qhi[x], 1);
+        }
+        float cost = INFINITY;
+        if (lane + 1 < s)
+          cost = half_area(plo, phi) * (float)(lane + 1) + half_area(q2lo, q2hi) * (float)(s - lane - 1);
+        // warp argmin, lowest position among equal costs
+        float bc = cost;
+        uint32_t bl = lane;
+        for (int o = 16; o > 0; o >>= 1) {
+          const float c2 = __shfl_xor_sync(0xFFFFFFFFu, bc, o);
+          const uint32_t l2 = __shfl_xor_sync(0xFFFFFFFFu, bl, o);
+          if (c2 < bc || (c2 == bc && l2 < bl)) { bc = c2; bl = l2; }
+        }
+        if (bc < best_cost) {               // warp-uniform
+          best_cost = bc;
+          best_axis = axis;
+          k_split = bl + 1;
+          // keep this axis's order
+          if (in) {
+            s_tmp[warp][lane] = s_slot[warp][b + val];
+            for (int x = 0; x < 6; ++x) s_tbox[warp][lane][x] = s_box[warp][b + val][x];
+          }
+        }
+        __syncwarp();
+      }
+      if (best_axis >= 0 && in) {
+        s_slot[warp][b + lane] = s_tmp[warp][lane];
+        for (int x = 0; x < 6; ++x) s_box[warp][b + lane][x] = s_tbox[warp][lane][x];
+      }
+      __syncwarp();
+    }
+    // child boxes of the split at k_split in the current order
+    float c0lo[3], c0hi[3], c1lo[3], c1hi[3];
+    for (int x = 0; x < 3; ++x) {
+      const bool l0 = in && lane < k_split, l1 = in && lane >= k_split;
+      const float vlo = in ? s_box[warp][b + lane][x] : INFINITY, vhi = in ? s_box[warp][b + lane][3 + x] : -INFINITY;
+      float a0 = l0 ? vlo : INFINITY, a1 = l1 ? vlo : INFINITY, z0 = l0 ? vhi : -INFINITY, z1 = l1 ? vhi : -INFINITY;
+      for (int o = 16; o > 0; o >>= 1) {
+        a0 = fminf(a0, __shfl_xor_sync(0xFFFFFFFFu, a0, o));
+        a1 = fminf(a1, __shfl_xor_sync(0xFFFFFFFFu, a1, o));
+        z0 = fmaxf(z0, __shfl_xor_sync(0xFFFFFFFFu, z0, o));
+        z1 = fmaxf(z1, __shfl_xor_sync(0xFFFFFFFFu, z1, o));
+      }
+      c0lo[x] = a0; c1lo[x] = a1; c0hi[x] = z0; c1hi[x] = z1;
+    }
+    if (lane == 0) {
+      const uint32_t split = base + b + k_split;      // global split position
+      const uint32_t id = split == 1 ? rs - 1 : split - 1;
+      reinterpret_cast<int32_t*>(out + 4 * (size_t)(t.parent_slot >> 1) + 3)[t.parent_slot & 1u] = (int32_t)id;
+      if (id < n - 1) {
+        float4* o = out + 4 * (size_t)id;
+        o[0] = make_float4(c0lo[0], c0hi[0], c0lo[1], c0hi[1]);
+        o[1] = make_float4(c1lo[0], c1hi[0], c1lo[1], c1hi[1]);
+        o[2] = make_float4(c0lo[2], c0hi[2], c1lo[2], c1hi[2]);
+        const uint32_t rb[2] = {b, b + k_split}, re[2] = {b + k_split, b + s};
+        int32_t child[2];
+        for (int c = 0; c < 2; ++c) {
+          if (re[c] - rb[c] == 1) {
+            child[c] = ~(int32_t)s_slot[warp][rb[c]];
+          } else {
+            child[c] = 0;                       // filled in when the child is built
+            s_stack[warp][sp + c] = Job{rb[c], re[c], id << 1 | (uint32_t)c, t.depth + 1};
+          }
+        }
+        o[3] = make_float4(__int_as_float(child[0]), __int_as_float(child[1]), 0.f, 0.f);
+      } else {
+        atomicOr(err, ERR_BUILD);
+      }
+    }
+    __syncwarp();
+    // the pushes lane 0 made (warp-uniform count)
+    sp += (k_split > 1 ? 1 : 0) + (s - k_split > 1 ? 1 : 0);
+    if (k_split == 1 && s - k_split > 1) {      // only the right child was pushed, at sp + 1
+      if (lane == 0) s_stack[warp][sp - 1] = s_stack[warp][sp];
+    }
+    __syncwarp();
+  }
+  if (sp != 0 && lane == 0) atomicOr(err, ERR_BUILD);
+}
+
 }  // namespace
 
 size_t sah_tmp_bytes(uint32_t n) {
   const size_t nn = n ? n : 1;
-  return 2 * nn * sizeof(float4) + 2 * nn * sizeof(uint32_t) + 2 * (nn / 2 + 1) * sizeof(Job) + 256;
+  return 2 * nn * sizeof(float4) + 2 * nn * sizeof(uint32_t) + 3 * (nn / 2 + 1) * sizeof(Job) + 256;
 }
 
 cudaError_t build_sah_tree(const float4* lbvh_nodes, const int32_t* parent, uint32_t n,
@@ -356,24 +555,41 @@ cudaError_t build_sah_tree(const float4* lbvh_nodes, const int32_t* parent, uint
   Job* jobs[2];
   jobs[0] = reinterpret_cast<Job*>(p); p += max_jobs * sizeof(Job);
   jobs[1] = reinterpret_cast<Job*>(p); p += max_jobs * sizeof(Job);
-  uint32_t* counters = reinterpret_cast<uint32_t*>(p);   // [0] next count, [1] root split
+  Job* small = reinterpret_cast<Job*>(p); p += max_jobs * sizeof(Job);
+  uint32_t** d_bufs = reinterpret_cast<uint32_t**>(p); p += 2 * sizeof(uint32_t*);
+  uint32_t* counters = reinterpret_cast<uint32_t*>(p);   // [0] next count, [1] root split, [2] small count
   const int g = (int)((n + 255) / 256);
   k_leaf_boxes<<<g, 256, 0, st>>>(lbvh_nodes, parent, n, lo, hi);
   k_iota<<<g, 256, 0, st>>>(idx[0], n);
   const Job root{0, n, 0xFFFFFFFFu, 0};
   cudaError_t e = cudaMemcpyAsync(jobs[0], &root, sizeof root, cudaMemcpyHostToDevice, st);
+  uint32_t* h_bufs[2] = {idx[0], idx[1]};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_bufs, h_bufs, sizeof h_bufs, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(counters + 2, 0, sizeof(uint32_t), st);
   uint32_t count = 1;
   for (int level = 0; level < kMaxDepth + 2 && count > 0 && e == cudaSuccess; ++level) {
     const int cur = level & 1;
     e = cudaMemsetAsync(counters, 0, sizeof(uint32_t), st);
     if (e != cudaSuccess) break;
-    k_sah_level<<<count, kSahThreads, 0, st>>>(lo, hi, idx[cur], idx[cur ^ 1], jobs[cur], count,
-                                               jobs[cur ^ 1], counters, out, counters + 1, n, err);
+    if (count < kTopJobs)
+      k_sah_level<kSahThreadsTop><<<count, kSahThreadsTop, 0, st>>>(
+          lo, hi, idx[cur], idx[cur ^ 1], jobs[cur], count, jobs[cur ^ 1], counters, small,
+          counters + 2, (uint32_t)(cur ^ 1), out, counters + 1, n, err);
+    else
+      k_sah_level<kSahThreads><<<count, kSahThreads, 0, st>>>(
+          lo, hi, idx[cur], idx[cur ^ 1], jobs[cur], count, jobs[cur ^ 1], counters, small,
+          counters + 2, (uint32_t)(cur ^ 1), out, counters + 1, n, err);
     e = cudaMemcpyAsync(&count, counters, sizeof count, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (count > max_jobs) { count = 0; e = cudaErrorUnknown; }
   }
   if (e == cudaSuccess && count != 0) e = cudaErrorUnknown;   // deeper than the depth budget
+  uint32_t n_small = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&n_small, counters + 2, sizeof n_small, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && n_small > max_jobs) e = cudaErrorUnknown;
+  if (e == cudaSuccess && n_small > 0)
+    k_sah_small<<<(n_small + kSmallWarps - 1) / kSmallWarps, 32 * kSmallWarps, 0, st>>>(
+        lo, hi, d_bufs, small, n_small, out, counters + 1, n, err);
   return e == cudaSuccess ? cudaGetLastError() : e;
 }
 
