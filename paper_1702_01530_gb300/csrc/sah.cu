@@ -586,7 +586,8 @@ cudaError_t build_sah_tree(const float4* lbvh_nodes, const int32_t* parent, uint
   }
   if (e == cudaSuccess && count != 0) e = cudaErrorUnknown;   // deeper than the depth budget
   uint32_t n_small = 0;
-  if (e == cudaSuccess) e = cudaMemcpy(&n_small, counters + 2, sizeof n_small, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&n_small, counters + 2, sizeof n_small, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e == cudaSuccess && n_small > max_jobs) e = cudaErrorUnknown;
   if (e == cudaSuccess && n_small > 0)
     k_sah_small<<<(n_small + kSmallWarps - 1) / kSmallWarps, 32 * kSmallWarps, 0, st>>>(
