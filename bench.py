@@ -84,6 +84,24 @@ def workload(args):
     return sg.config_blobs(args.seed, W=args.W, H=args.H)
 
 
+def max_over_ranks(values, world, device=None):
+    """Each value's maximum over the ranks (the slowest rank sets the job's
+    time); the values themselves on one rank."""
+    if world <= 1:
+        return [float(v) for v in values]
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+def job_rates(rays_per_rank, world, ms_max):
+    """Whole-job Mrays/s and stereo pairs/s of `world` replicas that each
+    trace rays_per_rank rays per step, the job taking ms_max per step."""
+    return world * rays_per_rank / (ms_max * 1e-3) / 1e6, world / (ms_max * 1e-3)
+
+
 def dist_setup(args):
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -506,13 +524,8 @@ def run_ours(args, rank, world, local):
     capi.rt_sync_status(g.handle)
     clocks = clk.summary()
 
-    ms = float(np.mean(step_ms))
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    mrays = world * total_rays / (ms * 1e-3) / 1e6
-    pairs = world / (ms * 1e-3)
+    ms = max_over_ranks([float(np.mean(step_ms))], world, dev)[0]
+    mrays, pairs = job_rates(total_rays, world, ms)
 
     # e2e: camera in, both images out to pinned host memory, through the C-ABI.
     # (1) the stream of K pairs through rt_render_stereo_sequence, each pair's
@@ -544,11 +557,7 @@ def run_ours(args, rank, world, local):
         capi.rt_render_stereo_host(g.handle, s.camera, s.eye_sep, s.convergence, s.W, s.H,
                                    s.max_depth, hl[0], hr[0], stream)
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
-    e2e_one = float(np.mean(e2e_ms))
-    if world > 1:
-        t = torch.tensor([e2e, e2e_one], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e, e2e_one = (float(x) for x in t.tolist())
+    e2e, e2e_one = max_over_ranks([e2e, float(np.mean(e2e_ms))], world, dev)
 
     # roofline of the dominant kernel (FP32 issue bound): the persistent
     # render kernel traces every ray of the pair; achieved = its algorithmic
