@@ -51,6 +51,15 @@ constexpr int kMaxTopBytes = 85 * 7 * 16;
 #ifndef RT_PREFETCH
 #define RT_PREFETCH 0
 #endif
+// binary traversal defers leaf tests: a lane keeps up to two leaves pending
+// and walks on; the warp tests the pending leaves together once
+// RT_DEFER_LEAVES lanes hold one, or as soon as any lane can go no further
+// (both slots full and the next node a leaf, or nothing left to visit).
+// Same images; 1.399 / 1.417 / 1.442 ms at 16 / 8 / 4 lanes against 1.149 ms
+// for leaves tested when met (SAH tree), so 0 = off by default
+#ifndef RT_DEFER_LEAVES
+#define RT_DEFER_LEAVES 0
+#endif
 // 4-wide closest-hit traversal pushes the other hit children farthest first
 #ifndef RT_ORDERED_PUSH
 #define RT_ORDERED_PUSH 0
@@ -432,6 +441,100 @@ __device__ __forceinline__ bool traverse_ww(const DeviceScene& sc, V3 o, V3 d, f
 }
 #endif
 
+#if RT_DEFER_LEAVES
+// Binary traversal with deferred leaves (the speculative "while-while" idea
+// of Aila & Laine, HPG 2009, in one loop): node visits and leaf tests of a
+// warp run in separate passes of the same iteration, so a leaf met by one
+// lane no longer costs every other lane a full primitive test. A deferred
+// leaf can only make the closest-hit bound tcur shrink later, so the set of
+// leaves tested contains the one the eager walk would accept: the hit (t,
+// lower id on ties) and the any-hit answer are the same.
+template <bool ANY>
+__device__ __forceinline__ bool traverse_dl(const DeviceScene& sc, V3 o, V3 d, float tmax,
+                                            float& t_best, uint32_t& id_best, uint32_t& k_best,
+                                            uint32_t* err) {
+  constexpr int32_t kDone = 0x7FFFFFFF;        // larger than any internal node index
+  const V3 idir = v3(safe_rcp(d.x), safe_rcp(d.y), safe_rcp(d.z));
+  const V3 ood = v3(o.x * idir.x, o.y * idir.y, o.z * idir.z);
+  int32_t stack[kStackSize];
+  int sp = 0;
+  const uint32_t n = sc.n_prims;
+  int32_t node = n == 1 ? ~0 : 0;
+  int32_t l0 = 0, l1 = 0;                      // pending leaves (~k), 0 = empty; l1 != 0 => l0 != 0
+  // every iteration visits a node, moves a leaf to a slot or tests the
+  // slots, and a ray visits each node and leaf at most once
+  const uint32_t it_max = 2u * n + 64u;
+  float tcur = ANY ? tmax : t_best;
+  bool any = false;
+  for (uint32_t it = 0;; ++it) {
+    if (it >= it_max) { atomicOr(err, ERR_ITER); break; }
+    if (node >= 0 && node != kDone) {
+      if ((uint32_t)node >= n - 1) { atomicOr(err, ERR_INDEX); break; }
+      const float4* np = sc.nodes + 4 * (size_t)node;
+      const float4 a = __ldg(np), b = __ldg(np + 1), c = __ldg(np + 2), e = __ldg(np + 3);
+      const float l0x = fmaf(a.x, idir.x, -ood.x), h0x = fmaf(a.y, idir.x, -ood.x);
+      const float l0y = fmaf(a.z, idir.y, -ood.y), h0y = fmaf(a.w, idir.y, -ood.y);
+      const float l0z = fmaf(c.x, idir.z, -ood.z), h0z = fmaf(c.y, idir.z, -ood.z);
+      const float l1x = fmaf(b.x, idir.x, -ood.x), h1x = fmaf(b.y, idir.x, -ood.x);
+      const float l1y = fmaf(b.z, idir.y, -ood.y), h1y = fmaf(b.w, idir.y, -ood.y);
+      const float l1z = fmaf(c.z, idir.z, -ood.z), h1z = fmaf(c.w, idir.z, -ood.z);
+      const float in0 = fmax3(fminf(l0x, h0x), fminf(l0y, h0y), fmaxf(fminf(l0z, h0z), 0.f));
+      const float out0 = fmin3(fmaxf(l0x, h0x), fmaxf(l0y, h0y), fminf(fmaxf(l0z, h0z), tcur));
+      const float in1 = fmax3(fminf(l1x, h1x), fminf(l1y, h1y), fmaxf(fminf(l1z, h1z), 0.f));
+      const float out1 = fmin3(fmaxf(l1x, h1x), fmaxf(l1y, h1y), fminf(fmaxf(l1z, h1z), tcur));
+      const bool hit0 = in0 <= out0 * kRobust;
+      const bool hit1 = in1 <= out1 * kRobust;
+      const int32_t cl = __float_as_int(e.x), cr = __float_as_int(e.y);
+      if (hit0 && hit1) {
+        if (sp >= kStackSize) { atomicOr(err, ERR_STACK); break; }
+        const bool swap = in1 < in0;
+        stack[sp++] = swap ? cl : cr;
+        node = swap ? cr : cl;
+      } else if (hit0 | hit1) {
+        node = hit0 ? cl : cr;
+      } else {
+        node = sp ? stack[--sp] : kDone;
+      }
+    }
+    if (node < 0 && l0 == 0) { l0 = node; node = sp ? stack[--sp] : kDone; }
+    if (node < 0 && l1 == 0) { l1 = node; node = sp ? stack[--sp] : kDone; }
+    const bool pend = l0 != 0;
+    const bool stuck = pend && (node < 0 || node == kDone);
+    const unsigned m = __activemask();
+    const bool flush = __any_sync(m, stuck) || __popc(__ballot_sync(m, pend)) >= RT_DEFER_LEAVES;
+    if (flush && pend) {
+      bool bad = false;
+#pragma unroll 1
+      for (int s = 0; s < 2; ++s) {
+        const int32_t lf = s ? l1 : l0;
+        if (lf == 0) break;
+        const uint32_t k = (uint32_t)~lf;
+        if (k >= n) { bad = true; break; }
+        const float4* pp = sc.prims + 3 * (size_t)k;
+        const float4 p0 = __ldg(pp), p1 = __ldg(pp + 1);
+        const uint32_t id = __float_as_uint(p0.w);
+        float t;
+        const bool h = id < sc.n_spheres ? hit_sphere(p0, p1.x, o, d, t)
+                                         : hit_tri(p0, p1, __ldg(pp + 2), o, d, t);
+        if (ANY) {
+          if (h && t < tmax) { any = true; node = kDone; break; }
+        } else if (h && (t < tcur || (t == tcur && id < id_best))) {
+          tcur = t;
+          id_best = id;
+          k_best = k;
+          any = true;
+        }
+      }
+      if (bad) { atomicOr(err, ERR_INDEX); break; }
+      l0 = l1 = 0;
+    }
+    if (node == kDone && l0 == 0) break;
+  }
+  if (!ANY) t_best = tcur;
+  return any;
+}
+#endif
+
 // The instrumented (COUNT) and the requested binary traversal walk the
 // binary radix tree, whose node visits define the algorithmic work; the
 // production path walks the 4-wide tree (the same leaves, the same hits).
@@ -440,6 +543,9 @@ __device__ __forceinline__ bool trace_ray(const DeviceScene& sc, const float4* t
                                           float tmax, float& t_best, uint32_t& id_best,
                                           uint32_t& k_best, WorkCount& wc, uint32_t* err) {
   if (WIDE && !COUNT) return traverse4<ANY>(sc, top, o, d, tmax, t_best, id_best, k_best, err);
+#if RT_DEFER_LEAVES
+  if (!COUNT) return traverse_dl<ANY>(sc, o, d, tmax, t_best, id_best, k_best, err);
+#endif
 #if RT_WHILE_WHILE
   return traverse_ww<ANY, COUNT>(sc, o, d, tmax, t_best, id_best, k_best, wc, err);
 #else
