@@ -254,13 +254,14 @@ int rt_debug_set_pool_capacity(rt_scene* scene, uint32_t entries);
  *                centroids; on the 256k-triangle blob scene at 1080p it needs
  *                15 % fewer node visits for shadow and mirror rays than the
  *                LBVH and is the fastest walk on GB300;
- *   RT_TREE_WIDE (1) the 4-wide tree derived from the LBVH (every inner node
- *                at even depth holds its grandchildren; its top two levels
- *                staged in shared memory);
+ *   RT_TREE_WIDE (1) the 4-wide tree collapsed from the SAH tree (every
+ *                inner node at even depth holds its grandchildren; its top
+ *                two levels staged in shared memory);
  *   RT_TREE_LBVH (2) the Morton-code binary radix tree itself, the tree
  *                rt_scene_get_bvh returns and rt_debug_set_node edits.
  * The instrumented work counts of rt_render_stereo_aux follow the binary
- * tree in use (the LBVH for RT_TREE_WIDE). Other values: RT_ERR_INVALID_ARG.
+ * tree in use (the SAH tree for RT_TREE_WIDE). Other values:
+ * RT_ERR_INVALID_ARG.
  */
 #define RT_TREE_SAH 0
 #define RT_TREE_WIDE 1

@@ -1,4 +1,4 @@
-// 4-wide BVH derived from the binary radix tree (sm_103a).
+// 4-wide BVH collapsed from a binary tree (the SAH render tree; sm_103a).
 //
 // Every internal node of the binary tree at even depth becomes one 4-wide
 // node whose children are its grandchildren (a child that is a leaf stays a
@@ -6,7 +6,8 @@
 // Traversal then needs about half the dependent node fetches per ray and
 // tests four boxes per fetch. Nodes whose 4-wide depth is below `top_depth`
 // are numbered first (0 .. n_top-1) so the renderer can stage them in shared
-// memory; the rest follow in binary-tree index order.
+// memory; the rest follow in binary-tree index order. The binary tree's root
+// is node 0 and `parent` gives the parent of each inner node.
 //
 // Node layout (7 x float4 = 112 B): lo.x[4], hi.x[4], lo.y[4], hi.y[4],
 // lo.z[4], hi.z[4], child[4] (int bits: >= 0 4-wide node, < 0 leaf ~k).
@@ -114,7 +115,25 @@ __global__ void k_scan_excl(uint32_t* a, uint32_t len) {
   for (uint32_t i = b; i < e; ++i) { const uint32_t v = a[i]; a[i] = run; run += v; }
 }
 
+// parent of every internal node of a binary tree (root 0, its own parent)
+__global__ void k_inner_parents(const float4* __restrict__ nodes, uint32_t n_inner, int32_t* parent) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_inner) return;
+  if (i == 0) parent[0] = 0;
+  const float4 e = nodes[4 * (size_t)i + 3];
+  const int32_t cl = __float_as_int(e.x), cr = __float_as_int(e.y);
+  if (cl > 0 && (uint32_t)cl < n_inner) parent[cl] = (int32_t)i;
+  if (cr > 0 && (uint32_t)cr < n_inner) parent[cr] = (int32_t)i;
+}
+
 }  // namespace
+
+cudaError_t inner_parents(const float4* nodes, uint32_t n, int32_t* parent, cudaStream_t st) {
+  if (n < 2) return cudaSuccess;
+  const uint32_t m = n - 1;
+  k_inner_parents<<<(m + 255) / 256, 256, 0, st>>>(nodes, m, parent);
+  return cudaGetLastError();
+}
 
 size_t bvh4_tmp_bytes(uint32_t n) {
   const size_t m = n > 1 ? n - 1 : 1;

@@ -12,7 +12,7 @@
 // same image 11 % faster. Any binary tree over the same conservative leaf
 // boxes yields the same closest hit and the same any-hit answer.
 //
-// Scene creation with this build (GB300; upload, LBVH, 4-wide tree, SAH
+// Scene creation with this build (GB300; upload, LBVH, SAH tree, 4-wide
 // tree): the blob scene's 257k primitives 6.3 ms, the 10M-triangle terrain
 // 0.18 s (with 256 threads for every level and no bin combining: 12.2 ms
 // and 0.49 s).

@@ -561,9 +561,10 @@ __device__ __forceinline__ bool traverse_dl(const DeviceScene& sc, V3 o, V3 d, f
 }
 #endif
 
-// The instrumented (COUNT) and the requested binary traversal walk the
-// binary radix tree, whose node visits define the algorithmic work; the
-// production path walks the 4-wide tree (the same leaves, the same hits).
+// The instrumented (COUNT) walk and the binary renders use the binary tree
+// in sc.nodes (the SAH tree, or the LBVH whose node visits define the
+// algorithmic work); a 4-wide render walks the 4-wide tree (the same leaves,
+// the same hits).
 template <bool ANY, bool COUNT, bool WIDE>
 __device__ __forceinline__ bool trace_ray(const DeviceScene& sc, const float4* top, V3 o, V3 d,
                                           float tmax, float& t_best, uint32_t& id_best,
