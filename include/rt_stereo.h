@@ -484,7 +484,10 @@ int rt_stereo_composite(const float* d_L, const float* d_R, uint32_t W, uint32_t
  * requests < 2^32; every request as rt_render_stereo validates it.
  *
  * rt_batch_config (24 bytes):
- *   tile_w x tile_h   pixels per 32-ray tile: (4,8), (8,4), (16,2) or (32,1)
+ *   tile_w x tile_h   pixels per 32-ray tile: 16 pixels traced for both eyes,
+ *                     the two rays of a pixel in neighbouring lanes ((2,8),
+ *                     (4,4), (8,2) or (16,1)), or 32 pixels of one eye ((4,8),
+ *                     (8,4), (16,2) or (32,1))
  *   blocks_per_sm     resident blocks of 128 threads per SM, 1..the kernel's
  *                     occupancy limit (0 = that limit)
  *   cap_r             mirror-queue entries per warp: 64, 128 or 256
@@ -517,7 +520,7 @@ typedef struct rt_batch rt_batch;  /* opaque */
  * clears, the persistent render kernel, the resolve kernel) into a CUDA
  * graph.
  *   reqs: host array of n_requests records (copied).
- *   cfg:  host pointer or NULL (= tile 8x4, occupancy limit, cap_r 64,
+ *   cfg:  host pointer or NULL (= tile 4x4, occupancy limit, cap_r 64,
  *         largest request first, latency tracking on).
  *   out_batch: receives the batch; released with rt_batch_destroy.
  * Synchronous. Errors: RT_ERR_INVALID_ARG, RT_ERR_OOM, RT_ERR_CUDA.

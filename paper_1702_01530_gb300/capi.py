@@ -307,7 +307,7 @@ BATCH_CONFIG_DT = np.dtype([(k, "<u4") for k in ("tile_w", "tile_h", "blocks_per
                                                   "order", "track_latency")])
 
 
-def batch_config(tile_w=8, tile_h=4, blocks_per_sm=0, cap_r=64, order=RT_BATCH_ORDER_LARGEST_FIRST,
+def batch_config(tile_w=4, tile_h=4, blocks_per_sm=0, cap_r=64, order=RT_BATCH_ORDER_LARGEST_FIRST,
                  track_latency=1) -> np.ndarray:
     c = np.zeros(1, BATCH_CONFIG_DT)
     for k, v in dict(tile_w=tile_w, tile_h=tile_h, blocks_per_sm=blocks_per_sm, cap_r=cap_r,

@@ -5,8 +5,10 @@
 //
 // Paper Sec. 3 / Figure 1: the image is split into parts traced by parallel
 // workers; here the parts of every request of a batch form one work list.
-// Tiles of 32 pixels (tile_w x tile_h) are numbered request after request in
-// the chosen order, the two eyes of a request alternating; warps pull tiles
+// Tiles of 32 rays are numbered request after request in the chosen order:
+// tile_w x tile_h = 16 pixels traced for both eyes, the two rays of a pixel in
+// neighbouring lanes (as the single-pair renderer does), or 32 pixels of one
+// eye, the two eyes of a request alternating between tiles; warps pull tiles
 // from one global counter, so small and large requests share the GPU without
 // a launch per request or per bounce depth. Each warp keeps the single-pair
 // renderer's two private wavefront queues (shadow rays, mirror rays); an
@@ -47,7 +49,7 @@ struct BatchReq {
   uint32_t max_depth;
   uint32_t pix_base;       // global pixel id of (left eye, pixel 0); right eye follows at + W*H
   uint32_t tile_base;      // first tile in the work list
-  uint32_t n_tiles;        // 2 * tiles_x * tiles_y
+  uint32_t n_tiles;        // tiles_x * tiles_y (both eyes per tile), else twice that
   uint32_t user;           // index in the caller's request array
   uint32_t pad;
   float* out_L;
@@ -58,7 +60,8 @@ struct KBatch {
   const BatchReq* __restrict__ req;
   uint32_t n_req;
   uint32_t n_tiles;
-  uint32_t tw_log2;        // tile width = 1 << tw_log2, height = 32 >> tw_log2
+  uint32_t tw_log2;        // tile width = 1 << tw_log2
+  uint32_t paired;         // 1: 16-pixel tiles of both eyes (height 16 >> tw_log2), 0: 32 of one
   uint32_t cap_s, cap_r, q_stride;   // queue capacities and per-warp stride in entries
   uint32_t* accum;
   float4* wq;
@@ -181,10 +184,11 @@ __global__ void __launch_bounds__(kThreads, RT_BATCH_MIN_BLOCKS) k_render_batch(
       hint = r;
       const BatchReq* rq = kp.req + r;
       const uint32_t lt = tile - rq->tile_base;
-      const uint32_t eye = lt & 1u, tt = lt >> 1;
+      const uint32_t eye = kp.paired ? lane & 1u : lt & 1u;
+      const uint32_t tt = kp.paired ? lt : lt >> 1, q = kp.paired ? lane >> 1 : lane;
       const uint32_t W = rq->cam.W, H = rq->cam.H, tx = rq->cam.tiles_x;
-      const uint32_t px = (tt % tx) * (tw_mask + 1u) + (lane & tw_mask);
-      const uint32_t py = (tt / tx) * (32u >> kp.tw_log2) + (lane >> kp.tw_log2);
+      const uint32_t px = (tt % tx) * (tw_mask + 1u) + (q & tw_mask);
+      const uint32_t py = (tt / tx) * ((kp.paired ? 16u : 32u) >> kp.tw_log2) + (q >> kp.tw_log2);
       active = px < W && py < H;
       pix = rq->pix_base + eye * (W * H) + py * W + px;
       if (active) primary_ray(rq->cam, px, py, eye, o, d);
@@ -302,7 +306,9 @@ constexpr uint32_t kCapRMax = 256;
 
 bool valid_config(const rt_batch_config& c) {
   const bool tile = (c.tile_w == 4 && c.tile_h == 8) || (c.tile_w == 8 && c.tile_h == 4) ||
-                    (c.tile_w == 16 && c.tile_h == 2) || (c.tile_w == 32 && c.tile_h == 1);
+                    (c.tile_w == 16 && c.tile_h == 2) || (c.tile_w == 32 && c.tile_h == 1) ||
+                    (c.tile_w == 2 && c.tile_h == 8) || (c.tile_w == 4 && c.tile_h == 4) ||
+                    (c.tile_w == 8 && c.tile_h == 2) || (c.tile_w == 16 && c.tile_h == 1);
   const bool cap = c.cap_r == 64 || c.cap_r == 128 || c.cap_r == 256;
   return tile && cap && c.order <= RT_BATCH_ORDER_SMALLEST_FIRST && c.track_latency <= 1 &&
          (int)c.blocks_per_sm <= batch_occupancy();
@@ -387,7 +393,7 @@ int apply_config(rt_batch* b, const rt_batch_config& c) {
     q.max_depth = a.max_depth;
     q.pix_base = b->pix_base[i];
     q.tile_base = (uint32_t)tiles;
-    q.n_tiles = 2u * q.cam.tiles_x * q.cam.tiles_y;
+    q.n_tiles = (tw * th == 16 ? 1u : 2u) * q.cam.tiles_x * q.cam.tiles_y;
     q.user = i;
     q.out_L = b->reqs[i].d_out_L;
     q.out_R = b->reqs[i].d_out_R;
@@ -405,6 +411,7 @@ int apply_config(rt_batch* b, const rt_batch_config& c) {
   kp.n_req = b->n;
   kp.n_tiles = b->n_tiles;
   kp.tw_log2 = tw_log2;
+  kp.paired = tw * th == 16 ? 1u : 0u;
   kp.cap_s = b->cap_s;
   kp.cap_r = c.cap_r;
   kp.q_stride = b->q_stride;
@@ -470,7 +477,7 @@ int rt_batch_create(const rt_request* reqs, uint32_t n_requests, const rt_batch_
   if (!reqs) return fail(RT_ERR_INVALID_ARG, "reqs is NULL");
   if (n_requests < 1 || n_requests > RT_BATCH_MAX_REQUESTS)
     return fail(RT_ERR_INVALID_ARG, "n_requests must be in 1..RT_BATCH_MAX_REQUESTS");
-  rt_batch_config c = {8, 4, 0, 64, RT_BATCH_ORDER_LARGEST_FIRST, 1};
+  rt_batch_config c = {4, 4, 0, 64, RT_BATCH_ORDER_LARGEST_FIRST, 1};
   if (cfg) c = *cfg;
   for (uint32_t i = 0; i < n_requests; ++i) {
     const rt_request& r = reqs[i];
@@ -637,7 +644,7 @@ int rt_batch_autotune(rt_batch* batch, uint32_t reps, void* cuda_stream, rt_batc
   float best_t = 0.f;
   int rc = time_config(best, best_t);
   const int occ = rt::batch_occupancy();
-  const uint32_t tiles[4][2] = {{8, 4}, {4, 8}, {16, 2}, {32, 1}};
+  const uint32_t tiles[6][2] = {{4, 4}, {8, 2}, {2, 8}, {8, 4}, {4, 8}, {16, 2}};
   for (int dim = 0; dim < 4 && rc == RT_OK; ++dim) {
     std::vector<rt_batch_config> cands;
     if (dim == 0) {

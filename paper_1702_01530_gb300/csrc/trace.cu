@@ -3,9 +3,13 @@
 // Paper Sec. 3: the left and right channel are independent ("parallel level
 // 1") and the pixels of a channel are traced in parallel ("parallel level 2");
 // the image is split into parts processed by parallel workers (Figure 1).
-// Here both eyes share one persistent launch: warps pull 8x4-pixel tiles from
-// a global counter, tiles alternating left / right eye, so the two eyes'
-// nearly identical rays touch the same BVH nodes close together in time.
+// Here both eyes share one persistent launch and one warp: a warp pulls a
+// tile of 4x4 pixels from a global counter and traces it for both eyes, the
+// two rays of a pixel in neighbouring lanes, so the eyes' nearly identical
+// rays fetch the same BVH nodes in the same load and their shadow and mirror
+// rays queue side by side (1080p blob pair: 1.143 -> 1.042 ms against 8x4
+// tiles of one eye, eyes alternating between warps). Renders of one eye use
+// 8x4 tiles.
 //
 // Per stereo pair:
 //   k_render   one persistent kernel. Every warp owns two small wavefront
@@ -56,7 +60,7 @@ struct KParams {
   uint32_t* counters;
   uint32_t cap_s, cap_r, cap_p;
   uint32_t epoch;      // this render's epoch (> 0)
-  uint32_t n_tiles;    // 2 * tiles_x * tiles_y
+  uint32_t n_tiles;    // primary tiles of 32 rays (pixel list: 32 entries each)
   bool share_partial;  // drain: hand over backlogs of less than a round too
 };
 
@@ -313,11 +317,17 @@ k_render(KParams kp) {
         const uint32_t pi = pix - eye * P;
         py = pi / cam.W;
         px = pi - py * cam.W;
-      } else {                             // 8x4 tiles, alternating eyes when both are traced
-        const uint32_t tt = a.eyes == 3u ? tile >> 1 : tile;
-        eye = a.eyes == 3u ? (tile & 1u) : (a.eyes == 2u ? 1u : 0u);
-        px = (tt % cam.tiles_x) * 8u + (lane & 7u);
-        py = (tt / cam.tiles_x) * 4u + (lane >> 3);
+      } else if (a.eyes == 3u) {           // 4x4 pixels of both eyes: lane 2q left, 2q+1 right
+        const uint32_t tx4 = (cam.W + 3u) / 4u, q = lane >> 1;
+        eye = lane & 1u;
+        px = (tile % tx4) * 4u + (q & 3u);
+        py = (tile / tx4) * 4u + (q >> 2);
+        active = px < cam.W && py < cam.H;
+        pix = eye * P + py * cam.W + px;
+      } else {                             // one eye: 8x4 tiles
+        eye = a.eyes == 2u ? 1u : 0u;
+        px = (tile % cam.tiles_x) * 8u + (lane & 7u);
+        py = (tile / cam.tiles_x) * 4u + (lane >> 3);
         active = px < cam.W && py < cam.H;
         pix = eye * P + py * cam.W + px;
       }
@@ -488,7 +498,8 @@ cudaError_t render_impl(const RenderArgs& a, Workspace& ws, cudaStream_t st) {
   kp.cap_s = ws.cap_s;
   kp.cap_r = ws.cap_r;
   kp.n_tiles = a.plist ? (a.plist_n + 31u) / 32u
-                       : (a.eyes == 3u ? 2u : 1u) * a.cam.tiles_x * a.cam.tiles_y;
+             : a.eyes == 3u ? ((a.cam.W + 3u) / 4u) * a.cam.tiles_y   // 4x4 pixels, both eyes
+                            : a.cam.tiles_x * a.cam.tiles_y;          // 8x4 pixels, one eye
   const int grid = render_grid();
   if ((uint64_t)grid * (kThreads / 32) > ws.n_warps) return cudaErrorInvalidValue;
   kp.share_partial = a.sc.n_prims >= kSharePartialPrims;

@@ -108,10 +108,10 @@ def test_batch_equals_single_renders_bitwise(fx):
     want = np.sum([r for _, r in fx.ref], axis=0)
     assert rays.tolist() == want.tolist()
     assert (lat > 0).all()
-    assert c["tile_w"][0] * c["tile_h"][0] == 32 and c["blocks_per_sm"][0] >= 1
+    assert (c["tile_w"][0], c["tile_h"][0]) == (4, 4) and c["blocks_per_sm"][0] >= 1
 
 
-@pytest.mark.parametrize("tile", [(4, 8), (16, 2), (32, 1)])
+@pytest.mark.parametrize("tile", [(8, 2), (2, 8), (16, 1), (8, 4), (4, 8), (32, 1)])
 @pytest.mark.parametrize("order", [capi.RT_BATCH_ORDER_GIVEN, capi.RT_BATCH_ORDER_SMALLEST_FIRST])
 def test_batch_configurations_give_identical_images(fx, tile, order):
     import torch
@@ -164,7 +164,7 @@ def test_batch_autotune_keeps_images(fx):
     try:
         cfg, ms = capi.rt_batch_autotune(b, reps=2)
         assert ms > 0
-        assert int(cfg["tile_w"][0]) * int(cfg["tile_h"][0]) == 32
+        assert int(cfg["tile_w"][0]) * int(cfg["tile_h"][0]) in (16, 32)
         assert int(cfg["cap_r"][0]) in (64, 128, 256)
         capi.rt_batch_launch(b)
         rays, lat, c = capi.rt_batch_stats(b, len(fx.outs))
