@@ -14,16 +14,16 @@ namespace rt {
 namespace {
 
 // Tuning knobs (compile-time; times are means of 100 1080p blob pairs on
-// GB300 with the drain pools of the render kernel, 1.299 ms by default):
+// GB300, SAH tree, both eyes of a 4x4-pixel tile per warp: 1.042 ms by
+// default, 0.221 ms for a 10-primitive scene):
 // RT_MIN_BLOCKS = minimum resident blocks per SM requested from the register
 // allocator (0 = no request; 8 measured best: 64 registers, 32 warps per SM;
-// 10 blocks (48 registers) give the same blob pair but spill in the shading
-// code, 0.30 against 0.24 ms on a 10-primitive scene); RT_WHILE_WHILE = 1
-// postpones the first leaf a ray meets and keeps descending until every
-// active lane of the warp holds a leaf, so the leaf tests of a warp run
-// together instead of interleaving with node visits (the "while-while" loop
-// of Aila & Laine, HPG 2009) -- 1.549 ms with one primitive per leaf, hence
-// off by default.
+// 6 blocks: 1.051 / 0.216 ms; 10 blocks (48 registers, spills in the shading
+// code): 1.047 / 0.242 ms); RT_WHILE_WHILE = 1 postpones the first leaf a ray
+// meets and keeps descending until every active lane of the warp holds a
+// leaf, so the leaf tests of a warp run together instead of interleaving
+// with node visits (the "while-while" loop of Aila & Laine, HPG 2009) --
+// 1.247 ms with one primitive per leaf, hence off by default.
 #ifndef RT_MIN_BLOCKS
 #define RT_MIN_BLOCKS 8
 #endif
@@ -40,14 +40,14 @@ constexpr int kMaxTopBytes = 85 * 7 * 16;
 // binary traversal keeps the top of its stack in a register: a pop hands
 // the register over at once and reloads it from local memory in the
 // background, so the pop and the next node fetch do not wait in series;
-// 1.370 ms: off by default
+// 1.093 ms: off by default
 #ifndef RT_STACK_TOP_REG
 #define RT_STACK_TOP_REG 0
 #endif
 // binary traversal prefetches both children of every visited node into L1
 // (prefetch.global.L1) as soon as their indices are known, so a child's
-// fetch that misses L1 overlaps the current node's slab tests; 1.583 ms:
-// off
+// fetch that misses L1 overlaps the current node's slab tests; 1.583
+// against 1.299 ms (LBVH, one eye per warp): off
 #ifndef RT_PREFETCH
 #define RT_PREFETCH 0
 #endif
@@ -55,8 +55,8 @@ constexpr int kMaxTopBytes = 85 * 7 * 16;
 // and walks on; the warp tests the pending leaves together once
 // RT_DEFER_LEAVES lanes hold one, or as soon as any lane can go no further
 // (both slots full and the next node a leaf, or nothing left to visit).
-// Same images; 1.399 / 1.417 / 1.442 ms at 16 / 8 / 4 lanes against 1.149 ms
-// for leaves tested when met (SAH tree), so 0 = off by default
+// Same images; 1.302 ms at 16 lanes against 1.042 (1.399 / 1.417 / 1.442 at
+// 16 / 8 / 4 against 1.149 with one eye per warp), so 0 = off by default
 #ifndef RT_DEFER_LEAVES
 #define RT_DEFER_LEAVES 0
 #endif
@@ -64,7 +64,7 @@ constexpr int kMaxTopBytes = 85 * 7 * 16;
 // (ld.global.nc.v8.f32, sm_100 and later) instead of four 16-byte ones:
 // half the load instructions and L1 requests per node visit; 1 = plain,
 // 2 = with an L1 evict-last hint. 1.149 / 1.150 ms against 1.146 (SAH
-// tree): off by default
+// tree, one eye per warp): off by default
 #ifndef RT_LD256
 #define RT_LD256 0
 #endif
