@@ -13,9 +13,9 @@
 // boxes yields the same closest hit and the same any-hit answer.
 //
 // Scene creation with this build (GB300; upload, LBVH, SAH tree, 4-wide
-// tree): the blob scene's 257k primitives 6.3 ms, the 10M-triangle terrain
-// 0.18 s (with 256 threads for every level and no bin combining: 12.2 ms
-// and 0.49 s).
+// tree): the blob scene's 257k primitives 4.5 ms, the 10M-triangle terrain
+// 95 ms (one block per node on every level: 6.3 ms and 0.18 s; with 256
+// threads for every level and no bin combining: 12.2 ms and 0.49 s).
 // One level of the tree per launch, one block per node of the level (nodes
 // of at most kSmallLeaves leaves: their whole subtree in one warp):
 //   1. centroid bounds of the node's leaves (block reduction);
@@ -39,6 +39,8 @@
 // and independent of launch order.
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <algorithm>
 
 #include "rt_internal.cuh"
 
@@ -78,6 +80,84 @@ __device__ __forceinline__ float half_area(const float lo[3], const float hi[3])
   const float dx = fmaxf(hi[0] - lo[0], 0.f), dy = fmaxf(hi[1] - lo[1], 0.f),
               dz = fmaxf(hi[2] - lo[2], 0.f);
   return dx * dy + dy * dz + dz * dx;
+}
+
+// SAH cost of splitting after bin s on axis a, from merged bins (counts and
+// order-preserving box images); INFINITY when a side is empty
+__device__ __forceinline__ float split_cost(const int (*cnt)[kBins], const int (*box)[kBins][6],
+                                            float cext_a, int a, int s) {
+  float llo[3] = {INFINITY, INFINITY, INFINITY}, lhi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  float rlo[3] = {INFINITY, INFINITY, INFINITY}, rhi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  int nl = 0, nr = 0;
+  for (int q = 0; q < kBins; ++q) {
+    const int c = cnt[a][q];
+    if (!c) continue;
+    float* blo = q <= s ? llo : rlo;
+    float* bhi = q <= s ? lhi : rhi;
+    for (int x = 0; x < 3; ++x) {
+      blo[x] = fminf(blo[x], o2f(box[a][q][x]));
+      bhi[x] = fmaxf(bhi[x], o2f(box[a][q][3 + x]));
+    }
+    if (q <= s) nl += c; else nr += c;
+  }
+  return (cext_a > 0.f && nl > 0 && nr > 0)
+             ? half_area(llo, lhi) * (float)nl + half_area(rlo, rhi) * (float)nr
+             : INFINITY;
+}
+
+// the first of equal least costs (deterministic): axis (-1 = none) and bin
+__device__ __forceinline__ void pick_split(const float* cost, int* choice) {
+  int best = -1;
+  float bc = INFINITY;
+  for (int i = 0; i < 3 * (kBins - 1); ++i)
+    if (cost[i] < bc) { bc = cost[i]; best = i; }
+  choice[0] = best < 0 ? -1 : best / (kBins - 1);
+  choice[1] = best < 0 ? 0 : best % (kBins - 1);
+}
+
+// Step 5 of a node (one thread): its id from its split position, its record
+// (child boxes cl/ch, leaf children as ~slot) and the jobs of its inner
+// children, next level or small list.
+__device__ void write_node(const Job& job, uint32_t n_left, const float cl[2][3], const float ch[2][3],
+                          const uint32_t* __restrict__ idx_out, Job* __restrict__ next,
+                          uint32_t* __restrict__ next_count, Job* __restrict__ small,
+                          uint32_t* __restrict__ small_count, uint32_t out_buf, float4* __restrict__ out,
+                          uint32_t* __restrict__ root_split, uint32_t n, uint32_t* __restrict__ err) {
+  const uint32_t b = job.begin, e = job.end;
+  const uint32_t split = b + n_left;               // split position in [1, n-1]
+  uint32_t id;
+  if (job.parent_slot == 0xFFFFFFFFu) {
+    id = 0;
+    *root_split = split;
+  } else {
+    const uint32_t rs = *root_split;                // written one level earlier
+    id = split == 1 ? rs - 1 : split - 1;
+    // hand the id to the parent's child slot
+    const uint32_t p = job.parent_slot >> 1, slot = job.parent_slot & 1u;
+    reinterpret_cast<int32_t*>(out + 4 * (size_t)p + 3)[slot] = (int32_t)id;
+  }
+  if (id >= n - 1) { atomicOr(err, ERR_BUILD); return; }
+  float4* o = out + 4 * (size_t)id;
+  o[0] = make_float4(cl[0][0], ch[0][0], cl[0][1], ch[0][1]);
+  o[1] = make_float4(cl[1][0], ch[1][0], cl[1][1], ch[1][1]);
+  o[2] = make_float4(cl[0][2], ch[0][2], cl[1][2], ch[1][2]);
+  int32_t child[2] = {0, 0};
+  const uint32_t rb[2] = {b, split}, re[2] = {split, e};
+  for (int c = 0; c < 2; ++c) {
+    if (re[c] - rb[c] == 1) {
+      child[c] = ~(int32_t)idx_out[rb[c]];
+    } else {
+      const bool is_small = re[c] - rb[c] <= (uint32_t)kSmallLeaves;
+      const uint32_t at = atomicAdd(is_small ? small_count : next_count, 1u);
+      if (at >= n / 2 + 1) { atomicOr(err, ERR_BUILD); continue; }
+      // a small subtree is built later by one warp from the leaf slots this
+      // level wrote (idx buffer out_buf, kept in the depth field's top bit)
+      (is_small ? small : next)[at] =
+          Job{rb[c], re[c], id << 1 | (uint32_t)c, (job.depth + 1) | (is_small ? out_buf << 31 : 0u)};
+      child[c] = 0;                                 // filled in by the child
+    }
+  }
+  o[3] = make_float4(__int_as_float(child[0]), __int_as_float(child[1]), 0.f, 0.f);
 }
 
 // leaf box of slot k: the child box of k's parent that holds leaf ~k
@@ -197,33 +277,10 @@ k_sah_level(const float4* __restrict__ leaf_lo, const float4* __restrict__ leaf_
     __syncthreads();
     if (tid < 3 * (kBins - 1)) {
       const int a = tid / (kBins - 1), s = tid % (kBins - 1);   // split after bin s
-      float llo[3] = {INFINITY, INFINITY, INFINITY}, lhi[3] = {-INFINITY, -INFINITY, -INFINITY};
-      float rlo[3] = {INFINITY, INFINITY, INFINITY}, rhi[3] = {-INFINITY, -INFINITY, -INFINITY};
-      int nl = 0, nr = 0;
-      for (int q = 0; q < kBins; ++q) {
-        const int c = s_cnt[0][a][q];
-        if (!c) continue;
-        float* blo = q <= s ? llo : rlo;
-        float* bhi = q <= s ? lhi : rhi;
-        for (int x = 0; x < 3; ++x) {
-          blo[x] = fminf(blo[x], o2f(s_box[0][a][q][x]));
-          bhi[x] = fmaxf(bhi[x], o2f(s_box[0][a][q][3 + x]));
-        }
-        if (q <= s) nl += c; else nr += c;
-      }
-      s_cost[tid] = (cext[a] > 0.f && nl > 0 && nr > 0)
-                        ? half_area(llo, lhi) * (float)nl + half_area(rlo, rhi) * (float)nr
-                        : INFINITY;
+      s_cost[tid] = split_cost(s_cnt[0], s_box[0], cext[a], a, s);
     }
     __syncthreads();
-    if (tid == 0) {
-      int best = -1;
-      float bc = INFINITY;
-      for (int i = 0; i < 3 * (kBins - 1); ++i)
-        if (s_cost[i] < bc) { bc = s_cost[i]; best = i; }   // first of equal costs: deterministic
-      s_choice[0] = best < 0 ? -1 : best / (kBins - 1);
-      s_choice[1] = best < 0 ? 0 : best % (kBins - 1);
-    }
+    if (tid == 0) pick_split(s_cost, s_choice);
   } else if (tid == 0) {
     s_choice[0] = -1;
     s_choice[1] = 0;
@@ -329,42 +386,305 @@ k_sah_level(const float4* __restrict__ leaf_lo, const float4* __restrict__ leaf_
   }
 
   // 5. this node's id, its record, and the jobs of its inner children
-  if (tid == 0) {
-    const uint32_t split = b + n_left;               // split position in [1, n-1]
-    uint32_t id;
-    if (job.parent_slot == 0xFFFFFFFFu) {
-      id = 0;
-      *root_split = split;
-    } else {
-      const uint32_t rs = *root_split;                // written one level earlier
-      id = split == 1 ? rs - 1 : split - 1;
-      // hand the id to the parent's child slot
-      const uint32_t p = job.parent_slot >> 1, slot = job.parent_slot & 1u;
-      reinterpret_cast<int32_t*>(out + 4 * (size_t)p + 3)[slot] = (int32_t)id;
-    }
-    if (id >= n - 1) { atomicOr(err, ERR_BUILD); return; }
-    float4* o = out + 4 * (size_t)id;
-    o[0] = make_float4(cl[0][0], ch[0][0], cl[0][1], ch[0][1]);
-    o[1] = make_float4(cl[1][0], ch[1][0], cl[1][1], ch[1][1]);
-    o[2] = make_float4(cl[0][2], ch[0][2], cl[1][2], ch[1][2]);
-    int32_t child[2] = {0, 0};
-    const uint32_t rb[2] = {b, split}, re[2] = {split, e};
-    for (int c = 0; c < 2; ++c) {
-      if (re[c] - rb[c] == 1) {
-        child[c] = ~(int32_t)idx_out[rb[c]];
-      } else {
-        const bool is_small = re[c] - rb[c] <= (uint32_t)kSmallLeaves;
-        const uint32_t at = atomicAdd(is_small ? small_count : next_count, 1u);
-        if (at >= n / 2 + 1) { atomicOr(err, ERR_BUILD); continue; }
-        // a small subtree is built later by one warp from the leaf slots this
-        // level wrote (idx buffer out_buf, kept in the depth field's top bit)
-        (is_small ? small : next)[at] =
-            Job{rb[c], re[c], id << 1 | (uint32_t)c, (job.depth + 1) | (is_small ? out_buf << 31 : 0u)};
-        child[c] = 0;                                 // filled in by the child
+  if (tid == 0)
+    write_node(job, n_left, cl, ch, idx_out, next, next_count, small, small_count, out_buf, out,
+               root_split, n, err);
+}
+
+// ---------------------------------------------------------------------------
+// The top levels, where a level has few nodes of many leaves each: one block
+// per node would leave most SMs idle (level 0 of a 257k-leaf scene is one
+// block over every leaf), so each node's leaves are cut into S slices and the
+// steps above run as five launches over (node, slice) blocks, with the
+// per-node results (centroid bounds, bins, the split, left counts per slice,
+// child boxes) combined in global memory by integer atomics and sums. Every
+// combined value equals the one-block value (min / max / sums of integers),
+// the split is chosen by the same code from the same bins, and the partition
+// is stable (slices in order, each slice's lefts and rights in order), so
+// the tree is the same as the one-block build's.
+constexpr int kWideThreads = 512;
+constexpr uint32_t kWideJobs = 32;       // levels of at most this many nodes may be sliced
+constexpr uint32_t kWideMinLeaves = 16384;   // ... when their nodes average at least this many leaves
+constexpr uint32_t kWideMinSlice = 1024;     // leaves per slice, at least
+constexpr uint32_t kWideMaxSlices = 1024;    // (node, slice) blocks of a level, at most
+
+struct WideNode {                        // per node of a sliced level
+  int bounds[6];                         // centroid bounds (order-preserving images)
+  int cnt[3][kBins];
+  int box[3][kBins][6];
+  int child[2][6];                       // child boxes (order-preserving images)
+  int choice[2];                         // axis (-1: median), bin
+  uint32_t n_left;                       // final left size
+};
+
+__device__ __forceinline__ void slice_range(const Job& job, uint32_t s, uint32_t S, uint32_t& sb,
+                                            uint32_t& se) {
+  const uint64_t m = job.end - job.begin;
+  sb = job.begin + (uint32_t)(m * s / S);
+  se = job.begin + (uint32_t)(m * (s + 1) / S);
+}
+
+__global__ void k_wide_init(WideNode* __restrict__ w, uint32_t count) {
+  const uint32_t j = blockIdx.x;
+  if (j >= count) return;
+  WideNode& v = w[j];
+  for (int i = threadIdx.x; i < 3 * kBins * 7; i += blockDim.x) {
+    const int a = i / (kBins * 7), q = (i / 7) % kBins, f = i % 7;
+    if (f == 6) v.cnt[a][q] = 0;
+    else v.box[a][q][f] = f < 3 ? f2o(INFINITY) : f2o(-INFINITY);
+  }
+  if (threadIdx.x < 6) v.bounds[threadIdx.x] = threadIdx.x < 3 ? f2o(INFINITY) : f2o(-INFINITY);
+  if (threadIdx.x < 12) v.child[threadIdx.x / 6][threadIdx.x % 6] =
+      (threadIdx.x % 6) < 3 ? f2o(INFINITY) : f2o(-INFINITY);
+}
+
+// 1. centroid bounds
+__global__ void __launch_bounds__(kWideThreads)
+k_wide_bounds(const float4* __restrict__ leaf_lo, const float4* __restrict__ leaf_hi,
+              const uint32_t* __restrict__ idx_in, const Job* __restrict__ jobs, uint32_t S,
+              WideNode* __restrict__ w) {
+  __shared__ int s_red[6];
+  const uint32_t j = blockIdx.x / S, sl = blockIdx.x % S, tid = threadIdx.x;
+  const Job job = jobs[j];
+  uint32_t sb, se;
+  slice_range(job, sl, S, sb, se);
+  if (tid < 6) s_red[tid] = tid < 3 ? f2o(INFINITY) : f2o(-INFINITY);
+  __syncthreads();
+  float clo[3] = {INFINITY, INFINITY, INFINITY}, chi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  for (uint32_t i = sb + tid; i < se; i += kWideThreads) {
+    const uint32_t k = idx_in[i];
+    const float4 lo = leaf_lo[k], hi = leaf_hi[k];
+    const float c[3] = {0.5f * (lo.x + hi.x), 0.5f * (lo.y + hi.y), 0.5f * (lo.z + hi.z)};
+    for (int a = 0; a < 3; ++a) { clo[a] = fminf(clo[a], c[a]); chi[a] = fmaxf(chi[a], c[a]); }
+  }
+  for (int a = 0; a < 3; ++a) { atomicMin(&s_red[a], f2o(clo[a])); atomicMax(&s_red[3 + a], f2o(chi[a])); }
+  __syncthreads();
+  if (tid < 3) atomicMin(&w[j].bounds[tid], s_red[tid]);
+  else if (tid < 6) atomicMax(&w[j].bounds[tid], s_red[tid]);
+}
+
+// the node's centroid frame and whether it splits at the object median
+__device__ __forceinline__ bool wide_frame(const WideNode& v, const Job& job, float cmin[3], float cext[3]) {
+  bool spread = false;
+  for (int a = 0; a < 3; ++a) {
+    cmin[a] = o2f(v.bounds[a]);
+    cext[a] = o2f(v.bounds[3 + a]) - cmin[a];
+    spread |= cext[a] > 0.f;
+  }
+  const uint32_t m = job.end - job.begin;
+  const uint32_t lg = 32 - __clz(m - 1);
+  return !spread || job.depth + lg >= (uint32_t)kMaxDepth - 4;
+}
+
+// 2. bins (per-warp bins of the block, merged, added to the node's)
+__global__ void __launch_bounds__(kWideThreads)
+k_wide_bins(const float4* __restrict__ leaf_lo, const float4* __restrict__ leaf_hi,
+            const uint32_t* __restrict__ idx_in, const Job* __restrict__ jobs, uint32_t S,
+            WideNode* __restrict__ w) {
+  constexpr int kWarps = kWideThreads / 32;
+  __shared__ int s_cnt[kWarps][3][kBins];
+  __shared__ int s_box[kWarps][3][kBins][6];
+  const uint32_t j = blockIdx.x / S, sl = blockIdx.x % S, tid = threadIdx.x;
+  const Job job = jobs[j];
+  float cmin[3], cext[3];
+  if (wide_frame(w[j], job, cmin, cext)) return;         // uniform over the block
+  uint32_t sb, se;
+  slice_range(job, sl, S, sb, se);
+  for (int i = tid; i < kWarps * 3 * kBins; i += kWideThreads) {
+    const int wi = i / (3 * kBins), a = (i / kBins) % 3, q = i % kBins;
+    s_cnt[wi][a][q] = 0;
+    for (int c = 0; c < 6; ++c) s_box[wi][a][q][c] = c < 3 ? f2o(INFINITY) : f2o(-INFINITY);
+  }
+  __syncthreads();
+  for (uint32_t i = sb + tid; i < se; i += kWideThreads) {
+    const uint32_t k = idx_in[i];
+    const float4 lo = leaf_lo[k], hi = leaf_hi[k];
+    const float c[3] = {0.5f * (lo.x + hi.x), 0.5f * (lo.y + hi.y), 0.5f * (lo.z + hi.z)};
+    const float l3[3] = {lo.x, lo.y, lo.z}, h3[3] = {hi.x, hi.y, hi.z};
+    const uint32_t active = __activemask();
+    for (int a = 0; a < 3; ++a) {
+      if (!(cext[a] > 0.f)) continue;
+      const int bin = min(kBins - 1, (int)((c[a] - cmin[a]) * ((float)kBins / cext[a])));
+      const uint32_t grp = __match_any_sync(active, bin);
+      int v[6];
+      for (int q = 0; q < 3; ++q) {
+        v[q] = __reduce_min_sync(grp, f2o(l3[q]));
+        v[3 + q] = __reduce_max_sync(grp, f2o(h3[q]));
+      }
+      if ((uint32_t)(__ffs(grp) - 1) == (tid & 31)) {
+        const int wi = tid >> 5;
+        atomicAdd(&s_cnt[wi][a][bin], __popc(grp));
+        for (int q = 0; q < 3; ++q) {
+          atomicMin(&s_box[wi][a][bin][q], v[q]);
+          atomicMax(&s_box[wi][a][bin][3 + q], v[3 + q]);
+        }
       }
     }
-    o[3] = make_float4(__int_as_float(child[0]), __int_as_float(child[1]), 0.f, 0.f);
   }
+  __syncthreads();
+  for (int i = tid; i < 3 * kBins * 7; i += kWideThreads) {
+    const int a = i / (kBins * 7), q = (i / 7) % kBins, f = i % 7;
+    if (f == 6) {
+      int t = 0;
+      for (int wi = 0; wi < kWarps; ++wi) t += s_cnt[wi][a][q];
+      if (t) atomicAdd(&w[j].cnt[a][q], t);
+    } else {
+      int v = s_box[0][a][q][f];
+      for (int wi = 1; wi < kWarps; ++wi) v = f < 3 ? min(v, s_box[wi][a][q][f]) : max(v, s_box[wi][a][q][f]);
+      if (f < 3) { if (v != f2o(INFINITY)) atomicMin(&w[j].box[a][q][f], v); }
+      else if (v != f2o(-INFINITY)) atomicMax(&w[j].box[a][q][f], v);
+    }
+  }
+}
+
+// the node's split from its merged bins (every block of the node the same)
+__device__ void wide_choice(const WideNode& v, const Job& job, float cmin[3], float cext[3],
+                            float* s_cost, int* s_choice) {
+  const uint32_t tid = threadIdx.x;
+  const bool median = wide_frame(v, job, cmin, cext);
+  if (!median && tid < 3 * (kBins - 1)) {
+    const int a = tid / (kBins - 1), s = tid % (kBins - 1);
+    s_cost[tid] = split_cost(v.cnt, v.box, cext[a], a, s);
+  }
+  __syncthreads();
+  if (tid == 0) {
+    if (median) { s_choice[0] = -1; s_choice[1] = 0; }
+    else pick_split(s_cost, s_choice);
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ bool goes_left(const float4& lo, const float4& hi, int axis, int split_bin,
+                                          const float cmin[3], const float cext[3]) {
+  const float c = 0.5f * ((&lo.x)[axis] + (&hi.x)[axis]);
+  return min(kBins - 1, (int)((c - cmin[axis]) * ((float)kBins / cext[axis]))) <= split_bin;
+}
+
+// 3. the split, and the left count of each slice
+__global__ void __launch_bounds__(kWideThreads)
+k_wide_count(const float4* __restrict__ leaf_lo, const float4* __restrict__ leaf_hi,
+             const uint32_t* __restrict__ idx_in, const Job* __restrict__ jobs, uint32_t S,
+             WideNode* __restrict__ w, uint32_t* __restrict__ slice_left) {
+  __shared__ float s_cost[3 * (kBins - 1)];
+  __shared__ int s_choice[2];
+  __shared__ uint32_t s_sum;
+  const uint32_t j = blockIdx.x / S, sl = blockIdx.x % S, tid = threadIdx.x;
+  const Job job = jobs[j];
+  float cmin[3], cext[3];
+  wide_choice(w[j], job, cmin, cext, s_cost, s_choice);
+  const int axis = s_choice[0], split_bin = s_choice[1];
+  if (sl == 0 && tid == 0) { w[j].choice[0] = axis; w[j].choice[1] = split_bin; }
+  if (axis < 0) return;
+  uint32_t sb, se;
+  slice_range(job, sl, S, sb, se);
+  if (tid == 0) s_sum = 0;
+  __syncthreads();
+  uint32_t c = 0;
+  for (uint32_t i = sb + tid; i < se; i += kWideThreads) {
+    const uint32_t k = idx_in[i];
+    c += goes_left(leaf_lo[k], leaf_hi[k], axis, split_bin, cmin, cext) ? 1u : 0u;
+  }
+  c = __reduce_add_sync(0xFFFFFFFFu, c);
+  if ((tid & 31) == 0) atomicAdd(&s_sum, c);
+  __syncthreads();
+  if (tid == 0) slice_left[blockIdx.x] = s_sum;
+}
+
+// 4. stable scatter of each slice (lefts, then rights, in order) and the
+//    child boxes
+__global__ void __launch_bounds__(kWideThreads)
+k_wide_scatter(const float4* __restrict__ leaf_lo, const float4* __restrict__ leaf_hi,
+               const uint32_t* __restrict__ idx_in, uint32_t* __restrict__ idx_out,
+               const Job* __restrict__ jobs, uint32_t S, WideNode* __restrict__ w,
+               const uint32_t* __restrict__ slice_left) {
+  constexpr int kWarps = kWideThreads / 32;
+  __shared__ uint32_t s_scan[kWarps];
+  __shared__ int s_red[12];
+  const uint32_t j = blockIdx.x / S, sl = blockIdx.x % S, tid = threadIdx.x;
+  const uint32_t lane = tid & 31, warp = tid >> 5;
+  const Job job = jobs[j];
+  const uint32_t b = job.begin, m = job.end - job.begin;
+  float cmin[3], cext[3];
+  wide_frame(w[j], job, cmin, cext);
+  const int axis = w[j].choice[0], split_bin = w[j].choice[1];
+  uint32_t before = 0, n_left = 0;
+  if (axis >= 0)
+    for (uint32_t q = 0; q < S; ++q) {
+      const uint32_t v = slice_left[j * S + q];
+      if (q < sl) before += v;
+      n_left += v;
+    }
+  // an empty side cannot happen (the scatter repeats the binning
+  // arithmetic); the object median stands in, as in the one-block build
+  const bool median = axis < 0 || n_left == 0 || n_left == m;
+  if (median) n_left = m / 2;
+  if (sl == 0 && tid == 0) w[j].n_left = n_left;
+  uint32_t sb, se;
+  slice_range(job, sl, S, sb, se);
+  if (tid < 12) s_red[tid] = (tid % 6) < 3 ? f2o(INFINITY) : f2o(-INFINITY);
+  float l[2][3], h[2][3];
+  for (int c = 0; c < 2; ++c)
+    for (int x = 0; x < 3; ++x) { l[c][x] = INFINITY; h[c][x] = -INFINITY; }
+  uint32_t cnt_left = 0;
+  const uint32_t rights_before = (sb - b) - before;
+  for (uint32_t base = sb; base < se; base += kWideThreads) {
+    const uint32_t i = base + tid;
+    bool left = false;
+    uint32_t k = 0;
+    float4 lo = make_float4(0.f, 0.f, 0.f, 0.f), hi = lo;
+    if (i < se) {
+      k = idx_in[i];
+      lo = leaf_lo[k];
+      hi = leaf_hi[k];
+      left = median ? (i - b) < n_left : goes_left(lo, hi, axis, split_bin, cmin, cext);
+    }
+    const uint32_t ball = __ballot_sync(0xFFFFFFFFu, left);
+    __syncthreads();
+    if (lane == 0) s_scan[warp] = __popc(ball);
+    __syncthreads();
+    uint32_t wb = 0, chunk = 0;
+    for (uint32_t q = 0; q < (uint32_t)kWarps; ++q) {
+      if (q < warp) wb += s_scan[q];
+      chunk += s_scan[q];
+    }
+    const uint32_t rank = wb + __popc(ball & ((1u << lane) - 1u));   // lefts before i in the chunk
+    if (i < se) {
+      const uint32_t t = i - base;
+      if (median) idx_out[i] = k;
+      else if (left) idx_out[b + before + cnt_left + rank] = k;
+      else idx_out[b + n_left + rights_before + ((base - sb) - cnt_left) + (t - rank)] = k;
+      const int c = left ? 0 : 1;
+      l[c][0] = fminf(l[c][0], lo.x); l[c][1] = fminf(l[c][1], lo.y); l[c][2] = fminf(l[c][2], lo.z);
+      h[c][0] = fmaxf(h[c][0], hi.x); h[c][1] = fmaxf(h[c][1], hi.y); h[c][2] = fmaxf(h[c][2], hi.z);
+    }
+    cnt_left += chunk;
+  }
+  for (int c = 0; c < 2; ++c)
+    for (int x = 0; x < 3; ++x) {
+      atomicMin(&s_red[6 * c + x], f2o(l[c][x]));
+      atomicMax(&s_red[6 * c + 3 + x], f2o(h[c][x]));
+    }
+  __syncthreads();
+  if (tid < 12) {
+    const int c = tid / 6, f = tid % 6;
+    if (f < 3) { if (s_red[tid] != f2o(INFINITY)) atomicMin(&w[j].child[c][f], s_red[tid]); }
+    else if (s_red[tid] != f2o(-INFINITY)) atomicMax(&w[j].child[c][f], s_red[tid]);
+  }
+}
+
+// 5. the node records and the next jobs (one thread per node)
+__global__ void k_wide_nodes(const Job* __restrict__ jobs, uint32_t count, const WideNode* __restrict__ w,
+                             const uint32_t* __restrict__ idx_out, Job* __restrict__ next,
+                             uint32_t* __restrict__ next_count, Job* __restrict__ small,
+                             uint32_t* __restrict__ small_count, uint32_t out_buf, float4* __restrict__ out,
+                             uint32_t* __restrict__ root_split, uint32_t n, uint32_t* __restrict__ err) {
+  const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= count) return;
+  float cl[2][3], ch[2][3];
+  for (int c = 0; c < 2; ++c)
+    for (int x = 0; x < 3; ++x) { cl[c][x] = o2f(w[j].child[c][x]); ch[c][x] = o2f(w[j].child[c][3 + x]); }
+  write_node(jobs[j], w[j].n_left, cl, ch, idx_out, next, next_count, small, small_count, out_buf, out,
+             root_split, n, err);
 }
 
 // warp-wide inclusive scan of a box (lanes in order), forward or backward
@@ -540,7 +860,8 @@ k_sah_small(const float4* __restrict__ leaf_lo, const float4* __restrict__ leaf_
 
 size_t sah_tmp_bytes(uint32_t n) {
   const size_t nn = n ? n : 1;
-  return 2 * nn * sizeof(float4) + 2 * nn * sizeof(uint32_t) + 3 * (nn / 2 + 1) * sizeof(Job) + 256;
+  return 2 * nn * sizeof(float4) + 2 * nn * sizeof(uint32_t) + 3 * (nn / 2 + 1) * sizeof(Job) + 256 +
+         kWideJobs * sizeof(WideNode) + kWideMaxSlices * sizeof(uint32_t) + 256;
 }
 
 cudaError_t build_sah_tree(const float4* lbvh_nodes, const int32_t* parent, uint32_t n,
@@ -559,6 +880,9 @@ cudaError_t build_sah_tree(const float4* lbvh_nodes, const int32_t* parent, uint
   Job* small = reinterpret_cast<Job*>(p); p += max_jobs * sizeof(Job);
   uint32_t** d_bufs = reinterpret_cast<uint32_t**>(p); p += 2 * sizeof(uint32_t*);
   uint32_t* counters = reinterpret_cast<uint32_t*>(p);   // [0] next count, [1] root split, [2] small count
+  p += 256 - 2 * sizeof(uint32_t*);
+  WideNode* wide = reinterpret_cast<WideNode*>(p); p += kWideJobs * sizeof(WideNode);
+  uint32_t* slice_left = reinterpret_cast<uint32_t*>(p);
   const int g = (int)((n + 255) / 256);
   k_leaf_boxes<<<g, 256, 0, st>>>(lbvh_nodes, parent, n, lo, hi);
   k_iota<<<g, 256, 0, st>>>(idx[0], n);
@@ -572,7 +896,23 @@ cudaError_t build_sah_tree(const float4* lbvh_nodes, const int32_t* parent, uint
     const int cur = level & 1;
     e = cudaMemsetAsync(counters, 0, sizeof(uint32_t), st);
     if (e != cudaSuccess) break;
-    if (count < kTopJobs)
+    // few nodes of many leaves each: slice every node over several blocks
+    const uint32_t per_job = n / count;
+    if (count <= kWideJobs && per_job >= kWideMinLeaves) {
+      uint32_t S = (2u * (uint32_t)num_sms() + count - 1) / count;
+      S = std::min(S, std::min(per_job / kWideMinSlice, kWideMaxSlices / count));
+      S = std::max(S, 1u);
+      const uint32_t blocks = count * S;
+      k_wide_init<<<count, 256, 0, st>>>(wide, count);
+      k_wide_bounds<<<blocks, kWideThreads, 0, st>>>(lo, hi, idx[cur], jobs[cur], S, wide);
+      k_wide_bins<<<blocks, kWideThreads, 0, st>>>(lo, hi, idx[cur], jobs[cur], S, wide);
+      k_wide_count<<<blocks, kWideThreads, 0, st>>>(lo, hi, idx[cur], jobs[cur], S, wide, slice_left);
+      k_wide_scatter<<<blocks, kWideThreads, 0, st>>>(lo, hi, idx[cur], idx[cur ^ 1], jobs[cur], S, wide,
+                                                      slice_left);
+      k_wide_nodes<<<(count + 31) / 32, 32, 0, st>>>(jobs[cur], count, wide, idx[cur ^ 1], jobs[cur ^ 1],
+                                                     counters, small, counters + 2, (uint32_t)(cur ^ 1),
+                                                     out, counters + 1, n, err);
+    } else if (count < kTopJobs)
       k_sah_level<kSahThreadsTop><<<count, kSahThreadsTop, 0, st>>>(
           lo, hi, idx[cur], idx[cur ^ 1], jobs[cur], count, jobs[cur ^ 1], counters, small,
           counters + 2, (uint32_t)(cur ^ 1), out, counters + 1, n, err);
