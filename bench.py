@@ -59,6 +59,9 @@ def parse():
                          "(0 = every pixel of one stereo pair)")
     ap.add_argument("--ncu", action="store_true",
                     help="profiling mode: build the scene, render twice, exit")
+    ap.add_argument("--ncu-terrain", action="store_true",
+                    help="profiling mode: build the 4K terrain scene and render frame 0 of its "
+                         "flight twice with rt_render_stereo, exit")
     ap.add_argument("--ncu-net", action="store_true",
                     help="profiling mode: run the retrace network on 1080p features twice, exit")
     ap.add_argument("--fp8", action="store_true",
@@ -726,6 +729,25 @@ def run_ncu_net(args):
     net.close()
 
 
+def run_ncu_terrain():
+    """Two renders of the terrain sequence's first stereo frame (3840x2160 per
+    eye, 10M triangles: the scene exceeds L2)."""
+    import torch
+
+    from paper_1702_01530_gb300 import build as rtbuild
+    from paper_1702_01530_gb300 import capi, scenegen as sg
+    rtbuild.build()
+    s = sg.config_terrain()
+    cam = sg.terrain_cameras(5, 1)[0]
+    g = capi.GpuScene(s)
+    img = torch.empty((2, s.H, s.W, 3), dtype=torch.float32, device="cuda")
+    for _ in range(2):
+        capi.rt_render_stereo(g.handle, cam, s.eye_sep, s.convergence, s.W, s.H, s.max_depth,
+                              img[0], img[1])
+    capi.rt_sync_status(g.handle)
+    g.close()
+
+
 # ------------------------------------------------------------------ study
 def _event_ms(fn, stream, reps=20, warm=3, flush=None):
     """Median CUDA-event time of fn() on ``stream``."""
@@ -908,6 +930,9 @@ def main():
     rank, world, local = dist_setup(args)
     if args.ncu_net:
         run_ncu_net(args)
+        return
+    if args.ncu_terrain:
+        run_ncu_terrain()
         return
     if args.study:
         if rank == 0:

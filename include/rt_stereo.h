@@ -231,6 +231,28 @@ int rt_debug_set_node(rt_scene* scene, uint32_t node, int32_t left, int32_t righ
                       int empty_right);
 
 /*
+ * rt_debug_get_sah_tree -- TEST HOOK. Copies the scene's SAH render tree (the
+ * tree RT_TREE_SAH renders walk, rebuilt from the LBVH's leaves) to the HOST
+ * array nodes[(n-1)*16] (n = primitives; nothing is copied when n == 1): per
+ * inner node (root 0) 16 words, the FP32 child boxes as lo.x, hi.x, lo.y, hi.y
+ * of child 0, the same of child 1, lo.z, hi.z of child 0, lo.z, hi.z of child
+ * 1, then the two children as int32 bit patterns (>= 0 inner node, < 0 leaf
+ * ~k, k indexing the LBVH's sorted primitives) and two unused words.
+ * Synchronises the device. RT_ERR_INVALID_ARG for a NULL scene or nodes.
+ */
+int rt_debug_get_sah_tree(const rt_scene* scene, float* nodes);
+
+/*
+ * rt_debug_set_sah_slicing -- TEST HOOK. Process-wide: with enable != 0 (the
+ * default) scene creation builds the top levels of the SAH tree (levels of at
+ * most 32 nodes averaging at least 16384 leaves) with every node sliced over
+ * many blocks; with 0 every level runs one block per node. Both give the same
+ * tree; the switch lets a test compare them. Host-only; affects scenes
+ * created afterwards. Returns RT_OK.
+ */
+int rt_debug_set_sah_slicing(int enable);
+
+/*
  * rt_debug_set_pool_capacity -- TEST HOOK; the paper has no counterpart.
  * Limits the two drain pools of the scene's renders to `entries` rays each
  * (0 restores the full capacity, which is 128 rays per warp of the render

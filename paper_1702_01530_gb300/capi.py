@@ -55,6 +55,8 @@ _SIGS = {
     "rt_scene_get_bvh": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "rt_scene_num_prims": (_u32, [_vp]),
     "rt_debug_set_pool_capacity": (ctypes.c_int, [_vp, _u32]),
+    "rt_debug_get_sah_tree": (ctypes.c_int, [_vp, _vp]),
+    "rt_debug_set_sah_slicing": (ctypes.c_int, [ctypes.c_int]),
     "rt_debug_set_node": (ctypes.c_int, [_vp, _u32, ctypes.c_int32, ctypes.c_int32,
                                          ctypes.c_int]),
     "rt_profile_enable": (ctypes.c_int, [_vp, ctypes.c_int]),
@@ -239,6 +241,18 @@ def rt_debug_set_node(scene, node, left, right, empty_right=False):
 
 def rt_debug_set_pool_capacity(scene, entries):
     _check(lib().rt_debug_set_pool_capacity(scene, entries))
+
+
+def rt_debug_get_sah_tree(scene) -> np.ndarray:
+    """The SAH render tree as (n-1, 16) uint32 words (boxes as FP32 bits)."""
+    n = rt_scene_num_prims(scene)
+    out = np.zeros((max(n - 1, 1), 16), np.uint32)
+    _check(lib().rt_debug_get_sah_tree(scene, out.ctypes.data))
+    return out[:max(n - 1, 0)]
+
+
+def rt_debug_set_sah_slicing(enable):
+    _check(lib().rt_debug_set_sah_slicing(int(bool(enable))))
 
 
 STAGES = ("clear", "trace", "resolve", "warp", "net", "mask", "retrace", "compose")

@@ -550,6 +550,22 @@ int rt_debug_set_node(rt_scene* scene, uint32_t node, int32_t left, int32_t righ
   return RT_OK;
 }
 
+int rt_debug_get_sah_tree(const rt_scene* scene, float* nodes) {
+  if (!scene || !nodes) return fail(RT_ERR_INVALID_ARG, "scene or nodes is NULL");
+  if (scene->n < 2) return RT_OK;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess)
+    e = cudaMemcpy(nodes, scene->nodes_sah, (size_t)(scene->n - 1) * 4 * sizeof(float4),
+                   cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "SAH tree download");
+  return RT_OK;
+}
+
+int rt_debug_set_sah_slicing(int enable) {
+  rt::set_sah_slicing(enable != 0);
+  return RT_OK;
+}
+
 int rt_debug_set_pool_capacity(rt_scene* scene, uint32_t entries) {
   if (!scene) return fail(RT_ERR_INVALID_ARG, "scene is NULL");
   scene->ws.cap_p_limit = entries;

@@ -173,6 +173,7 @@ size_t sah_tmp_bytes(uint32_t n);
 cudaError_t build_sah_tree(const float4* lbvh_nodes, const int32_t* parent, uint32_t n,
                            float4* out, void* tmp, uint32_t* err, cudaStream_t st);
 size_t bvh4_tmp_bytes(uint32_t n);
+void set_sah_slicing(bool on);   // slice the top levels of the SAH build (default on)
 cudaError_t inner_parents(const float4* nodes, uint32_t n, int32_t* parent, cudaStream_t st);
 cudaError_t build_bvh4(const float4* nodes, const int32_t* parent, uint32_t n, int top_depth,
                        float4* nodes4, uint32_t* counts_dev, void* tmp, cudaStream_t st);

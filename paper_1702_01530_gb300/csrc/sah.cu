@@ -858,6 +858,12 @@ k_sah_small(const float4* __restrict__ leaf_lo, const float4* __restrict__ leaf_
 
 }  // namespace
 
+namespace {
+bool g_sah_slicing = true;
+}  // namespace
+
+void set_sah_slicing(bool on) { g_sah_slicing = on; }
+
 size_t sah_tmp_bytes(uint32_t n) {
   const size_t nn = n ? n : 1;
   return 2 * nn * sizeof(float4) + 2 * nn * sizeof(uint32_t) + 3 * (nn / 2 + 1) * sizeof(Job) + 256 +
@@ -898,7 +904,7 @@ cudaError_t build_sah_tree(const float4* lbvh_nodes, const int32_t* parent, uint
     if (e != cudaSuccess) break;
     // few nodes of many leaves each: slice every node over several blocks
     const uint32_t per_job = n / count;
-    if (count <= kWideJobs && per_job >= kWideMinLeaves) {
+    if (g_sah_slicing && count <= kWideJobs && per_job >= kWideMinLeaves) {
       uint32_t S = (2u * (uint32_t)num_sms() + count - 1) / count;
       S = std::min(S, std::min(per_job / kWideMinSlice, kWideMaxSlices / count));
       S = std::max(S, 1u);

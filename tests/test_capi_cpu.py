@@ -75,6 +75,7 @@ def test_render_rejects_null_scene_and_bad_view(lib):
         capi.rt_sync_status(None, stream=0)
     assert lib.rt_debug_set_node(None, 0, 0, 0, 0) == capi.RT_ERR_INVALID_ARG
     assert lib.rt_debug_set_pool_capacity(None, 0) == capi.RT_ERR_INVALID_ARG
+    assert lib.rt_debug_get_sah_tree(None, None) == capi.RT_ERR_INVALID_ARG
     assert lib.rt_render_stereo_sequence(None, None, 1, 0.065, 10.0, 8, 8, 1, None, None,
                                          None) == capi.RT_ERR_INVALID_ARG
     assert "NULL" in capi.rt_last_error()

@@ -168,6 +168,31 @@ def test_sah_tree_is_another_tree_with_the_same_results():
     assert 0.5 < sah["work"][:, 1:].sum() / lbvh["work"][:, 1:].sum() < 2.0
 
 
+def test_sliced_sah_build_gives_the_one_block_tree():
+    # the top levels of a 257k-primitive scene are built with each node sliced
+    # over many blocks; with slicing off every level runs one block per node:
+    # the same tree word for word
+    s = sg.config_blobs(2, W=64, H=36)
+    trees = []
+    try:
+        for slicing in (True, False):
+            capi.rt_debug_set_sah_slicing(slicing)
+            g = capi.GpuScene(s)
+            try:
+                trees.append(capi.rt_debug_get_sah_tree(g.handle))
+            finally:
+                g.close()
+    finally:
+        capi.rt_debug_set_sah_slicing(True)
+    assert trees[0].shape == (s.n_prims - 1, 16)
+    assert np.array_equal(trees[0], trees[1])
+    # a valid binary tree over every leaf: each leaf and inner node (but the root) once
+    kids = trees[0][:, 12:14].view(np.int32).ravel()
+    n = trees[0].shape[0] + 1
+    assert np.array_equal(np.sort(~kids[kids < 0]), np.arange(n))
+    assert np.array_equal(np.sort(kids[kids >= 0]), np.arange(1, n - 1))
+
+
 def test_host_render_matches_device_render():
     import torch
     s = sg.config_small(2, W=80, H=60)
