@@ -282,8 +282,11 @@ int rt_debug_set_pool_capacity(rt_scene* scene, uint32_t entries);
  *   RT_TREE_LBVH (2) the Morton-code binary radix tree itself, the tree
  *                rt_scene_get_bvh returns and rt_debug_set_node edits.
  * The instrumented work counts of rt_render_stereo_aux follow the binary
- * tree in use (the SAH tree for RT_TREE_WIDE). Other values:
- * RT_ERR_INVALID_ARG.
+ * tree in use (the SAH tree for RT_TREE_WIDE). The 4-wide tree is built the
+ * first time it is chosen (synchronous: the device is synchronised and a
+ * scratch buffer of ~21 bytes per primitive is allocated and freed; errors
+ * RT_ERR_CUDA); choosing a tree is otherwise host-only and takes effect with
+ * the next render. Other values: RT_ERR_INVALID_ARG.
  */
 #define RT_TREE_SAH 0
 #define RT_TREE_WIDE 1

@@ -261,12 +261,7 @@ int rt_scene_create(const rt_sphere* spheres, uint32_t n_spheres, const rt_trian
   // temporary: raw input records + LBVH scratch
   const size_t b_sph = align256((size_t)n_spheres * sizeof(rt_sphere) + 16);
   const size_t b_tri = align256((size_t)n_tris * sizeof(rt_triangle) + 16);
-  // 256-byte multiple: the two uint32 counts of the 4-wide build follow it;
-  // the 4-wide build also keeps the SAH tree's inner parents after its own
-  // scratch
-  const size_t b_tmp = align256(std::max(rt::lbvh_tmp_bytes((uint32_t)n),
-                                         std::max(align256(rt::bvh4_tmp_bytes((uint32_t)n)) + 4 * (size_t)n,
-                                                  rt::sah_tmp_bytes((uint32_t)n))));
+  const size_t b_tmp = align256(std::max(rt::lbvh_tmp_bytes((uint32_t)n), rt::sah_tmp_bytes((uint32_t)n)));
   void* tmp = nullptr;
   e = cudaMalloc(&tmp, b_sph + b_tri + b_tmp + 256);
   if (e != cudaSuccess) { cudaGetLastError(); rt_scene_destroy(sc); return cuda_fail(e, "build scratch allocation"); }
@@ -284,24 +279,10 @@ int rt_scene_create(const rt_sphere* spheres, uint32_t n_spheres, const rt_trian
   // the render tree: SAH splits over the LBVH's leaves
   if (e == cudaSuccess)
     e = rt::build_sah_tree(sc->nodes, sc->parent, (uint32_t)n, sc->nodes_sah, d_lbvh, sc->err, st);
-  // the 4-wide tree, collapsed from the SAH tree (whose inner parents go
-  // after the 4-wide build's scratch); its counts go to the spare 256 bytes
-  // after the scratch. From the SAH tree rather than the LBVH: 1.28 against
-  // 1.40 ms on the 1080p blob pair
-  uint32_t* d_counts = reinterpret_cast<uint32_t*>(tp + b_sph + b_tri + b_tmp);
-  if (e == cudaSuccess) e = cudaMemsetAsync(d_counts, 0, 2 * sizeof(uint32_t), st);
-  int32_t* sah_parent = reinterpret_cast<int32_t*>(static_cast<char*>(d_lbvh) +
-                                                   align256(rt::bvh4_tmp_bytes((uint32_t)n)));
-  if (e == cudaSuccess) e = rt::inner_parents(sc->nodes_sah, (uint32_t)n, sah_parent, st);
-  if (e == cudaSuccess)
-    e = rt::build_bvh4(sc->nodes_sah, sah_parent, (uint32_t)n, rt::treelet_depth(), sc->nodes4,
-                       d_counts, d_lbvh, st);
-  uint32_t counts[2] = {0, 0};
-  if (e == cudaSuccess) e = cudaMemcpyAsync(counts, d_counts, sizeof counts, cudaMemcpyDeviceToHost, st);
+  // (the 4-wide tree is built when a render first asks for it:
+  // rt_scene_set_traversal)
   if (e == cudaSuccess) e = cudaMemcpyAsync(sc->h_err, sc->err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  sc->n_top = counts[0];
-  sc->n4 = counts[1];
   cudaFree(tmp);
   if (e != cudaSuccess) { rt_scene_destroy(sc); return cuda_fail(e, "BVH build"); }
   if (*sc->h_err) {
@@ -576,6 +557,33 @@ int rt_scene_set_traversal(rt_scene* scene, int tree) {
   if (!scene) return fail(RT_ERR_INVALID_ARG, "scene is NULL");
   if (tree != RT_TREE_SAH && tree != RT_TREE_WIDE && tree != RT_TREE_LBVH)
     return fail(RT_ERR_INVALID_ARG, "tree must be RT_TREE_SAH, RT_TREE_WIDE or RT_TREE_LBVH");
+  if (tree == RT_TREE_WIDE && !scene->wide_built && scene->n > 1) {
+    // the 4-wide tree, collapsed from the SAH tree (1.28 against 1.40 ms on
+    // the 1080p blob pair when collapsed from the LBVH); scratch: the build's
+    // own, then the SAH tree's inner parents, then two counts
+    const uint32_t n = scene->n;
+    const size_t b4 = align256(rt::bvh4_tmp_bytes(n)), bp = align256(4 * (size_t)n);
+    void* tmp = nullptr;
+    cudaError_t e = cudaSetDevice(scene->device);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMalloc(&tmp, b4 + bp + 256);
+    if (e != cudaSuccess) { cudaGetLastError(); return cuda_fail(e, "4-wide tree scratch"); }
+    char* t = static_cast<char*>(tmp);
+    int32_t* sah_parent = reinterpret_cast<int32_t*>(t + b4);
+    uint32_t* d_counts = reinterpret_cast<uint32_t*>(t + b4 + bp);
+    uint32_t counts[2] = {0, 0};
+    e = cudaMemset(d_counts, 0, 2 * sizeof(uint32_t));
+    if (e == cudaSuccess) e = rt::inner_parents(scene->nodes_sah, n, sah_parent, 0);
+    if (e == cudaSuccess)
+      e = rt::build_bvh4(scene->nodes_sah, sah_parent, n, rt::treelet_depth(), scene->nodes4, d_counts,
+                         tmp, 0);
+    if (e == cudaSuccess) e = cudaMemcpy(counts, d_counts, sizeof counts, cudaMemcpyDeviceToHost);
+    cudaFree(tmp);
+    if (e != cudaSuccess) return cuda_fail(e, "4-wide tree build");
+    scene->n_top = counts[0];
+    scene->n4 = counts[1];
+    scene->wide_built = true;
+  }
   scene->tree = tree;
   return RT_OK;
 }

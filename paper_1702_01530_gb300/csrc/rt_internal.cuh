@@ -238,6 +238,7 @@ struct rt_scene {
   float4* nodes4 = nullptr;
   float4* nodes_sah = nullptr; // binary tree rebuilt with the SAH over the same leaves (sah.cu)
   uint32_t n4 = 0, n_top = 0;
+  bool wide_built = false;     // nodes4 holds the 4-wide tree (built on first use)
   int tree = RT_TREE_SAH;      // the tree renders walk (rt_scene_set_traversal)
   float4* prims = nullptr;
   float4* mats = nullptr;

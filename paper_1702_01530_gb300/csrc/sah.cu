@@ -12,10 +12,11 @@
 // same image 11 % faster. Any binary tree over the same conservative leaf
 // boxes yields the same closest hit and the same any-hit answer.
 //
-// Scene creation with this build (GB300; upload, LBVH, SAH tree, 4-wide
-// tree): the blob scene's 257k primitives 4.5 ms, the 10M-triangle terrain
-// 95 ms (one block per node on every level: 6.3 ms and 0.18 s; with 256
-// threads for every level and no bin combining: 12.2 ms and 0.49 s).
+// Scene creation with this build (GB300; upload, LBVH, SAH tree): the blob
+// scene's 257k primitives 4.0 ms, the 10M-triangle terrain 77 ms (with the
+// 4-wide tree built too: 4.5 ms and 95 ms; with one block per node on every
+// level: 6.3 ms and 0.18 s; with 256 threads for every level and no bin
+// combining: 12.2 ms and 0.49 s).
 // One level of the tree per launch, one block per node of the level (nodes
 // of at most kSmallLeaves leaves: their whole subtree in one warp):
 //   1. centroid bounds of the node's leaves (block reduction);
