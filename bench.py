@@ -677,10 +677,11 @@ def run_reference(args, rank, world):
     total = 2 * s.W * s.H
     rng = np.random.default_rng(11)
     t0 = time.perf_counter()
-    osc.render(pixels=rng.choice(total, size=65536, replace=False), n_threads=cores)
-    rate = 65536 / max(time.perf_counter() - t0, 1e-6)          # pixels per second
+    n_cal = min(65536, total)
+    osc.render(pixels=rng.choice(total, size=n_cal, replace=False), n_threads=cores)
+    rate = n_cal / max(time.perf_counter() - t0, 1e-6)          # pixels per second
     budget = 60.0 / max(1, args.steps + args.warmup)
-    per_step = int(min(total, max(4096, rate * budget)))
+    per_step = int(min(total, max(min(4096, total), rate * budget)))
     if args.cpu_sample:
         per_step = min(total, args.cpu_sample)
     for _ in range(args.warmup):
