@@ -8,8 +8,8 @@
 // two rays of a pixel in neighbouring lanes, so the eyes' nearly identical
 // rays fetch the same BVH nodes in the same load and their shadow and mirror
 // rays queue side by side (1080p blob pair: 1.143 -> 1.042 ms against 8x4
-// tiles of one eye, eyes alternating between warps). Renders of one eye use
-// 8x4 tiles.
+// tiles of one eye, eyes alternating between warps). Renders of one eye, and
+// of scenes of fewer than kPairEyesPrims primitives, use those 8x4 tiles.
 //
 // Per stereo pair:
 //   k_render   one persistent kernel. Every warp owns two small wavefront
@@ -62,6 +62,7 @@ struct KParams {
   uint32_t epoch;      // this render's epoch (> 0)
   uint32_t n_tiles;    // primary tiles of 32 rays (pixel list: 32 entries each)
   bool share_partial;  // drain: hand over backlogs of less than a round too
+  bool pair_eyes;      // primary tiles of 4x4 pixels of both eyes (else 8x4 of one eye)
 };
 
 constexpr uint32_t kNullPix = 0xFFFFFFFFu;   // pool entry that carries no ray
@@ -70,6 +71,11 @@ constexpr uint32_t kSpinMax = 1u << 22;        // bound of every wait on another
 // (1080p blob pair, 257k primitives: 1.301 ms sharing everything, 1.330
 // keeping partial backlogs; small scene, 10 primitives: 0.262 against 0.239)
 constexpr uint32_t kSharePartialPrims = 1024;
+// scenes of at least this many primitives trace both eyes of a pixel in one
+// warp; in smaller ones the walks are a few nodes long and 8x4 tiles of one
+// eye, eyes alternating between warps, are faster (polyhedra of 12-180
+// triangles at 1080p: 5-9 % with one or two lights)
+constexpr uint32_t kPairEyesPrims = 1024;
 
 // Polls use relaxed (L2-coherent) loads: an acquire load would invalidate
 // the SM's L1, which holds the top of the BVH for every warp on the SM. A
@@ -317,17 +323,18 @@ k_render(KParams kp) {
         const uint32_t pi = pix - eye * P;
         py = pi / cam.W;
         px = pi - py * cam.W;
-      } else if (a.eyes == 3u) {           // 4x4 pixels of both eyes: lane 2q left, 2q+1 right
+      } else if (a.eyes == 3u && kp.pair_eyes) {   // 4x4 pixels of both eyes: lane 2q left, 2q+1 right
         const uint32_t tx4 = (cam.W + 3u) / 4u, q = lane >> 1;
         eye = lane & 1u;
         px = (tile % tx4) * 4u + (q & 3u);
         py = (tile / tx4) * 4u + (q >> 2);
         active = px < cam.W && py < cam.H;
         pix = eye * P + py * cam.W + px;
-      } else {                             // one eye: 8x4 tiles
-        eye = a.eyes == 2u ? 1u : 0u;
-        px = (tile % cam.tiles_x) * 8u + (lane & 7u);
-        py = (tile / cam.tiles_x) * 4u + (lane >> 3);
+      } else {                             // 8x4 tiles of one eye, eyes alternating when both are traced
+        const uint32_t tt = a.eyes == 3u ? tile >> 1 : tile;
+        eye = a.eyes == 3u ? (tile & 1u) : (a.eyes == 2u ? 1u : 0u);
+        px = (tt % cam.tiles_x) * 8u + (lane & 7u);
+        py = (tt / cam.tiles_x) * 4u + (lane >> 3);
         active = px < cam.W && py < cam.H;
         pix = eye * P + py * cam.W + px;
       }
@@ -497,9 +504,10 @@ cudaError_t render_impl(const RenderArgs& a, Workspace& ws, cudaStream_t st) {
   kp.counters = ws.counters;
   kp.cap_s = ws.cap_s;
   kp.cap_r = ws.cap_r;
+  kp.pair_eyes = a.eyes == 3u && a.sc.n_prims >= kPairEyesPrims;
   kp.n_tiles = a.plist ? (a.plist_n + 31u) / 32u
-             : a.eyes == 3u ? ((a.cam.W + 3u) / 4u) * a.cam.tiles_y   // 4x4 pixels, both eyes
-                            : a.cam.tiles_x * a.cam.tiles_y;          // 8x4 pixels, one eye
+             : kp.pair_eyes ? ((a.cam.W + 3u) / 4u) * a.cam.tiles_y   // 4x4 pixels, both eyes
+                            : (a.eyes == 3u ? 2u : 1u) * a.cam.tiles_x * a.cam.tiles_y;   // 8x4, one eye
   const int grid = render_grid();
   if ((uint64_t)grid * (kThreads / 32) > ws.n_warps) return cudaErrorInvalidValue;
   kp.share_partial = a.sc.n_prims >= kSharePartialPrims;
