@@ -1,6 +1,7 @@
 """Batched stereo rendering on the GPU, through the C-ABI.
 
 * every request of a batch (uneven resolutions incl. 1x1 and ragged tiles,
+  also for a scene whose single renders trace both eyes of a pixel in one warp,
   depths 0-6, several scenes, one scene under two cameras) equals the
   single-pair rt_render_stereo of the same arguments bit for bit, for every
   tile shape, request order, mirror-queue capacity and residency;
@@ -39,7 +40,7 @@ def _scenes():
 # (scene index, W, H, max_depth, eye_sep, camera shift along x)
 _REQS = [(0, 320, 240, 3, 0.065, 0.0), (1, 203, 77, 2, 0.2, 0.0), (2, 160, 90, 6, 0.065, 0.0),
          (0, 1, 1, 3, 0.065, 0.0), (2, 33, 9, 0, 0.5, 0.0), (0, 97, 61, 5, 0.065, 1.5),
-         (1, 64, 64, 4, 0.0, 0.0)]
+         (1, 64, 64, 4, 0.0, 0.0), (2, 1, 1, 4, 0.065, 0.0), (2, 3, 2, 5, 0.3, 0.0)]
 
 
 class _Fixture:
