@@ -334,9 +334,9 @@ int rt_profile_read(const rt_scene* scene, float* ms);
  *   The call synchronises cuda_stream and returns RT_ERR_DEVICE_CHECK if the
  *   device-side refit check trips. Every call uses the same scratch array:
  *   calls whose GPU work overlaps (other streams or host threads) race and
- *   must be serialised by the caller. The first call on a device looks up
- *   the array's device address; make that first call before any stream
- *   capture begins.
+ *   must be serialised by the caller. Each call looks up the array's device
+ *   address in the current context (cudaGetSymbolAddress), so the address
+ *   stays right after a device reset or a context switch.
  */
 int rt_build_lbvh_noalloc(const rt_sphere* d_spheres, uint32_t n_spheres,
                           const rt_triangle* d_tris, uint32_t n_tris,
@@ -405,6 +405,45 @@ int rt_net_set_fp8(rt_net* net, const float* act_scales);
  */
 int rt_net_activation_amax(rt_net* net, const uint16_t* d_feat16, uint32_t W, uint32_t H,
                            float* host_amax, void* cuda_stream);
+
+/*
+ * rt_net_calibrate_fp8 -- choose the FP8 activation scales from data and
+ * switch the network to FP8 inference. The paper has no network; the scales
+ * follow the scaling described at rt_net_set_fp8: the BF16 network runs on
+ * every feature map, amax[i] is the largest value hidden activation i takes
+ * over all of them, and act_scales[i] is the largest power of two s with
+ * amax[i] * s <= 448 (the largest E4M3 value; 1 when amax[i] is 0), clamped
+ * to [2^-30, 2^30]. Then it does what rt_net_set_fp8(net, act_scales) does.
+ *   d_feats: HOST array of n_maps >= 1 DEVICE feature maps, each W*H*16 BF16
+ *     (as for rt_net_forward, 16-byte aligned).
+ *   host_amax, host_scales: HOST float[3] each, may be NULL; receive the
+ *     maxima and the chosen scales.
+ * Synchronises cuda_stream. Errors: RT_ERR_INVALID_ARG, RT_ERR_OOM,
+ * RT_ERR_CUDA.
+ */
+int rt_net_calibrate_fp8(rt_net* net, const uint16_t* const* d_feats, uint32_t n_maps, uint32_t W,
+                         uint32_t H, float* host_amax, float* host_scales, void* cuda_stream);
+
+/*
+ * rt_net_save / rt_net_load -- a training checkpoint in a file: the FP32
+ * parameters, both Adam moment vectors and the Adam step count, and the FP8
+ * inference state (on/off and the activation scales), so that training
+ * continued from a loaded checkpoint performs exactly the updates the saved
+ * network would have (training steps are deterministic). The paper has no
+ * network; this serves the training loop above.
+ * File layout (little-endian, no padding): char magic[8] = "RTNETCK1";
+ * uint32 version (1), n_params (RT_NET_PARAMS), adam_step, fp8 (0 or 1);
+ * float act_scales[3]; float params[n_params], adam_m[n_params],
+ * adam_v[n_params]; uint32 CRC-32 (zlib convention) of all bytes before it.
+ *   rt_net_save: path is a HOST file name, created or overwritten. The net
+ *     is synchronised with the device first.
+ *   rt_net_load: verifies magic, version, size and CRC, then creates a new
+ *     network (released with rt_net_destroy) in *out. Synchronises.
+ * Errors: RT_ERR_INVALID_ARG (file missing, unreadable, unwritable,
+ * truncated or corrupt), RT_ERR_OOM, RT_ERR_CUDA.
+ */
+int rt_net_save(const rt_net* net, const char* path);
+int rt_net_load(const char* path, rt_net** out);
 
 /*
  * rt_net_forward -- retrace probability of every pixel of a W x H feature map.

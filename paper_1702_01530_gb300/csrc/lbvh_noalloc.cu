@@ -20,7 +20,6 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include <mutex>
 #include <string>
 
 #include "rt_internal.cuh"
@@ -33,31 +32,22 @@ constexpr size_t kErrOffset = kNoAllocScratchBytes - 256;  // error word at the 
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-void* g_scratch_ptr[kMaxDevices] = {};
-
 int fail(int code, const std::string& msg) {
   rt_set_error(msg);
   return code;
 }
 
-// Device address of the scratch array on the current device (looked up once
-// per device; the host-side symbol itself is not a device address).
+// Device address of the scratch array in the current context. The host-side
+// symbol is not a device address, and the device address belongs to the
+// context that loaded the module (a device reset or another context on the
+// same device loads it again, possibly elsewhere), so it is looked up on
+// every call; the lookup is cheap next to a build that synchronises.
 int scratch_address(void** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return fail(RT_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
-  if (dev < 0 || dev >= kMaxDevices) return fail(RT_ERR_INVALID_ARG, "device index out of range");
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_scratch_ptr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p)
-      return fail(RT_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-    g_scratch_ptr[dev] = p;
-  }
-  *out = g_scratch_ptr[dev];
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || !p)
+    return fail(RT_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+  *out = p;
   return RT_OK;
 }
 

@@ -417,3 +417,26 @@ def test_bvh_cycle_stops_at_iteration_bound():
         g.close()
     gpu = gpu_render(sg.config_small(1, W=32, H=24))  # the context is still usable
     assert gpu["rgb"].shape == (2, 24, 32, 3)
+
+
+@pytest.mark.parametrize("n_prims", [1023, 1024])
+def test_pair_eyes_cutoff_both_sides(n_prims):
+    """Scenes of 1024 or more primitives trace a pixel's two eyes in
+    neighbouring lanes (4x4-pixel tiles), smaller ones 8x4 tiles of one eye:
+    parity on both sides of the cut-off at an odd size, and a zero
+    separation gives identical eyes bit for bit on both sides."""
+    rng = np.random.default_rng(77)
+    sph = []
+    for k in range(n_prims):
+        c = (float(rng.uniform(-30, 30)), float(rng.uniform(-7, 7)), float(rng.uniform(-20, -8)))
+        sph.append((c, float(rng.uniform(0.3, 1.0)), k % 3))
+    mats = [(0.8, 0.3, 0.2, 0.0), (0.2, 0.7, 0.3, 0.0), (0.6, 0.6, 0.6, 0.5)]
+    s = scene(spheres=sph, mats=mats, lights=[((3.0, 10.0, 0.0), 1.0)], W=33, H=9,
+              eye_sep=0.065, convergence=15.0, max_depth=3)
+    assert s.n_prims == n_prims
+    ref = oracle.render(s)
+    assert (ref["hit_id"] != capi.RT_MISS_ID).mean() > 0.5
+    check_parity(gpu_render(s), ref, 1, 3)
+    z = gpu_render(s.with_view(eye_sep=0.0))
+    assert np.array_equal(z["rgb"][0], z["rgb"][1])
+    assert np.array_equal(z["hit_id"][0], z["hit_id"][1])

@@ -105,3 +105,47 @@ def test_noalloc_build_rejects_sizes_beyond_its_limit():
     with pytest.raises(capi.RtError) as e:
         capi.rt_build_lbvh_noalloc(16, (1 << 20) + 1, None, 0, 16, 16, 16, 16)
     assert e.value.code == capi.RT_ERR_INVALID_ARG and "limit" in str(e.value)
+
+
+def _bvh_arrays(nodes, n):
+    """keys-free BVH arrays (left, right, leaf and inner boxes) from raw
+    64-byte nodes, vectorised for large trees."""
+    f = nodes.reshape(max(n - 1, 1), 16)[:n - 1]
+    ints = f.view(np.int32)
+    left, right = ints[:, 12].copy(), ints[:, 13].copy()
+    box0 = f[:, [0, 2, 8, 1, 3, 9]]
+    box1 = f[:, [4, 6, 10, 5, 7, 11]]
+    leaf_box = np.zeros((n, 6), np.float32)
+    inner_box = np.zeros((n - 1, 6), np.float32)
+    for c, b in ((left, box0), (right, box1)):
+        lf = c < 0
+        leaf_box[~c[lf]] = b[lf]
+        inner_box[c[~lf]] = b[~lf]
+    inner_box[0] = np.concatenate([np.minimum(box0[0, :3], box1[0, :3]),
+                                   np.maximum(box0[0, 3:], box1[0, 3:])])
+    return dict(left=left, right=right, leaf_box=leaf_box, inner_box=inner_box)
+
+
+def test_noalloc_build_near_its_limit():
+    """A terrain grid of 725 x 725 heights: 1,048,352 triangles, 224 short of
+    the 2^20-primitive limit, so the scratch array holds the largest build it
+    admits; the tree equals rt_scene_create's bit for bit."""
+    import torch
+    s = sg.config_terrain(5, n_grid=725, n_spheres=0, n_lights=1, W=64, H=36)
+    n = s.n_prims
+    assert (1 << 20) - 256 < n <= (1 << 20)
+    tr = torch.from_numpy(np.ascontiguousarray(s.triangles).view(np.uint8).copy()).cuda()
+    nodes = torch.full(((n - 1) * 16,), -7.0, dtype=torch.float32, device="cuda")
+    prims = torch.full((n * 12,), -7.0, dtype=torch.float32, device="cuda")
+    keys = torch.zeros(n, dtype=torch.int64, device="cuda")
+    parent = torch.zeros(2 * n - 1, dtype=torch.int32, device="cuda")
+    capi.rt_build_lbvh_noalloc(None, 0, tr, n, nodes, prims, keys, parent)
+    got = _bvh_arrays(nodes.cpu().numpy(), n)
+    got.update(keys=keys.cpu().numpy().view(np.uint64), parent=parent.cpu().numpy())
+    g = capi.GpuScene(s)
+    try:
+        ref = capi.rt_scene_get_bvh(g.handle)
+    finally:
+        g.close()
+    for k in ("keys", "left", "right", "parent", "leaf_box", "inner_box"):
+        assert np.array_equal(got[k], ref[k]), k
