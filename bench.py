@@ -222,7 +222,7 @@ def reproj_leg(blob_scene):
     params, thr = tr.load_weights()
     net = capi.Net(params)
     try:
-        scales = tr.fp8_calibration_scales(net.handle)
+        scales = tr.fp8_calibrate(net.handle)
         out = {"weights": "paper_1702_01530_gb300/weights/reproj_net.bin", "threshold": thr,
                "fp8_act_scales": [float(x) for x in scales]}
 
@@ -416,8 +416,7 @@ def sequence_leg(stream, n_frames=120, per_launch=8):
         ok = [t for t in thresholds if summary(t)["right_psnr_db_min"] >= 40.0]
         best = max(ok) if ok else min(thresholds)
         # the same network with FP8 inference at that threshold
-        scales = tr.fp8_calibration_scales(net.handle)
-        capi.rt_net_set_fp8(net.handle, scales)
+        scales = tr.fp8_calibrate(net.handle)
         for f in range(0, n_frames, 10):
             cam = cams[f]
             capi.rt_render_stereo(g.handle, cam, s.eye_sep, s.convergence, W, H, D, img[0], img[1],

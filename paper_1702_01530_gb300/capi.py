@@ -70,6 +70,9 @@ _SIGS = {
     "rt_net_forward": (ctypes.c_int, [_vp, _vp, _u32, _u32, _vp, _vp]),
     "rt_net_set_fp8": (ctypes.c_int, [_vp, _vp]),
     "rt_net_activation_amax": (ctypes.c_int, [_vp, _vp, _u32, _u32, _vp, _vp]),
+    "rt_net_calibrate_fp8": (ctypes.c_int, [_vp, _vp, _u32, _u32, _u32, _vp, _vp, _vp]),
+    "rt_net_save": (ctypes.c_int, [_vp, ctypes.c_char_p]),
+    "rt_net_load": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(_vp)]),
     "rt_net_train_step": (ctypes.c_int, [_vp, _vp, _vp, _u32, _u32, _f32, _vp, _vp, _vp]),
     "rt_reproj_warp": (ctypes.c_int, [_vp, _vp, _vp, _vp, _u32, _u32, _f32, _f32, _f32, _vp, _vp,
                                       _vp, _vp, _vp, _vp]),
@@ -446,15 +449,26 @@ def rt_net_activation_amax(net, feat16, W, H, stream=None) -> np.ndarray:
     return out
 
 
-def fp8_scales(amax) -> np.ndarray:
-    """The largest power of two s with amax * s <= 448, per activation."""
-    amax = np.asarray(amax, np.float64)
-    out = np.ones(len(amax))
-    for i, a in enumerate(amax):
-        if a > 0:
-            _, k = np.frexp(448.0 / a)
-            out[i] = 2.0 ** (k - 1)
-    return out.astype(np.float32)
+def rt_net_calibrate_fp8(net, feats, W, H, stream=None):
+    """Run the BF16 network on every feature map in ``feats``, choose the FP8
+    activation scales in the library and switch the network to FP8.
+    Returns (amax, scales), three floats each."""
+    ptrs = (ctypes.c_void_p * max(1, len(feats)))(*[_dptr(f) for f in feats])
+    amax = np.zeros(3, np.float32)
+    scales = np.zeros(3, np.float32)
+    _check(lib().rt_net_calibrate_fp8(net, ctypes.cast(ptrs, ctypes.c_void_p), len(feats), W, H,
+                                      amax.ctypes.data, scales.ctypes.data, _stream(stream)))
+    return amax, scales
+
+
+def rt_net_save(net, path):
+    _check(lib().rt_net_save(net, os.fsencode(path)))
+
+
+def rt_net_load(path) -> int:
+    h = _vp()
+    _check(lib().rt_net_load(os.fsencode(path), ctypes.byref(h)))
+    return h.value
 
 
 def rt_net_train_step(net, feat16, label, W, H, lr, want_loss=True, grads=None, stream=None):

@@ -579,9 +579,13 @@ __global__ void k_bce(const float* __restrict__ prob, const float* __restrict__ 
 }
 
 // ------------------------------------------------------ weight gradients
-// dW[co][ci][ky][kx] += scale * sum_x dZ[y][x][co] * A[y+ky-1][x+kx-1][ci],
-// db[co] += scale * sum_x dZ[y][x][co]; one CTA per image row, a 128-pixel
-// chunk at a time through shared memory, FP32 accumulation, atomics at the end.
+// dW[co][ci][ky][kx] = scale * sum_x dZ[y][x][co] * A[y+ky-1][x+kx-1][ci],
+// db[co] = scale * sum_x dZ[y][x][co]; each CTA takes every gridDim.x-th image
+// row, a 64-pixel chunk at a time through shared memory, FP32 accumulation,
+// and writes its unscaled partial sums (canonical layout: the layer's weights
+// then its biases) to its own row of `part`; k_wgrad_reduce then adds the
+// rows in a fixed order, so the gradient -- and training -- is the same bit
+// for bit from run to run (atomics would add the CTAs in arrival order).
 // A is interleaved [P][16] when CIN_PAD = 16 (the input features) and planar
 // [4][P][8] when CIN_PAD = 32 (activations); dZ comes as FP32 (layer 4, one
 // channel) or as a planar 32-channel BF16 map.
@@ -589,8 +593,7 @@ template <int CIN_PAD, int COUT>
 __global__ void __launch_bounds__(256) k_wgrad(const __nv_bfloat16* __restrict__ A, int cin,
                                                const __nv_bfloat16* __restrict__ dz16,
                                                const float* __restrict__ dz32, uint32_t W,
-                                               uint32_t H, float scale, float* __restrict__ dW,
-                                               float* __restrict__ db) {
+                                               uint32_t H, float* __restrict__ part) {
   const size_t P = (size_t)W * H;
   constexpr int kChunk = 64;
   constexpr int kOut = COUT * CIN_PAD * 9;
@@ -644,16 +647,39 @@ __global__ void __launch_bounds__(256) k_wgrad(const __nv_bfloat16* __restrict__
         for (int xx = 0; xx < nx; ++xx) bacc += sZ[xx][tid];
     }
   }
+  const size_t n_w = (size_t)COUT * cin * 9;
+  float* row = part + (size_t)blockIdx.x * (n_w + COUT);
 #pragma unroll
   for (int i = 0; i < kPer; ++i) {
     const int o = tid + i * 256;
     if (o < kOut) {
       const int tap = o % 9, rest = o / 9;
       const int ci = rest % CIN_PAD, co = rest / CIN_PAD;
-      if (ci < cin) atomicAdd(&dW[((size_t)co * cin + ci) * 9 + tap], acc[i] * scale);
+      if (ci < cin) row[((size_t)co * cin + ci) * 9 + tap] = acc[i];
     }
   }
-  if (tid < COUT) atomicAdd(&db[tid], bacc * scale);
+  if (tid < COUT) row[n_w + tid] = bacc;
+}
+
+// out[j] = scale * sum over b = 0 .. nblk-1 of part[b][j], in a fixed order:
+// warp w of a block adds rows w, w + 8, w + 16, ... of 32 consecutive
+// columns, then thread 0..31 adds the 8 warp sums in warp order.
+__global__ void __launch_bounds__(256) k_wgrad_reduce(const float* __restrict__ part, uint32_t nblk,
+                                                      uint32_t n, float scale, float* __restrict__ out) {
+  __shared__ float s[8][32];
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t j = blockIdx.x * 32 + lane;
+  float a = 0.f;
+  if (j < n)
+    for (uint32_t b = warp; b < nblk; b += 8) a += part[(size_t)b * n + j];
+  s[warp][lane] = a;
+  __syncthreads();
+  if (warp == 0 && j < n) {
+    float t = 0.f;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) t += s[w][lane];
+    out[j] = t * scale;
+  }
 }
 
 // ---------------------------------------------------------------- Adam
@@ -856,9 +882,10 @@ cudaError_t forward_fp8(const __nv_bfloat16* feat16, const float* params, __nv_b
                                                     nullptr, prob, W, H, err, st);
 }
 
+// raises amax3[l] to the largest value of hidden activation l (the caller
+// clears amax3 before the first map it measures)
 cudaError_t activation_amax(const __nv_bfloat16* const act[3], uint64_t P, unsigned* amax3,
                             cudaStream_t st) {
-  cudaMemsetAsync(amax3, 0, 3 * sizeof(unsigned), st);
   for (int l = 0; l < 3; ++l) k_amax<<<num_sms() * 4, 256, 0, st>>>(act[l], P * 32, amax3 + l);
   return cudaGetLastError();
 }
@@ -868,37 +895,45 @@ cudaError_t activation_amax(const __nv_bfloat16* const act[3], uint64_t P, unsig
 cudaError_t backward(const __nv_bfloat16* feat16, const float* label, __nv_bfloat16* const wb[4],
                      const __nv_bfloat16* act1, const __nv_bfloat16* act2,
                      const __nv_bfloat16* act3, const float* prob, __nv_bfloat16* g16, float* g32,
-                     __nv_bfloat16* dz_a, __nv_bfloat16* dz_b, float* grads, float* loss_sum,
-                     uint32_t W, uint32_t H, uint32_t* err, cudaStream_t st) {
+                     __nv_bfloat16* dz_a, __nv_bfloat16* dz_b, float* wpart, float* grads,
+                     float* loss_sum, uint32_t W, uint32_t H, uint32_t* err, cudaStream_t st) {
   const uint32_t P = W * H;
   const float scale = 1.f / (float)P;
-  const int rows_grid = (int)(H < (uint32_t)(num_sms() * 4) ? H : (uint32_t)(num_sms() * 4));
-  cudaMemsetAsync(grads, 0, (size_t)(kOffB[3] + 1) * sizeof(float), st);
+  const int rows_grid = wgrad_blocks(H);
+  // weight gradient of layer l from its per-CTA partial sums (fixed order)
+  auto reduce = [&](int l) {
+    const uint32_t n = (uint32_t)kCout[l] * (uint32_t)kCin[l] * 9u + (uint32_t)kCout[l];
+    k_wgrad_reduce<<<(n + 31) / 32, 256, 0, st>>>(wpart, (uint32_t)rows_grid, n, scale, grads + kOffW[l]);
+  };
   cudaMemsetAsync(loss_sum, 0, sizeof(float), st);
   k_bce<<<num_sms() * 8, 256, 0, st>>>(prob, label, P, g16, g32, loss_sum);
   // layer 4: dW from g32 (one channel), data gradient into dz_a (masked by act3 > 0)
-  k_wgrad<32, 1><<<rows_grid, 256, 0, st>>>(act3, 32, nullptr, g32, W, H, scale,
-                                             grads + kOffW[3], grads + kOffB[3]);
+  k_wgrad<32, 1><<<rows_grid, 256, 0, st>>>(act3, 32, nullptr, g32, W, H, wpart);
+  reduce(3);
   cudaError_t e = launch_conv<16, 32, EPI_BWD_MASK_BF16>(g16, wb[3], nullptr, nullptr, 1.f, act3, dz_a,
                                                          nullptr, W, H, err, st);
   if (e != cudaSuccess) return e;
   // layer 3
-  k_wgrad<32, 32><<<rows_grid, 256, 0, st>>>(act2, 32, dz_a, nullptr, W, H, scale,
-                                              grads + kOffW[2], grads + kOffB[2]);
+  k_wgrad<32, 32><<<rows_grid, 256, 0, st>>>(act2, 32, dz_a, nullptr, W, H, wpart);
+  reduce(2);
   e = launch_conv<32, 32, EPI_BWD_MASK_BF16>(dz_a, wb[2], nullptr, nullptr, 1.f, act2, dz_b, nullptr,
                                              W, H, err, st);
   if (e != cudaSuccess) return e;
   // layer 2
-  k_wgrad<32, 32><<<rows_grid, 256, 0, st>>>(act1, 32, dz_b, nullptr, W, H, scale,
-                                              grads + kOffW[1], grads + kOffB[1]);
+  k_wgrad<32, 32><<<rows_grid, 256, 0, st>>>(act1, 32, dz_b, nullptr, W, H, wpart);
+  reduce(1);
   e = launch_conv<32, 32, EPI_BWD_MASK_BF16>(dz_b, wb[1], nullptr, nullptr, 1.f, act1, dz_a, nullptr,
                                              W, H, err, st);
   if (e != cudaSuccess) return e;
   // layer 1 (no data gradient for the input features)
-  k_wgrad<16, 32><<<rows_grid, 256, 0, st>>>(feat16, 9, dz_a, nullptr, W, H, scale,
-                                              grads + kOffW[0], grads + kOffB[0]);
+  k_wgrad<16, 32><<<rows_grid, 256, 0, st>>>(feat16, 9, dz_a, nullptr, W, H, wpart);
+  reduce(0);
   return cudaGetLastError();
 }
+
+int wgrad_blocks(uint32_t H) { return (int)(H < (uint32_t)(num_sms() * 4) ? H : (uint32_t)(num_sms() * 4)); }
+
+size_t wgrad_part_floats(uint32_t H) { return (size_t)wgrad_blocks(H) * (32u * 32u * 9u + 32u); }
 
 cudaError_t adam(float* params, const float* grads, float* m, float* v, uint32_t n, float lr,
                  uint32_t step, cudaStream_t st) {

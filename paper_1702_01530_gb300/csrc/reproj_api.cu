@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <cmath>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -37,6 +38,7 @@ struct rt_net {
   __nv_bfloat16* g16 = nullptr;
   float* g32 = nullptr;
   __nv_bfloat16* dz[2] = {};
+  float* wpart = nullptr;       // per-CTA partial sums of the weight gradients
   // FP8 inference (rt_net_set_fp8): E4M3 weights of layers 2-4, their
   // per-output-channel scales and the inverse scales the epilogues apply
   bool fp8 = false;
@@ -65,9 +67,9 @@ cudaError_t net_forward(rt_net* net, const __nv_bfloat16* feat16, __nv_bfloat16*
 int net_buffers(rt_net* net, uint64_t P) {
   if (net->tb && net->tcap >= P) return RT_OK;
   const size_t b_act = a256(P * 32 * 2), b_prob = a256(P * 4), b_g16 = a256(P * 16 * 2),
-               b_g32 = a256(P * 4);
+               b_g32 = a256(P * 4), b_part = a256(rt::nn::wgrad_part_floats(0xFFFFFFFFu) * 4);
   void* base = nullptr;
-  cudaError_t e = cudaMalloc(&base, 3 * b_act + b_prob + b_g16 + b_g32 + 2 * b_act);
+  cudaError_t e = cudaMalloc(&base, 3 * b_act + b_prob + b_g16 + b_g32 + 2 * b_act + b_part);
   if (e != cudaSuccess) { cudaGetLastError(); return cuda_fail(e, "network activations"); }
   if (net->tb) cudaFree(net->tb);
   net->tb = base;
@@ -78,6 +80,7 @@ int net_buffers(rt_net* net, uint64_t P) {
   net->g16 = reinterpret_cast<__nv_bfloat16*>(p); p += b_g16;
   net->g32 = reinterpret_cast<float*>(p); p += b_g32;
   for (int i = 0; i < 2; ++i) { net->dz[i] = reinterpret_cast<__nv_bfloat16*>(p); p += b_act; }
+  net->wpart = reinterpret_cast<float*>(p);
   return RT_OK;
 }
 
@@ -108,6 +111,37 @@ int reproj_buffers(const rt_scene* sc_c, uint64_t P) {
   rp.prob = reinterpret_cast<float*>(p); p += b4;
   for (int i = 0; i < 3; ++i) { rp.act[i] = reinterpret_cast<__nv_bfloat16*>(p); p += bact; }
   return RT_OK;
+}
+
+// CRC-32 of the IEEE 802.3 / zlib convention (reflected polynomial
+// 0xEDB88320, initial value and final xor 0xFFFFFFFF), bit by bit
+uint32_t crc32(const unsigned char* p, size_t n) {
+  uint32_t c = 0xFFFFFFFFu;
+  for (size_t i = 0; i < n; ++i) {
+    c ^= p[i];
+    for (int k = 0; k < 8; ++k) c = (c >> 1) ^ (0xEDB88320u & (0u - (c & 1u)));
+  }
+  return c ^ 0xFFFFFFFFu;
+}
+
+// Training checkpoint: everything needed to continue training exactly where
+// it stopped. Little-endian, no padding:
+//   char magic[8] = "RTNETCK1"; uint32 version (1), n_params, adam_step,
+//   fp8 (0/1); float act_scale[3]; float params[n], adam_m[n], adam_v[n];
+//   uint32 CRC-32 of every byte before it.
+constexpr char kCkptMagic[8] = {'R', 'T', 'N', 'E', 'T', 'C', 'K', '1'};
+constexpr uint32_t kCkptVersion = 1;
+constexpr size_t kCkptHeader = 8 + 4 * 4 + 3 * 4;
+
+// largest power of two s with amax * s <= 448 (the E4M3 maximum), 1 for
+// amax = 0, kept within the [2^-30, 2^30] that rt_net_set_fp8 accepts
+float fp8_pow2_scale(float amax) {
+  if (!(amax > 0.f)) return 1.f;
+  int k = 0;
+  std::frexp(448.0 / (double)amax, &k);        // 448 / amax = m 2^k, m in [0.5, 1)
+  double s = std::ldexp(1.0, k - 1);
+  while ((double)amax * s > 448.0) s *= 0.5;   // a rounded quotient could reach 2^k
+  return (float)std::min(std::max(s, std::ldexp(1.0, -30)), std::ldexp(1.0, 30));
 }
 
 float focal_px(const rt_camera* cam, uint32_t H) {
@@ -242,14 +276,112 @@ int rt_net_activation_amax(rt_net* net, const uint16_t* d_feat16, uint32_t W, ui
   int rc = net_buffers(net, (uint64_t)W * H);
   if (rc) return rc;
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
-  cudaError_t e = rt::nn::forward(reinterpret_cast<const __nv_bfloat16*>(d_feat16), net->params, net->wf,
-                                  net->act[0], net->act[1], net->act[2], net->prob, W, H, net->err, st);
+  cudaError_t e = cudaMemsetAsync(net->amax, 0, 3 * sizeof(unsigned), st);
+  if (e == cudaSuccess)
+    e = rt::nn::forward(reinterpret_cast<const __nv_bfloat16*>(d_feat16), net->params, net->wf,
+                        net->act[0], net->act[1], net->act[2], net->prob, W, H, net->err, st);
   if (e == cudaSuccess) e = rt::nn::activation_amax(net->act, (uint64_t)W * H, net->amax, st);
   unsigned bits[3] = {0, 0, 0};
   if (e == cudaSuccess) e = cudaMemcpyAsync(bits, net->amax, sizeof bits, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(e, "rt_net_activation_amax");
   for (int i = 0; i < 3; ++i) std::memcpy(&host_amax[i], &bits[i], 4);
+  return RT_OK;
+}
+
+int rt_net_calibrate_fp8(rt_net* net, const uint16_t* const* d_feats, uint32_t n_maps, uint32_t W,
+                         uint32_t H, float* host_amax, float* host_scales, void* cuda_stream) {
+  if (!net || !d_feats || n_maps < 1 || W < 1 || H < 1) return fail(RT_ERR_INVALID_ARG, "bad argument");
+  if ((uint64_t)W * H > (1ull << 30)) return fail(RT_ERR_INVALID_ARG, "image too large");
+  for (uint32_t i = 0; i < n_maps; ++i)
+    if (!d_feats[i]) return fail(RT_ERR_INVALID_ARG, "feature map " + std::to_string(i) + " is NULL");
+  int rc = net_buffers(net, (uint64_t)W * H);
+  if (rc) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  // maxima of the BF16 network's three hidden activations over every map
+  cudaError_t e = cudaMemsetAsync(net->amax, 0, 3 * sizeof(unsigned), st);
+  for (uint32_t i = 0; i < n_maps && e == cudaSuccess; ++i) {
+    e = rt::nn::forward(reinterpret_cast<const __nv_bfloat16*>(d_feats[i]), net->params, net->wf,
+                        net->act[0], net->act[1], net->act[2], net->prob, W, H, net->err, st);
+    if (e == cudaSuccess) e = rt::nn::activation_amax(net->act, (uint64_t)W * H, net->amax, st);
+  }
+  unsigned bits[3] = {0, 0, 0};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(bits, net->amax, sizeof bits, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "rt_net_calibrate_fp8");
+  float amax[3], scales[3];
+  for (int i = 0; i < 3; ++i) {
+    std::memcpy(&amax[i], &bits[i], 4);
+    scales[i] = fp8_pow2_scale(amax[i]);
+  }
+  rc = rt_net_set_fp8(net, scales);
+  if (rc) return rc;
+  for (int i = 0; i < 3; ++i) {
+    if (host_amax) host_amax[i] = amax[i];
+    if (host_scales) host_scales[i] = scales[i];
+  }
+  return RT_OK;
+}
+
+int rt_net_save(const rt_net* net, const char* path) {
+  if (!net || !path) return fail(RT_ERR_INVALID_ARG, "net or path is NULL");
+  const size_t n = rt::nn::kParams;
+  std::vector<unsigned char> buf(kCkptHeader + 3 * n * 4 + 4);
+  unsigned char* p = buf.data();
+  std::memcpy(p, kCkptMagic, 8);
+  const uint32_t head[4] = {kCkptVersion, (uint32_t)n, net->step, net->fp8 ? 1u : 0u};
+  std::memcpy(p + 8, head, sizeof head);
+  std::memcpy(p + 24, net->act_scale, 3 * 4);
+  cudaError_t e = cudaDeviceSynchronize();
+  float* const src[3] = {net->params, net->m, net->v};
+  for (int k = 0; k < 3 && e == cudaSuccess; ++k)
+    e = cudaMemcpy(p + kCkptHeader + (size_t)k * n * 4, src[k], n * 4, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "rt_net_save: download");
+  const uint32_t crc = crc32(p, buf.size() - 4);
+  std::memcpy(p + buf.size() - 4, &crc, 4);
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return fail(RT_ERR_INVALID_ARG, std::string("rt_net_save: cannot open ") + path);
+  const bool ok = std::fwrite(p, 1, buf.size(), f) == buf.size();
+  if (std::fclose(f) != 0 || !ok) return fail(RT_ERR_INVALID_ARG, std::string("rt_net_save: write failed: ") + path);
+  return RT_OK;
+}
+
+int rt_net_load(const char* path, rt_net** out) {
+  if (!path || !out) return fail(RT_ERR_INVALID_ARG, "path or out is NULL");
+  *out = nullptr;
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return fail(RT_ERR_INVALID_ARG, std::string("rt_net_load: cannot open ") + path);
+  const size_t n = rt::nn::kParams, want = kCkptHeader + 3 * n * 4 + 4;
+  std::vector<unsigned char> buf(want + 1);
+  const size_t got = std::fread(buf.data(), 1, buf.size(), f);
+  std::fclose(f);
+  const unsigned char* p = buf.data();
+  if (got != want || std::memcmp(p, kCkptMagic, 8) != 0)
+    return fail(RT_ERR_INVALID_ARG, std::string("rt_net_load: not a network checkpoint (or wrong size): ") + path);
+  uint32_t head[4], crc = 0;
+  std::memcpy(head, p + 8, sizeof head);
+  std::memcpy(&crc, p + want - 4, 4);
+  if (head[0] != kCkptVersion || head[1] != n || head[3] > 1)
+    return fail(RT_ERR_INVALID_ARG, "rt_net_load: unsupported checkpoint version or parameter count");
+  if (crc32(p, want - 4) != crc) return fail(RT_ERR_INVALID_ARG, "rt_net_load: CRC mismatch");
+  std::vector<float> params(n), m(n), v(n);
+  std::memcpy(params.data(), p + kCkptHeader, n * 4);
+  std::memcpy(m.data(), p + kCkptHeader + n * 4, n * 4);
+  std::memcpy(v.data(), p + kCkptHeader + 2 * n * 4, n * 4);
+  float act[3];
+  std::memcpy(act, p + 24, sizeof act);
+  rt_net* net = nullptr;
+  int rc = rt_net_create(params.data(), (uint32_t)n, &net);
+  if (rc) return rc;
+  cudaError_t e = cudaMemcpy(net->m, m.data(), n * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(net->v, v.data(), n * 4, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) { rt_net_destroy(net); return cuda_fail(e, "rt_net_load: upload"); }
+  net->step = head[2];
+  if (head[3]) {
+    rc = rt_net_set_fp8(net, act);
+    if (rc) { rt_net_destroy(net); return rc; }
+  }
+  *out = net;
   return RT_OK;
 }
 
@@ -279,8 +411,8 @@ int rt_net_train_step(rt_net* net, const uint16_t* d_feat16, const float* d_labe
                                   net->prob, W, H, net->err, st);
   if (e == cudaSuccess)
     e = rt::nn::backward(f16, d_label, net->wb, net->act[0], net->act[1], net->act[2], net->prob,
-                         net->g16, net->g32, net->dz[0], net->dz[1], net->grads, net->loss, W, H,
-                         net->err, st);
+                         net->g16, net->g32, net->dz[0], net->dz[1], net->wpart, net->grads,
+                         net->loss, W, H, net->err, st);
   if (e == cudaSuccess && d_grads)
     e = cudaMemcpyAsync(d_grads, net->grads, (size_t)rt::nn::kParams * 4, cudaMemcpyDeviceToDevice, st);
   if (e == cudaSuccess && lr > 0.f) {

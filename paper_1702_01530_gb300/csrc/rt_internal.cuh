@@ -212,8 +212,12 @@ cudaError_t forward(const __nv_bfloat16* feat16, const float* params, __nv_bfloa
 cudaError_t backward(const __nv_bfloat16* feat16, const float* label, __nv_bfloat16* const wb[4],
                      const __nv_bfloat16* act1, const __nv_bfloat16* act2,
                      const __nv_bfloat16* act3, const float* prob, __nv_bfloat16* g16, float* g32,
-                     __nv_bfloat16* dz_a, __nv_bfloat16* dz_b, float* grads, float* loss_sum,
-                     uint32_t W, uint32_t H, uint32_t* err, cudaStream_t st);
+                     __nv_bfloat16* dz_a, __nv_bfloat16* dz_b, float* wpart, float* grads,
+                     float* loss_sum, uint32_t W, uint32_t H, uint32_t* err, cudaStream_t st);
+// CTAs of the weight-gradient kernels for an image of H rows, and the floats
+// of their partial-sum buffer (one row of a layer's gradients per CTA)
+int wgrad_blocks(uint32_t H);
+size_t wgrad_part_floats(uint32_t H);
 cudaError_t adam(float* params, const float* grads, float* m, float* v, uint32_t n, float lr,
                  uint32_t step, cudaStream_t st);
 size_t packed_fp8_bytes(int l);

@@ -96,26 +96,27 @@ def train(data, W, H, epochs=8, lr=1e-3, seed=0, log=print):
     return net, history
 
 
-def fp8_calibration_scales(net_handle, seeds=(2000, 2001, 2002), W=1920, H=1080):
-    """FP8 activation scales of a network: the largest power of two s with
-    amax * s <= 448 for each hidden activation, amax over the BF16 network's
-    activations on the reprojection features of held-out small scenes."""
+def fp8_calibrate(net_handle, seeds=(2000, 2001, 2002), W=1920, H=1080):
+    """Switch a network to FP8 inference with activation scales chosen by the
+    library (rt_net_calibrate_fp8) from the reprojection features of held-out
+    small scenes; returns the scales."""
     import torch
-    amax = np.zeros(3, np.float32)
     P = W * H
     L = torch.empty((H, W, 3), dtype=torch.float32, device="cuda")
     R = torch.empty_like(L)
-    f16 = torch.empty((P, 16), dtype=torch.bfloat16, device="cuda")
     lab = torch.empty(P, dtype=torch.float32, device="cuda")
+    feats = []
     for seed in seeds:
         s = sg.config_small(seed, W=W, H=H)
         g = capi.GpuScene(s)
+        f16 = torch.empty((P, 16), dtype=torch.bfloat16, device="cuda")
         capi.rt_reproj_training_pair(g.handle, s.camera, s.eye_sep, s.convergence, W, H,
                                      s.max_depth, L, R, f16, lab, 1e-2)
         capi.rt_sync_status(g.handle)
         g.close()
-        amax = np.maximum(amax, capi.rt_net_activation_amax(net_handle, f16, W, H))
-    return capi.fp8_scales(amax)
+        feats.append(f16)
+    _, scales = capi.rt_net_calibrate_fp8(net_handle, feats, W, H)
+    return scales
 
 
 def psnr(a, b) -> float:

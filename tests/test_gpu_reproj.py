@@ -265,7 +265,71 @@ def test_activation_amax_matches_bf16_oracle_activations():
         x = orp._bf16(torch.relu(F.conv2d(x, orp._bf16(torch.tensor(w)), torch.tensor(b), padding=1)))
         want.append(float(x.max()))
     assert np.allclose(amax, want, rtol=2e-2), (amax, want)
-    assert (capi.fp8_scales(amax) * amax <= 448).all()
+
+
+def test_fp8_calibration_picks_power_of_two_scales_from_two_maps():
+    """rt_net_calibrate_fp8 takes each hidden activation's maximum over all
+    the maps it is given and the largest power of two keeping it <= 448; the
+    network then runs in FP8 exactly as after rt_net_set_fp8 with them."""
+    import torch
+    W, H = 64, 9
+    params = sg.net_params_he(21)
+    fa = _t(sg.bf16_features_synthetic(22, W, H), torch.bfloat16)
+    fb = _t(sg.bf16_features_synthetic(23, W, H) * 3.0, torch.bfloat16)
+    net = capi.Net(params)
+    try:
+        a1 = capi.rt_net_activation_amax(net.handle, fa, W, H)
+        a2 = capi.rt_net_activation_amax(net.handle, fb, W, H)
+        amax, scales = capi.rt_net_calibrate_fp8(net.handle, [fa, fb], W, H)
+        prob = torch.empty(W * H, dtype=torch.float32, device="cuda")
+        capi.rt_net_forward(net.handle, fa, W, H, prob)
+        got = prob.clone()
+        capi.rt_net_set_fp8(net.handle, scales)
+        capi.rt_net_forward(net.handle, fa, W, H, prob)
+        capi.rt_net_status(net.handle)
+        assert torch.equal(prob, got)
+    finally:
+        net.close()
+    assert np.array_equal(amax, np.maximum(a1, a2))
+    assert np.array_equal(scales, orp.pow2_scale(amax.astype(np.float64)).astype(np.float32))
+    assert (scales * amax <= 448).all() and (2 * scales * amax > 448).all()
+
+
+def test_checkpoint_resumes_training_bit_for_bit(tmp_path):
+    """Training is deterministic (weight gradients reduced in a fixed order),
+    and a checkpoint holds the parameters, both Adam moments and the step:
+    3 steps, save, 3 more steps equals 3 steps, save, load into a new network,
+    3 more steps, bit for bit; the file's CRC catches a flipped byte."""
+    import torch
+    W, H = 300, 40
+    f = _t(sg.bf16_features_synthetic(61, W, H), torch.bfloat16)
+    y = _t((np.random.default_rng(62).random(W * H) < 0.3).astype(np.float32))
+    path = str(tmp_path / "net.ckpt")
+    a = capi.Net(sg.net_params_he(63))
+    try:
+        for _ in range(3):
+            capi.rt_net_train_step(a.handle, f, y, W, H, 1e-2, want_loss=False)
+        capi.rt_net_save(a.handle, path)
+        for _ in range(3):
+            capi.rt_net_train_step(a.handle, f, y, W, H, 1e-2, want_loss=False)
+        want = a.params()
+    finally:
+        a.close()
+    b = capi.rt_net_load(path)
+    try:
+        for _ in range(3):
+            capi.rt_net_train_step(b, f, y, W, H, 1e-2, want_loss=False)
+        capi.rt_net_status(b)
+        got = capi.rt_net_get_params(b)
+    finally:
+        capi.rt_net_destroy(b)
+    assert np.array_equal(got.view(np.uint32), want.view(np.uint32))
+    data = bytearray(open(path, "rb").read())
+    data[100] ^= 0x10
+    bad = str(tmp_path / "bad.ckpt")
+    open(bad, "wb").write(bytes(data))
+    with pytest.raises(capi.RtError):
+        capi.rt_net_load(bad)
 
 
 def test_reprojection_with_fp8_network_runs_and_matches_bf16_closely():
@@ -296,3 +360,131 @@ def test_reprojection_with_fp8_network_runs_and_matches_bf16_closely():
     finally:
         net.close()
         g.close()
+
+
+# ------------------------------------------- persistent multi-tile path
+# The convolution kernel is persistent: a grid of (SMs x CTAs per SM) walks
+# the tiles of 128 pixels x 4 rows, each CTA through a ring of 3 halo
+# buffers and 2 TMEM accumulator sets. These sizes give every CTA of every
+# layer (2 CTAs per SM for the 16-channel layers, 1 for the 32-channel ones)
+# at least 4 tiles, so the ring wraps, both accumulator sets are reused and
+# the barrier parities flip; the widths leave a ragged last column tile.
+MULTI = [(1920, 544), (1000, 620)]
+
+
+def _tiles_per_cta(W, H, ctas_per_sm):
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    tiles = -(-W // 128) * -(-H // 4)
+    return tiles / (sms * ctas_per_sm)
+
+
+@pytest.mark.parametrize("W,H", MULTI)
+def test_network_forward_multi_tile_per_cta(W, H):
+    import torch
+    assert _tiles_per_cta(W, H, 2) >= 4
+    params = sg.net_params_he(41)
+    rng = np.random.default_rng(42)
+    params[2592:2624] = rng.normal(0, 0.1, 32)
+    params[21408] = -0.5
+    feat = sg.bf16_features_synthetic(43, W, H)
+    net = capi.Net(params)
+    try:
+        prob = torch.empty(W * H, dtype=torch.float32, device="cuda")
+        f = _t(feat, torch.bfloat16)
+        capi.rt_net_forward(net.handle, f, W, H, prob)
+        got = prob.cpu().numpy().reshape(H, W)
+        capi.rt_net_set_fp8(net.handle, FP8_SCALES)
+        capi.rt_net_forward(net.handle, f, W, H, prob)
+        got8 = prob.cpu().numpy().reshape(H, W)
+        capi.rt_net_status(net.handle)
+    finally:
+        net.close()
+    ref = orp.forward(params, feat, W, H, bf16=True)
+    err = np.abs(got - ref)
+    assert err.max() <= 5e-3 and err.mean() <= 2e-4, (err.max(), err.mean())
+    ref8 = orp.forward_fp8(params, feat, W, H, FP8_SCALES)
+    err8 = np.abs(got8 - ref8)
+    assert err8.max() <= 3e-2 and err8.mean() <= 1e-3 and (err8 <= 1e-3).mean() >= 0.98, \
+        (err8.max(), err8.mean())
+    # every tile row of the last column and the last tile row are covered
+    assert ref.std() > 1e-3 and np.isfinite(got).all()
+
+
+@pytest.mark.parametrize("W,H", MULTI[:1])
+def test_gradients_multi_tile_per_cta(W, H):
+    import torch
+    assert _tiles_per_cta(W, H, 2) >= 4
+    params = sg.net_params_he(51)
+    params[21408] = 0.2
+    feat = sg.bf16_features_synthetic(52, W, H)
+    label = (np.random.default_rng(53).random(W * H) < 0.3).astype(np.float32)
+    net = capi.Net(params)
+    try:
+        grads = torch.zeros(capi.RT_NET_PARAMS, dtype=torch.float32, device="cuda")
+        capi.rt_net_train_step(net.handle, _t(feat, torch.bfloat16), _t(label), W, H, 0.0,
+                               grads=grads)
+        capi.rt_net_status(net.handle)
+        g = grads.cpu().numpy().astype(np.float64)
+    finally:
+        net.close()
+    emu = orp.grads_emulated(params, feat, label, W, H, bf16=True)
+    k = 0
+    for ci, co in orp.LAYERS:
+        for n in (co * ci * 9, co):
+            a, b = g[k:k + n], emu[k:k + n]
+            rel = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-12)
+            assert rel <= 1e-2, (k, n, rel)
+            k += n
+
+
+# ---------------------------------------------- mixed retrace mask (A9)
+def test_reprojection_mixed_mask_matches_oracle():
+    """Trained weights at threshold 0.1 on a 320x240 small scene: the right
+    pixels retraced are the holes and the pixels whose oracle probability
+    (on the GPU's own features) exceeds the threshold; retraced pixels equal
+    the full trace, the others the oracle's warped left colour. Pixels whose
+    probability lies within 5e-3 of the threshold may go either way."""
+    import torch
+    from paper_1702_01530_gb300 import train_reproj as tr
+    s = sg.config_small(7, W=320, H=240)
+    params, _ = tr.load_weights()
+    thr = 0.1
+    W, H, P = s.W, s.H, s.W * s.H
+    g = capi.GpuScene(s)
+    net = capi.Net(params)
+    try:
+        full = g.render(aux=True)
+        depth_L = full["depth"][0].cpu().numpy()
+        fL, fR = full["rgb"][0], full["rgb"][1]
+        L = torch.empty((H, W, 3), dtype=torch.float32, device="cuda")
+        R = torch.empty_like(L)
+        f16 = torch.empty((P, 16), dtype=torch.bfloat16, device="cuda")
+        lab = torch.empty(P, dtype=torch.float32, device="cuda")
+        capi.rt_reproj_training_pair(g.handle, s.camera, s.eye_sep, s.convergence, W, H,
+                                     s.max_depth, L, R, f16, lab, 1e-2)
+        feat = f16.float().cpu().numpy()
+        n = torch.zeros(1, dtype=torch.int32, device="cuda")
+        capi.rt_render_stereo_reproj(g.handle, s.camera, s.eye_sep, s.convergence, W, H,
+                                     s.max_depth, net.handle, thr, L, R, n)
+        capi.rt_sync_status(g.handle)
+        capi.rt_net_status(net.handle)
+        assert torch.equal(L, fL)
+        Lh, Rh, fRh = L.cpu().numpy(), R.cpu().numpy(), fR.cpu().numpy()
+    finally:
+        net.close()
+        g.close()
+    f_px = capi.focal_px(s.camera, H)
+    _, hole, warped, _ = orp.warp(depth_L, np.zeros((P, 3)), np.zeros(P, np.uint32), Lh, W, H,
+                                  f_px, s.eye_sep, s.convergence)
+    p = orp.forward(params, feat, W, H, bf16=True).reshape(P)
+    near = np.abs(p - thr) < 5e-3
+    want = hole | (p > thr)
+    R2, F2, Wp = Rh.reshape(P, 3), fRh.reshape(P, 3), warped.reshape(P, 3).astype(np.float32)
+    sel = want & ~near
+    assert np.array_equal(R2[sel], F2[sel])                       # retraced = full trace
+    keep = ~want & ~near
+    assert np.array_equal(R2[keep], Wp[keep])                     # others = warped colour
+    assert abs(int(n.item()) - int(want.sum())) <= int(near.sum())
+    # a mixed mask: some pixels retraced for p > thr beyond the holes, most kept
+    assert (want & ~hole).sum() > 0 and 0 < want.mean() < 0.5, (want.sum(), hole.sum())

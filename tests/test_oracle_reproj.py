@@ -273,3 +273,123 @@ def test_fp8_forward_close_to_float64_network():
     p8 = orp.forward_fp8(params, feat, W, H, (8.0, 8.0, 8.0))
     assert np.abs(p8 - ref).max() < 0.1 and np.abs(p8 - ref).mean() < 0.02
     assert np.abs(x - ref).max() < np.abs(p8 - ref).max()     # FP8 loses more than BF16
+
+
+# ---------------------------------- BF16 rounding points, pinned exactly
+# Independent restatements (no PyTorch convolution or autograd) of the
+# network with BF16 rounding where the tensor-core kernels round: inputs,
+# weights and hidden activations in the forward pass; the (p - y) map fed
+# to the layer-4 data gradient (the layer-4 weight gradient takes p - y
+# unrounded) and every data gradient after its ReLU mask in the backward
+# pass. Random values carry ~50 significant bits, so each rounding moves
+# results by ~2^-9 relative: dropping or moving one rounding point fails the
+# 1e-9 comparisons below by many orders of magnitude.
+def _rne_bf16(x):
+    """Round to 8 significant bits, ties to even (BF16 in its normal range)."""
+    m, e = np.frexp(np.asarray(x, np.float64))
+    return np.ldexp(np.round(m * 256.0) / 256.0, e)
+
+
+def _pad(a):
+    C, H, W = a.shape
+    ap = np.zeros((C, H + 2, W + 2))
+    ap[:, 1:-1, 1:-1] = a
+    return ap
+
+
+def _conv_wgrad(a, dz):
+    """dW[o, c, ky, kx] = sum_{y, x} dz[o, y, x] a_pad[c, y + ky, x + kx]."""
+    C, H, W = a.shape
+    ap = _pad(a)
+    dW = np.zeros((dz.shape[0], C, 3, 3))
+    for ky in range(3):
+        for kx in range(3):
+            dW[:, :, ky, kx] = np.einsum("oyx,cyx->oc", dz, ap[:, ky:ky + H, kx:kx + W])
+    return dW
+
+
+def _conv_dgrad(dz, w, H, W):
+    """Data gradient of a 3x3 zero-padded cross-correlation: every output
+    dz[o, y, x] sends w[o, c, ky, kx] dz[o, y, x] back to input (c, y+ky-1,
+    x+kx-1)."""
+    dap = np.zeros((w.shape[1], H + 2, W + 2))
+    for ky in range(3):
+        for kx in range(3):
+            dap[:, ky:ky + H, kx:kx + W] += np.einsum("oc,oyx->cyx", w[:, :, ky, kx], dz)
+    return dap[:, 1:-1, 1:-1]
+
+
+def _net_loops_bf16(params, feat, label, W, H):
+    """Probability map and mean-BCE gradient with BF16 rounding points."""
+    layers = orp.unpack(np.asarray(params, np.float64))
+    a = [_rne_bf16(np.asarray(feat, np.float64)[:, :9].reshape(H, W, 9).transpose(2, 0, 1))]
+    for li in range(3):
+        w, b = layers[li]
+        a.append(_rne_bf16(np.maximum(_conv_loops(a[-1], _rne_bf16(w), b), 0.0)))
+    w4, b4 = layers[3]
+    q = 1.0 / (1.0 + np.exp(-_conv_loops(a[3], _rne_bf16(w4), b4)))
+    P = W * H
+    g = q - np.asarray(label, np.float64).reshape(1, H, W)
+    grads = [None] * 4
+    dz_w, dz_in = g, _rne_bf16(g)            # layer 4: weight gradient unrounded
+    for li in (3, 2, 1, 0):
+        w, _ = layers[li]
+        grads[li] = (_conv_wgrad(a[li], dz_w) / P, dz_w.sum(axis=(1, 2)) / P)
+        if li > 0:
+            da = _conv_dgrad(dz_in, _rne_bf16(w), H, W)
+            dz_w = dz_in = _rne_bf16(da * (a[li] > 0))
+    flat = np.concatenate([np.concatenate([dw.reshape(-1), db]) for dw, db in grads])
+    return q[0], flat
+
+
+def _bf16_case():
+    W, H = 7, 5
+    params = sg.net_params_he(15).astype(np.float64)
+    params += 0.01 * np.random.default_rng(16).standard_normal(params.size)
+    feat = np.random.default_rng(17).random((W * H, 16))        # not BF16 values
+    y = (np.random.default_rng(18).random(W * H) < 0.4).astype(np.float64)
+    return params, feat, y, W, H
+
+
+def check_forward_bf16(mod):
+    params, feat, _, W, H = _bf16_case()
+    q, _ = _net_loops_bf16(params, feat, np.zeros(W * H), W, H)
+    got = mod.forward(params, feat, W, H, bf16=True)
+    assert np.abs(got - q).max() <= 1e-9, np.abs(got - q).max()
+
+
+def check_grads_bf16(mod):
+    params, feat, y, W, H = _bf16_case()
+    _, g = _net_loops_bf16(params, feat, y, W, H)
+    got = mod.grads_emulated(params, feat, y, W, H, bf16=True)
+    k = 0
+    for ci, co in orp.LAYERS:
+        for n in (co * ci * 9, co):
+            a, b = got[k:k + n], g[k:k + n]
+            assert np.abs(a - b).max() <= 1e-9 * max(1e-3, np.abs(b).max()), (k, n, np.abs(a - b).max())
+            k += n
+
+
+def test_forward_bf16_rounding_points_match_explicit_loops():
+    check_forward_bf16(orp)
+    # the rounding matters at this size: the unrounded network is far away
+    params, feat, _, W, H = _bf16_case()
+    q, _ = _net_loops_bf16(params, feat, np.zeros(W * H), W, H)
+    assert np.abs(orp.forward(params, feat, W, H, bf16=False) - q).max() > 1e-5
+
+
+def test_emulated_backward_bf16_rounding_points_match_explicit_loops():
+    check_grads_bf16(orp)
+    params, feat, y, W, H = _bf16_case()
+    _, g = _net_loops_bf16(params, feat, y, W, H)
+    plain = orp.grads_emulated(params, feat, y, W, H, bf16=False)
+    assert np.abs(plain - g).max() > 1e-6
+
+
+def test_rne_bf16_helper_against_hand_values():
+    # 1 + 2^-8 is the tie between 1 and 1 + 2^-7: even mantissa -> 1
+    assert _rne_bf16(1.0 + 2.0 ** -8) == 1.0
+    assert _rne_bf16(1.0 + 3 * 2.0 ** -8) == 1.0 + 2.0 ** -6     # tie -> even (...10)
+    assert _rne_bf16(1.0 + 2.0 ** -8 + 2.0 ** -20) == 1.0 + 2.0 ** -7
+    assert _rne_bf16(-3.0) == -3.0 and _rne_bf16(0.0) == 0.0
+    assert _rne_bf16(255.5) == 256.0 and _rne_bf16(2.0 ** 130 * 1.3) == 2.0 ** 130 * (166 / 128)
