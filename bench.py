@@ -207,7 +207,8 @@ def cpu_baseline(scene, n_pixels: int, seed: int = 7):
     r = osc.render(pixels=pix, n_threads=cores)
     dt = time.perf_counter() - t0
     rays = int(r["rays"].sum())
-    return {"seconds": dt, "rays": rays, "pixels": n_pixels, "cores": cores,
+    order = "seeded random sample" if 0 < n_pixels < total else "every pixel, row order"
+    return {"seconds": dt, "rays": rays, "pixels": n_pixels, "cores": cores, "order": order,
             "mrays_per_s": rays / dt / 1e6,
             "pairs_per_s_est": (n_pixels / (2 * scene.W * scene.H)) / dt}
 
@@ -651,8 +652,8 @@ def run_ours(args, rank, world, local):
         cb = cpu_baseline(s, args.cpu_sample)
         line["cpu_baseline"] = {"value": round(cb["mrays_per_s"], 4), "unit": UNIT,
                                 "cores": cb["cores"], "kind": "oracle",
-                                "sample": f"{cb['pixels']} seeded random pixels of the workload "
-                                          f"({cb['rays']} rays, {cb['seconds']:.1f} s, FP64)",
+                                "sample": f"{cb['pixels']} pixels of the workload ({cb['order']}; "
+                                          f"{cb['rays']} rays, {cb['seconds']:.1f} s, FP64)",
                                 "stereo_pairs_per_s_est": round(cb["pairs_per_s_est"], 6)}
     g.close()
     if world > 1:

@@ -36,6 +36,9 @@ MUTANTS = [
     ("box not outward", "if ((double)f < s || ((double)f == s && err > 0.0)) f = nextafterf(f, INFINITY);", ""),
     ("shadow ignored", "if (!occ) lsum += (double)s->li[l].intensity * ndl;", "lsum += (double)s->li[l].intensity * ndl;"),
     ("light vector sign", "v3 lv = sub(vf(s->li[l].pos), o2);", "v3 lv = sub(o2, vf(s->li[l].pos));"),
+    ("no near tie at the shadow cut-off",
+     "if (!is_best && fabs(t - tlim) * dl <= fmax(TIE_REL * tlim * dl, delta_k)) return 1;", ""),
+    ("no near tie for a grazing light", "if (fabs(ndl) < TIE_REL) tc->flagged = 1;", ""),
 ]
 
 
@@ -51,3 +54,43 @@ def test_pins_catch_planted_mistake(name, orig, bad, tmp_path):
                         os.path.join(ROOT, "tests", "test_oracle_pins.py")],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"the pins did not catch the mutant '{name}'"
+
+
+# The network oracle (oracle/reproj.py) with one BF16 rounding point dropped
+# or moved: the exact rounding-point pins must fail on each.
+REPROJ_SRC = os.path.join(ROOT, "oracle", "reproj.py")
+REPROJ_MUTANTS = [
+    ("forward: weights unrounded", "            wt = _bf16(wt)\n", "            pass\n", "forward"),
+    ("forward: hidden activations unrounded", "                x = _bf16(x)\n", "                pass\n",
+     "forward"),
+    ("forward: input unrounded", "        x = _bf16(x)\n    layers = unpack(params)",
+     "        pass\n    layers = unpack(params)", "forward"),
+    ("backward: input unrounded",
+     "a = [rb(torch.tensor(np.asarray(feat, np.float64)[:, :9].reshape(H, W, 9)).permute(2, 0, 1)[None])]",
+     "a = [torch.tensor(np.asarray(feat, np.float64)[:, :9].reshape(H, W, 9)).permute(2, 0, 1)[None]]",
+     "grads"),
+    ("backward: hidden activations unrounded",
+     "a.append(rb(torch.relu(F.conv2d(a[-1], rb(w), b, padding=1))))",
+     "a.append(torch.relu(F.conv2d(a[-1], rb(w), b, padding=1)))", "grads"),
+    ("backward: data-gradient weights unrounded",
+     "da = G.conv2d_input(a[li].shape, rb(w), dz_in, padding=1)",
+     "da = G.conv2d_input(a[li].shape, w, dz_in, padding=1)", "grads"),
+    ("backward: p - y rounded for the layer-4 weight gradient", "    dz = g\n", "    dz = rb(g)\n", "grads"),
+    ("backward: p - y unrounded for the data gradient", "dz_in = rb(g)", "dz_in = g", "grads"),
+    ("backward: masked data gradient unrounded", "dz = rb(da * (a[li] > 0))", "dz = da * (a[li] > 0)",
+     "grads"),
+]
+
+
+@pytest.mark.parametrize("name,orig,bad,which", REPROJ_MUTANTS, ids=[m[0] for m in REPROJ_MUTANTS])
+def test_network_pins_catch_planted_mistake(name, orig, bad, which):
+    import types
+
+    from tests import test_oracle_reproj as pins
+    src = open(REPROJ_SRC).read()
+    assert src.count(orig) == 1, f"mutation site not unique: {orig!r}"
+    mod = types.ModuleType("reproj_mutant")
+    exec(compile(src.replace(orig, bad), "reproj_mutant.py", "exec"), mod.__dict__)
+    check = pins.check_forward_bf16 if which == "forward" else pins.check_grads_bf16
+    with pytest.raises(AssertionError):
+        check(mod)

@@ -431,3 +431,58 @@ def test_pixel_list_matches_full_render():
     assert np.array_equal(part["rgb"], full["rgb"].reshape(-1, 3)[pix])
     assert np.array_equal(part["hit_id"], full["hit_id"].reshape(-1)[pix])
     assert part["rays"][0] == len(pix) and full["rays"][0] == 2 * 64 * 48
+
+
+# ------------------------------------------- near-tie criteria (iv), (v)
+# One pixel looking down -z at a large triangle in the plane z = -5 (hit
+# point (0, 0, -5), normal +z, secondary origin o2 = p + 5e-4 n); the pixel
+# is flagged (bit 1) when some decision of its ray tree is within relative
+# 1e-5 of flipping, and not flagged 1e-3 away from the decision.
+_GROUND = [((-1000.0, -1000.0, -5.0), (1000.0, -1000.0, -5.0), (0.0, 1000.0, -5.0), 0)]
+_O2 = np.array([0.0, 0.0, -5.0 + 5e-4])
+
+
+def _one_pixel(tris, light):
+    return scene(tris=tris, mats=[(0.5, 0.5, 0.5, 0.0)], lights=[(tuple(light), 1.0)],
+                 W=1, H=1, eye_sep=0.0, max_depth=0)
+
+
+@pytest.mark.parametrize("c,flagged", [(1e-6, True), (-1e-6, True), (1e-3, False), (-1e-3, False)])
+def test_near_tie_flag_grazing_light(c, flagged):
+    """n.l = c: a light 100 away from o2 at elevation asin(c) over the plane;
+    |n.l| < 1e-5 is a near tie whatever its sign (criterion (v))."""
+    L = _O2 + 100.0 * np.array([math.sqrt(1.0 - c * c), 0.0, c])
+    r = oracle.render(_one_pixel(_GROUND, L))
+    assert r["hit_id"][0, 0, 0] == 0
+    assert bool(r["flags"][0, 0, 0] & 2) == flagged, r["flags"][0, 0, 0]
+    if not flagged:
+        # lit when the light is above the plane, ambient only below it
+        expect = 0.5 * (KA + max(c, 0.0))
+        assert np.allclose(r["rgb"][0, 0, 0], expect, atol=1e-9)
+
+
+@pytest.mark.parametrize("delta,flagged,lit", [(1e-6, True, None), (-1e-6, True, None),
+                                               (1e-3, False, True), (-1e-3, False, False)])
+def test_near_tie_flag_occluder_at_the_shadow_cutoff(delta, flagged, lit):
+    """A small occluder triangle, perpendicular to the shadow ray, at distance tmax (1 + delta)
+    from o2, tmax = |L - o2| - eps: within relative 1e-5 of the cut-off it is
+    a near tie (criterion (iv)); 1e-3 before it blocks the light, 1e-3 past
+    it does not."""
+    L = np.array([3.0, 0.0, -1.0])
+    lv = L - _O2
+    ld = float(np.linalg.norm(lv))
+    lh = lv / ld
+    tmax = ld - 5e-4
+    c = _O2 + lh * tmax * (1.0 + delta)
+    u = np.cross(lh, [0.0, 1.0, 0.0])
+    u /= np.linalg.norm(u)
+    v = np.cross(lh, u)
+    h = 0.005
+    occ = [(tuple(c - h * u - h * v), tuple(c + h * u - h * v), tuple(c + h * v), 0)]
+    r = oracle.render(_one_pixel(_GROUND + occ, L))
+    assert r["hit_id"][0, 0, 0] == 0
+    assert bool(r["flags"][0, 0, 0] & 2) == flagged, r["flags"][0, 0, 0]
+    if lit is not None:
+        ndl = float(lh[2])
+        expect = 0.5 * (KA + (ndl if lit else 0.0))
+        assert np.allclose(r["rgb"][0, 0, 0], expect, atol=1e-6), (r["rgb"][0, 0, 0], expect)
