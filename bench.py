@@ -75,6 +75,10 @@ def parse():
     ap.add_argument("--sequence-only", action="store_true",
                     help="print only the 4K terrain-sequence measurement as one JSON object")
     ap.add_argument("--sequence-frames", type=int, default=120)
+    ap.add_argument("--split", choices=["replicas", "rows"], default="replicas",
+                    help="replicas: every rank renders the whole pair (weak scaling); rows: "
+                         "rank r of N renders band r of the pair's rows over its own copy of "
+                         "the scene and the bands are gathered on rank 0 (strong scaling)")
     ap.add_argument("--study", action="store_true",
                     help="print one JSON object with the stage split of the small and blob "
                          "scenes, the polyhedra complexity sweep, the L2 / MUFU probes and the "
@@ -444,6 +448,91 @@ def sequence_leg(stream, n_frames=120, per_launch=8):
         net.close()
         g.close()
     return out
+
+
+# ------------------------------------------------------ row-band split
+def run_split_rows(args, rank, world, local):
+    """Strong scaling over N GPUs (paper Figure 1): rank r renders rows
+    row_bands(H, N)[r] of both eyes (rt_render_stereo_rows) over its own copy
+    of the scene. One step = every band of one pair, then the bands gathered
+    into whole images on rank 0 (NCCL all-gather); the gather is timed
+    separately as well. value = the pair's rays / the slowest rank's step."""
+    import torch
+    import torch.distributed as dist
+
+    from paper_1702_01530_gb300 import bands, capi
+    from paper_1702_01530_gb300 import build as rtbuild
+
+    rtbuild.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    s = workload(args)
+    stream = torch.cuda.current_stream()
+    g = capi.GpuScene(s)
+    r0, k = bands.row_bands(s.H, world)[rank]
+    bl = torch.empty((max(k, 1), s.W, 3), dtype=torch.float32, device=dev)
+    br = torch.empty_like(bl)
+    rays = torch.zeros(3, dtype=torch.int64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def band(count=False):
+        if k > 0:
+            capi.rt_render_stereo_rows(g.handle, s.camera, s.eye_sep, s.convergence, s.W, s.H,
+                                       s.max_depth, r0, k, bl, br, rays if count else None, stream)
+
+    band(count=True)
+    capi.rt_sync_status(g.handle)
+    band_rays = rays.clone()
+    if world > 1:
+        dist.all_reduce(band_rays)
+    total_rays = int(band_rays.sum().item())
+    clk = ClockSampler(local).__enter__()
+    for _ in range(args.warmup):
+        band()
+        if world > 1:
+            bands.gather_bands(bl, br, s.H, rank, world)
+    render_ms, step_ms = [], []
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        band()
+        e1.record(stream)
+        if world > 1:
+            bands.gather_bands(bl, br, s.H, rank, world)
+        e2.record(stream)
+        e2.synchronize()
+        render_ms.append(e0.elapsed_time(e1))
+        step_ms.append(e0.elapsed_time(e2))
+    torch.cuda.synchronize()
+    clk.__exit__()
+    if world > 1:
+        dist.barrier()
+    capi.rt_sync_status(g.handle)
+    ms, ms_render = max_over_ranks([float(np.mean(step_ms)), float(np.mean(render_ms))], world, dev)
+    if rank == 0:
+        line = {"metric": METRIC, "value": round(total_rays / (ms * 1e-3) / 1e6, 2), "unit": UNIT,
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "strong",
+                "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic (seeded scene generator; no dataset)",
+                "config": {"workload": WORKLOAD, "seed": args.seed, "W": s.W, "H": s.H,
+                           "max_depth": s.max_depth, "parallelism": f"rowbands{world}",
+                           "bands": bands.row_bands(s.H, world),
+                           "l2": "flushed before every timed step (256 MiB write), per-step CUDA events"},
+                "stereo_pairs_per_s": round(1.0 / (ms * 1e-3), 2),
+                "render_ms_slowest_rank": round(ms_render, 4),
+                "gather_ms": round(ms - ms_render, 4),
+                "gpu_launches": int(args.steps * 2), "clocks": clk.summary()}
+        print(json.dumps(line))
+    g.close()
+    if world > 1:
+        dist.destroy_process_group()
 
 
 # ---------------------------------------------------------------- our arm
@@ -957,6 +1046,8 @@ def main():
         return
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.split == "rows":
+        run_split_rows(args, rank, world, local)
     else:
         run_ours(args, rank, world, local)
 

@@ -65,3 +65,64 @@ def test_single_rank_needs_no_process_group():
     import bench
     assert bench.max_over_ranks([1.5, 3.0], 1) == [1.5, 3.0]
     assert bench.job_rates(1_000_000, 1, 1.0) == pytest.approx((1000.0, 1000.0))
+
+
+# ------------------------------------------------------------ row bands
+def test_row_bands_partition():
+    from paper_1702_01530_gb300.bands import row_bands
+    assert row_bands(10, 3) == [(0, 4), (4, 3), (7, 3)]
+    assert row_bands(1080, 8) == [(135 * r, 135) for r in range(8)]
+    assert row_bands(2, 4) == [(0, 1), (1, 1), (2, 0), (2, 0)]
+    for H in (1, 7, 61, 1080):
+        for n in (1, 2, 3, 5, 8):
+            b = row_bands(H, n)
+            assert sum(k for _, k in b) == H and b[0][0] == 0
+            assert all(b[i][0] + b[i][1] == b[i + 1][0] for i in range(n - 1))
+            assert max(k for _, k in b) - min(k for _, k in b) <= 1
+
+
+def _band_rank(rank, world, port, H, W, queue):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world))
+    sys.path.insert(0, ROOT)
+    import torch
+    import torch.distributed as dist
+
+    from paper_1702_01530_gb300.bands import gather_bands, row_bands
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        # each rank "renders" its band of a known image: value = row * 1000 + col (+0.5 right eye)
+        r0, k = row_bands(H, world)[rank]
+        rows = torch.arange(r0, r0 + k, dtype=torch.float32)[:, None, None]
+        cols = torch.arange(W, dtype=torch.float32)[None, :, None]
+        band_L = (rows * 1000 + cols).expand(k, W, 3).contiguous()
+        band_R = band_L + 0.5
+        out = gather_bands(band_L, band_R, H, rank, world)
+        if rank == 0:
+            L, R = out
+            queue.put((rank, L.numpy().copy(), R.numpy().copy()))
+        else:
+            queue.put((rank, out, None))
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.timeout(120)
+def test_two_gloo_ranks_gather_uneven_bands_in_row_order():
+    import numpy as np
+    world, H, W = 2, 7, 5
+    ctx = mp.get_context("spawn")
+    queue = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_band_rank, args=(r, world, port, H, W, queue)) for r in range(world)]
+    for p in procs:
+        p.start()
+    out = dict((r, (a, b)) for r, a, b in (queue.get(timeout=90) for _ in range(world)))
+    for p in procs:
+        p.join(timeout=30)
+        assert p.exitcode == 0
+    want = (np.arange(H)[:, None] * 1000 + np.arange(W)[None, :]).astype(np.float32)
+    L, R = out[0]
+    assert np.array_equal(L, np.repeat(want[:, :, None], 3, axis=2))
+    assert np.array_equal(R, L + 0.5)
+    assert out[1] == (None, None)
