@@ -151,6 +151,27 @@ int rt_render_stereo_aux(const rt_scene* scene, const rt_camera* cam,
                          void* cuda_stream);
 
 /*
+ * rt_render_stereo_rows -- a horizontal band of both eyes of a stereo pair.
+ * Paper: Sec. 3, Figure 1 (the image is divided into parts and each
+ * processor renders its part); with several GPUs, each renders one band of
+ * rows of both eyes over its own copy of the scene. The rays are those of
+ * the whole W x H pair: the rows row0 .. row0 + n_rows - 1 of the band equal
+ * the same rows of rt_render_stereo bit for bit, so bands stitched in row
+ * order give the full pair.
+ *   W, H: the whole image; 1 <= n_rows, row0 + n_rows <= H.
+ *   out_L, out_R: DEVICE buffers of n_rows*W*3 float32 each, row-major
+ *     (band row 0 = image row row0); owned by the caller.
+ *   ray_counts: DEVICE 3 uint64 or NULL (rays of the band by kind).
+ * Otherwise as rt_render_stereo (asynchronous on cuda_stream).
+ */
+int rt_render_stereo_rows(const rt_scene* scene, const rt_camera* cam,
+                          float eye_sep, float convergence,
+                          uint32_t W, uint32_t H, uint32_t max_depth,
+                          uint32_t row0, uint32_t n_rows,
+                          float* out_L, float* out_R, uint64_t* ray_counts,
+                          void* cuda_stream);
+
+/*
  * rt_render_stereo_host -- end-to-end render into HOST buffers.
  * Paper: Sec. 4-5 (the synthesis time splits into GPU computation and the
  * copies between CPU and GPU memory). Both images land in host_L/host_R
@@ -507,6 +528,26 @@ int rt_render_stereo_reproj(const rt_scene* scene, const rt_camera* cam, float e
                             float convergence, uint32_t W, uint32_t H, uint32_t max_depth,
                             rt_net* net, float threshold, float* d_out_L, float* d_out_R,
                             uint32_t* d_n_retraced, void* cuda_stream);
+
+/*
+ * rt_render_stereo_reproj_frames -- rt_render_stereo_reproj for up to
+ * RT_MAX_FRAMES frames of one scene in one pass: each stage runs once for
+ * all frames (one launch traces the left eyes of every frame, one warps
+ * them, one per network layer classifies every right pixel, one retraces
+ * the masked right pixels of every frame, one composes). Frame f's images
+ * equal those of rt_render_stereo_reproj with cams[f] bit for bit.
+ *   cams: HOST array of n_frames cameras (1 <= n_frames <= RT_MAX_FRAMES),
+ *     all with the same vfov_deg (the warp needs one focal length).
+ *   d_out_L, d_out_R: DEVICE, n_frames*H*W*3 float32 each, frame after frame
+ *     (each frame laid out as rt_render_stereo's images).
+ *   d_n_retraced: DEVICE uint32 or NULL: right pixels retraced, all frames.
+ * Otherwise as rt_render_stereo_reproj (asynchronous on cuda_stream).
+ */
+#define RT_MAX_FRAMES 8
+int rt_render_stereo_reproj_frames(const rt_scene* scene, const rt_camera* cams, uint32_t n_frames,
+                                   float eye_sep, float convergence, uint32_t W, uint32_t H,
+                                   uint32_t max_depth, rt_net* net, float threshold, float* d_out_L,
+                                   float* d_out_R, uint32_t* d_n_retraced, void* cuda_stream);
 
 /*
  * rt_stereo_composite -- convert a stereo pair into a display frame.

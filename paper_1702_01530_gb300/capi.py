@@ -51,6 +51,8 @@ _SIGS = {
                                                  _vp, _vp, _vp]),
     "rt_render_stereo_host": (ctypes.c_int, [_vp, _vp, _f32, _f32, _u32, _u32, _u32, _vp, _vp,
                                              _vp]),
+    "rt_render_stereo_rows": (ctypes.c_int, [_vp, _vp, _f32, _f32, _u32, _u32, _u32, _u32, _u32,
+                                             _vp, _vp, _vp, _vp]),
     "rt_sync_status": (ctypes.c_int, [_vp, _vp]),
     "rt_scene_get_bvh": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "rt_scene_num_prims": (_u32, [_vp]),
@@ -80,6 +82,8 @@ _SIGS = {
                                                _vp, _vp, _f32, _vp]),
     "rt_render_stereo_reproj": (ctypes.c_int, [_vp, _vp, _f32, _f32, _u32, _u32, _u32, _vp, _f32,
                                                _vp, _vp, _vp, _vp]),
+    "rt_render_stereo_reproj_frames": (ctypes.c_int, [_vp, _vp, _u32, _f32, _f32, _u32, _u32, _u32,
+                                                      _vp, _f32, _vp, _vp, _vp, _vp]),
     "rt_stereo_composite": (ctypes.c_int, [_vp, _vp, _u32, _u32, ctypes.c_int, _vp, _vp]),
     "rt_batch_create": (ctypes.c_int, [_vp, _u32, _vp, ctypes.POINTER(_vp)]),
     "rt_batch_destroy": (None, [_vp]),
@@ -199,6 +203,16 @@ def rt_render_stereo_aux(scene, camera, eye_sep, convergence, W, H, max_depth, o
                                       _dptr(out_L), _dptr(out_R), _dptr(hit_id_L),
                                       _dptr(hit_id_R), _dptr(depth_L), _dptr(depth_R),
                                       _dptr(ray_counts), _dptr(work), _stream(stream)))
+
+
+def rt_render_stereo_rows(scene, camera, eye_sep, convergence, W, H, max_depth, row0, n_rows,
+                          out_L, out_R, ray_counts=None, stream=None):
+    """Rows row0 .. row0 + n_rows - 1 of both eyes of the W x H pair into
+    band buffers of n_rows x W x 3 float32 each."""
+    c, pc = _cam(camera)
+    _check(lib().rt_render_stereo_rows(scene, pc, eye_sep, convergence, W, H, max_depth, row0,
+                                       n_rows, _dptr(out_L), _dptr(out_R), _dptr(ray_counts),
+                                       _stream(stream)))
 
 
 def _hptr(x):
@@ -500,6 +514,20 @@ def rt_render_stereo_reproj(scene, camera, eye_sep, convergence, W, H, max_depth
     _check(lib().rt_render_stereo_reproj(scene, pc, eye_sep, convergence, W, H, max_depth, net,
                                          threshold, _dptr(out_L), _dptr(out_R), _dptr(n_retraced),
                                          _stream(stream)))
+
+
+RT_MAX_FRAMES = 8
+
+
+def rt_render_stereo_reproj_frames(scene, cameras, eye_sep, convergence, W, H, max_depth, net,
+                                   threshold, out_L, out_R, n_retraced=None, stream=None):
+    """Learned reprojection of len(cameras) <= RT_MAX_FRAMES frames in one
+    pass; out_L / out_R hold (frames, H, W, 3) float32 each."""
+    cams = np.ascontiguousarray(np.asarray(cameras, dtype=scenegen.CAMERA_DT).reshape(-1))
+    _check(lib().rt_render_stereo_reproj_frames(scene, cams.ctypes.data, len(cams), eye_sep,
+                                                convergence, W, H, max_depth, net, threshold,
+                                                _dptr(out_L), _dptr(out_R), _dptr(n_retraced),
+                                                _stream(stream)))
 
 
 def focal_px(camera, H) -> float:

@@ -190,6 +190,17 @@ __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, i
       : "memory");
 }
 
+// 5-D tiled TMA load (the same, with an image index among the coordinates)
+__device__ __forceinline__ void tma_load_5d(void* dst, const CUtensorMap* map, int c0, int c1,
+                                            int c2, int c3, int c4, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4),
+      "r"(smem_u32(bar))
+      : "memory");
+}
+
 // 16 consecutive TMEM columns of this warp's 32 lanes
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
   uint32_t r[16];
@@ -296,7 +307,7 @@ __global__ void __launch_bounds__(kConvTmaThreads, 1)
     k_conv_tma(const __grid_constant__ CUtensorMap tmap, const void* __restrict__ wpk,
                const float* __restrict__ bias, const float* __restrict__ inv,
                float out_scale, const __nv_bfloat16* __restrict__ mask16, void* __restrict__ out,
-               float* __restrict__ out32, uint32_t W, uint32_t H, uint32_t* err) {
+               float* __restrict__ out32, uint32_t W, uint32_t H, uint32_t n_img, uint32_t* err) {
   using Lt = ConvTmaLayout<CIN, COUT, IN_FP8>;
   static_assert(CIN % 16 == 0 && (COUT == 16 || COUT == 32), "shape");
   static_assert(Lt::kTmemCols <= 512, "two accumulator sets must fit in TMEM");
@@ -313,8 +324,11 @@ __global__ void __launch_bounds__(kConvTmaThreads, 1)
   uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 12);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // n_img images of W x H pixels stacked in memory (image-major); a tile
+  // never spans two images, and the halo rows outside its image read zeros
   const uint32_t tiles_x = (W + kTileM - 1) / kTileM;
-  const uint32_t n_tiles = tiles_x * ((H + kRows - 1) / kRows);
+  const uint32_t tiles_img = tiles_x * ((H + kRows - 1) / kRows);
+  const uint32_t n_tiles = tiles_img * n_img;
   {
     const uint4* src = reinterpret_cast<const uint4*>(wpk);
     uint4* dst = reinterpret_cast<uint4*>(wsm);
@@ -353,17 +367,19 @@ __global__ void __launch_bounds__(kConvTmaThreads, 1)
       auto load = [&](uint32_t j) {
         const uint32_t tile = blockIdx.x + j * gridDim.x;
         const int b = (int)(j % kStages);
-        const int ty = (int)(tile / tiles_x);
-        const int y = ty * kRows, x0 = (int)(tile - (uint32_t)ty * tiles_x) * kTileM;
+        const int img = (int)(tile / tiles_img);
+        const uint32_t it_img = tile - (uint32_t)img * tiles_img;
+        const int ty = (int)(it_img / tiles_x);
+        const int y = ty * kRows, x0 = (int)(it_img - (uint32_t)ty * tiles_x) * kTileM;
         mbar_arrive_expect_tx(halo_full + b, (uint32_t)Lt::kChunks * Lt::kBox);
 #pragma unroll
         for (int c = 0; c < Lt::kChunks; ++c)
-          if (PLANAR_IN)   // tensor {16 B of channels, W, H, chunks}
-            tma_load_4d(halo0 + (size_t)b * Lt::kHalo + (size_t)c * Lt::kPlane, &tmap, 0, x0 - 1,
-                        y - 1, c, halo_full + b);
-          else             // tensor {16 B of channels, chunks, W, H}
-            tma_load_4d(halo0 + (size_t)b * Lt::kHalo + (size_t)c * Lt::kPlane, &tmap, 0, c, x0 - 1,
-                        y - 1, halo_full + b);
+          if (PLANAR_IN)   // tensor {16 B of channels, W, H, images, chunks}
+            tma_load_5d(halo0 + (size_t)b * Lt::kHalo + (size_t)c * Lt::kPlane, &tmap, 0, x0 - 1,
+                        y - 1, img, c, halo_full + b);
+          else             // tensor {16 B of channels, chunks, W, H, images}
+            tma_load_5d(halo0 + (size_t)b * Lt::kHalo + (size_t)c * Lt::kPlane, &tmap, 0, c, x0 - 1,
+                        y - 1, img, halo_full + b);
         issued_halo[b] = true;
         halo_par[b] = (j / kStages) & 1u;
       };
@@ -405,17 +421,19 @@ __global__ void __launch_bounds__(kConvTmaThreads, 1)
         break;
       }
       fence_after();
-      const int ty = (int)(tile / tiles_x);
+      const uint32_t img = tile / tiles_img;
+      const uint32_t it_img = tile - img * tiles_img;
+      const int ty = (int)(it_img / tiles_x);
       const int y = ty * kRows;
-      const int x0 = (int)(tile - (uint32_t)ty * tiles_x) * kTileM;
+      const int x0 = (int)(it_img - (uint32_t)ty * tiles_x) * kTileM;
       const int quarter = warp & 3, group = warp >> 2;   // TMEM lanes 32*quarter .. +31
       const int x = x0 + quarter * 32 + lane;
 #pragma unroll
       for (int ry = group; ry < kRows; ry += RT_CONV_EPI_WG) {
         const int yy = y + ry;
         const bool valid = x < (int)W && yy < (int)H;
-        const size_t p = (size_t)yy * W + x;
-        const size_t P = (size_t)W * H;
+        const size_t p = ((size_t)img * H + yy) * W + x;
+        const size_t P = (size_t)W * H * n_img;   // pixels of a channel plane
         const uint32_t lane_addr =
             tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)s * Lt::kSet + (uint32_t)(ry * COUT);
         if (EPI == EPI_SIGMOID_F32) {
@@ -747,29 +765,30 @@ EncodeTiledFn encode_tiled() {
 // {chunk elements, 1, 130, R+2}; planar [chunks][H][W][chunk elements] as
 // {chunk elements, W, H, chunks} with box {chunk elements, 130, R+2, 1}.
 template <int CIN, bool PLANAR, bool FP8>
-cudaError_t make_halo_map(CUtensorMap* map, const void* in, uint32_t W, uint32_t H) {
+cudaError_t make_halo_map(CUtensorMap* map, const void* in, uint32_t W, uint32_t H, uint32_t n_img) {
   const EncodeTiledFn fn = encode_tiled();
   if (!fn) return cudaErrorNotSupported;
   if (reinterpret_cast<uintptr_t>(in) & 15u) return cudaErrorInvalidValue;
   constexpr int kElem = FP8 ? 1 : 2, kPer = 16 / kElem, kChunks = CIN / kPer;
   const cuuint64_t P = (cuuint64_t)W * H;
-  cuuint64_t dims[4], strides[3];
-  cuuint32_t box[4];
-  if (PLANAR) {
-    const cuuint64_t d[4] = {kPer, W, H, kChunks};
-    const cuuint64_t st[3] = {16, (cuuint64_t)W * 16, P * 16};
-    const cuuint32_t bx[4] = {kPer, (cuuint32_t)kHaloW, (cuuint32_t)(kRows + 2), 1};
-    for (int i = 0; i < 4; ++i) { dims[i] = d[i]; box[i] = bx[i]; }
-    for (int i = 0; i < 3; ++i) strides[i] = st[i];
-  } else {
-    const cuuint64_t d[4] = {kPer, kChunks, W, H};
-    const cuuint64_t st[3] = {16, (cuuint64_t)CIN * kElem, (cuuint64_t)W * CIN * kElem};
-    const cuuint32_t bx[4] = {kPer, 1, (cuuint32_t)kHaloW, (cuuint32_t)(kRows + 2)};
-    for (int i = 0; i < 4; ++i) { dims[i] = d[i]; box[i] = bx[i]; }
-    for (int i = 0; i < 3; ++i) strides[i] = st[i];
+  cuuint64_t dims[5], strides[4];
+  cuuint32_t box[5];
+  if (PLANAR) {       // [chunks][images][H][W][chunk elements]
+    const cuuint64_t d[5] = {kPer, W, H, n_img, kChunks};
+    const cuuint64_t st[4] = {16, (cuuint64_t)W * 16, P * 16, P * n_img * 16};
+    const cuuint32_t bx[5] = {kPer, (cuuint32_t)kHaloW, (cuuint32_t)(kRows + 2), 1, 1};
+    for (int i = 0; i < 5; ++i) { dims[i] = d[i]; box[i] = bx[i]; }
+    for (int i = 0; i < 4; ++i) strides[i] = st[i];
+  } else {            // [images][H][W][chunks][chunk elements]
+    const cuuint64_t d[5] = {kPer, kChunks, W, H, n_img};
+    const cuuint64_t st[4] = {16, (cuuint64_t)CIN * kElem, (cuuint64_t)W * CIN * kElem,
+                              P * CIN * kElem};
+    const cuuint32_t bx[5] = {kPer, 1, (cuuint32_t)kHaloW, (cuuint32_t)(kRows + 2), 1};
+    for (int i = 0; i < 5; ++i) { dims[i] = d[i]; box[i] = bx[i]; }
+    for (int i = 0; i < 4; ++i) strides[i] = st[i];
   }
-  const cuuint32_t estr[4] = {1, 1, 1, 1};
-  const CUresult r = fn(map, FP8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4,
+  const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+  const CUresult r = fn(map, FP8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5,
                         const_cast<void*>(in), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                         CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -781,9 +800,9 @@ cudaError_t make_halo_map(CUtensorMap* map, const void* in, uint32_t W, uint32_t
 template <int CIN, int COUT, int EPI, bool IN_FP8 = false>
 cudaError_t launch_conv(const void* in, const void* wpk, const float* bias, const float* inv,
                         float out_scale, const __nv_bfloat16* mask16, void* out, float* out32,
-                        uint32_t W, uint32_t H, uint32_t* err, cudaStream_t st) {
+                        uint32_t W, uint32_t H, uint32_t* err, cudaStream_t st, uint32_t n_img = 1) {
   constexpr bool kPlanarIn = IN_FP8 || CIN == 32;
-  const uint32_t tiles = ((W + kTileM - 1) / kTileM) * ((H + kRows - 1) / kRows);
+  const uint32_t tiles = ((W + kTileM - 1) / kTileM) * ((H + kRows - 1) / kRows) * n_img;
   using Lt = ConvTmaLayout<CIN, COUT, IN_FP8>;
   size_t smem = Lt::kSmem + (size_t)(g_conv_smem_pad + conv_smem_pad());
   // a CTA that takes all 512 TMEM columns must be alone on its SM: ask for
@@ -797,7 +816,7 @@ cudaError_t launch_conv(const void* in, const void* wpk, const float* bias, cons
     configured = smem;
   }
   CUtensorMap map;
-  cudaError_t e = make_halo_map<CIN, kPlanarIn, IN_FP8>(&map, in, W, H);
+  cudaError_t e = make_halo_map<CIN, kPlanarIn, IN_FP8>(&map, in, W, H, n_img);
   if (e != cudaSuccess) return e;
   // resident CTAs per SM from the shared-memory footprint (227 KB usable,
   // 1 KB reserved per CTA) and the TMEM columns (512 per SM) each CTA takes
@@ -807,7 +826,7 @@ cudaError_t launch_conv(const void* in, const void* wpk, const float* bias, cons
   uint32_t grid = (uint32_t)(num_sms() * per_sm);
   if (grid > tiles) grid = tiles;
   k_conv_tma<CIN, COUT, EPI, kPlanarIn, IN_FP8><<<grid, kConvTmaThreads, smem, st>>>(
-      map, wpk, bias, inv, out_scale, mask16, out, out32, W, H, err);
+      map, wpk, bias, inv, out_scale, mask16, out, out32, W, H, n_img, err);
   return cudaGetLastError();
 }
 }  // namespace
@@ -837,19 +856,19 @@ cudaError_t pack_weights(const float* params, __nv_bfloat16* const wf[4], __nv_b
 
 cudaError_t forward(const __nv_bfloat16* feat16, const float* params, __nv_bfloat16* const wf[4],
                     __nv_bfloat16* act1, __nv_bfloat16* act2, __nv_bfloat16* act3, float* prob,
-                    uint32_t W, uint32_t H, uint32_t* err, cudaStream_t st) {
+                    uint32_t W, uint32_t H, uint32_t* err, cudaStream_t st, uint32_t n_img) {
   cudaError_t e;
   e = launch_conv<16, 32, EPI_RELU_BF16>(feat16, wf[0], params + kOffB[0], nullptr, 1.f, nullptr, act1,
-                                         nullptr, W, H, err, st);
+                                         nullptr, W, H, err, st, n_img);
   if (e != cudaSuccess) return e;
   e = launch_conv<32, 32, EPI_RELU_BF16>(act1, wf[1], params + kOffB[1], nullptr, 1.f, nullptr, act2,
-                                         nullptr, W, H, err, st);
+                                         nullptr, W, H, err, st, n_img);
   if (e != cudaSuccess) return e;
   e = launch_conv<32, 32, EPI_RELU_BF16>(act2, wf[2], params + kOffB[2], nullptr, 1.f, nullptr, act3,
-                                         nullptr, W, H, err, st);
+                                         nullptr, W, H, err, st, n_img);
   if (e != cudaSuccess) return e;
   return launch_conv<32, 16, EPI_SIGMOID_F32>(act3, wf[3], params + kOffB[3], nullptr, 1.f, nullptr,
-                                             nullptr, prob, W, H, err, st);
+                                             nullptr, prob, W, H, err, st, n_img);
 }
 
 cudaError_t pack_weights_fp8(const float* params, const float* const scale[3], uint8_t* const w8[3],
@@ -867,19 +886,19 @@ size_t packed_fp8_bytes(int l) { return 9ull * kCinPad[l] * kCoutPad[l]; }
 cudaError_t forward_fp8(const __nv_bfloat16* feat16, const float* params, __nv_bfloat16* const wf[4],
                         uint8_t* const w8[3], const float* const inv[3], const float act_scale[3],
                         uint8_t* act8_1, uint8_t* act8_2, uint8_t* act8_3, float* prob, uint32_t W,
-                        uint32_t H, uint32_t* err, cudaStream_t st) {
+                        uint32_t H, uint32_t* err, cudaStream_t st, uint32_t n_img) {
   cudaError_t e;
   e = launch_conv<16, 32, EPI_RELU_FP8>(feat16, wf[0], params + kOffB[0], nullptr, act_scale[0], nullptr,
-                                        act8_1, nullptr, W, H, err, st);
+                                        act8_1, nullptr, W, H, err, st, n_img);
   if (e != cudaSuccess) return e;
   e = launch_conv<32, 32, EPI_RELU_FP8, true>(act8_1, w8[0], params + kOffB[1], inv[0], act_scale[1],
-                                              nullptr, act8_2, nullptr, W, H, err, st);
+                                              nullptr, act8_2, nullptr, W, H, err, st, n_img);
   if (e != cudaSuccess) return e;
   e = launch_conv<32, 32, EPI_RELU_FP8, true>(act8_2, w8[1], params + kOffB[2], inv[1], act_scale[2],
-                                              nullptr, act8_3, nullptr, W, H, err, st);
+                                              nullptr, act8_3, nullptr, W, H, err, st, n_img);
   if (e != cudaSuccess) return e;
   return launch_conv<32, 16, EPI_SIGMOID_F32, true>(act8_3, w8[2], params + kOffB[3], inv[2], 1.f, nullptr,
-                                                    nullptr, prob, W, H, err, st);
+                                                    nullptr, prob, W, H, err, st, n_img);
 }
 
 // raises amax3[l] to the largest value of hidden activation l (the caller

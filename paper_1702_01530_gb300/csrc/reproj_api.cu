@@ -56,12 +56,13 @@ size_t a256(size_t b) { return (b + 255) & ~size_t(255); }
 // the network's forward pass in the precision it is set to (BF16, or FP8
 // after rt_net_set_fp8); act: three scratch maps of W*H*32 BF16 each
 cudaError_t net_forward(rt_net* net, const __nv_bfloat16* feat16, __nv_bfloat16* const act[3],
-                        float* prob, uint32_t W, uint32_t H, cudaStream_t st) {
+                        float* prob, uint32_t W, uint32_t H, cudaStream_t st, uint32_t n_img = 1) {
   if (!net->fp8)
-    return rt::nn::forward(feat16, net->params, net->wf, act[0], act[1], act[2], prob, W, H, net->err, st);
+    return rt::nn::forward(feat16, net->params, net->wf, act[0], act[1], act[2], prob, W, H, net->err, st,
+                           n_img);
   return rt::nn::forward_fp8(feat16, net->params, net->wf, net->w8, net->inv, net->act_scale,
                              reinterpret_cast<uint8_t*>(act[0]), reinterpret_cast<uint8_t*>(act[1]),
-                             reinterpret_cast<uint8_t*>(act[2]), prob, W, H, net->err, st);
+                             reinterpret_cast<uint8_t*>(act[2]), prob, W, H, net->err, st, n_img);
 }
 
 int net_buffers(rt_net* net, uint64_t P) {
@@ -534,6 +535,86 @@ int rt_render_stereo_reproj(const rt_scene* scene, const rt_camera* cam, float e
   if (e == cudaSuccess && d_n_retraced)
     e = cudaMemcpyAsync(d_n_retraced, rp.count, 4, cudaMemcpyDeviceToDevice, st);
   if (e != cudaSuccess) return cuda_fail(e, "reprojection render");
+  return RT_OK;
+}
+
+int rt_render_stereo_reproj_frames(const rt_scene* scene, const rt_camera* cams, uint32_t n_frames,
+                                   float eye_sep, float convergence, uint32_t W, uint32_t H,
+                                   uint32_t max_depth, rt_net* net, float threshold, float* d_out_L,
+                                   float* d_out_R, uint32_t* d_n_retraced, void* cuda_stream) {
+  if (!cams || n_frames < 1 || n_frames > (uint32_t)rt::kMaxFrames)
+    return fail(RT_ERR_INVALID_ARG, "need 1 <= n_frames <= RT_MAX_FRAMES cameras");
+  rt::RenderArgs a;
+  int rc = rt::make_render_args(scene, &cams[0], eye_sep, convergence, W, H, max_depth, a);
+  if (rc) return rc;
+  if (!d_out_L || !d_out_R || !std::isfinite(threshold)) return fail(RT_ERR_INVALID_ARG, "bad argument");
+  const uint64_t P = (uint64_t)W * H, FP = P * n_frames;
+  if (2 * FP > (1ull << 31)) return fail(RT_ERR_INVALID_ARG, "2 * n_frames * W * H exceeds 2^31");
+  // every frame's camera, validated like a single render's; the warp's
+  // disparity needs one focal length, so the vertical fields of view agree
+  rt::CameraParams frames[rt::kMaxFrames];
+  frames[0] = a.cam;
+  for (uint32_t f = 1; f < n_frames; ++f) {
+    if (cams[f].vfov_deg != cams[0].vfov_deg)
+      return fail(RT_ERR_INVALID_ARG, "all frames need the same vfov_deg");
+    rt::RenderArgs b;
+    rc = rt::make_render_args(scene, &cams[f], eye_sep, convergence, W, H, max_depth, b);
+    if (rc) return rc;
+    frames[f] = b.cam;
+  }
+  rc = rt::ensure_workspace(scene, W, H * n_frames);
+  if (!rc) rc = reproj_buffers(scene, FP);
+  if (!rc && net) rc = net_buffers(net, FP);
+  if (rc) return rc;
+  rt_scene* sc = const_cast<rt_scene*>(scene);
+  rt::ReprojBuffers& rp = sc->ws.rp;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  a.n_frames = n_frames;
+  a.frames = frames;
+  // 1. left eyes of all frames, one launch, with their G-buffers
+  rt::profile_begin(sc->ws, st);
+  a.eyes = 1u;
+  a.out_L = d_out_L; a.out_R = d_out_R;
+  a.hit_L = rp.id_L; a.depth_L = rp.depth_L; a.normal_L = rp.normal_L;
+  cudaError_t e = rt::render(a, sc->ws, st);
+  // 2. forward warp: it moves pixels along their row only, so the frames,
+  //    stacked as one image of n_frames * H rows, warp in one pass
+  if (e == cudaSuccess)
+    e = rt::reproj_warp(rp.depth_L, rp.normal_L, rp.id_L, d_out_L, W, H * n_frames, focal_px(&cams[0], H),
+                        eye_sep, convergence, rp.zbuf, net ? rp.feat16 : nullptr, nullptr, rp.hole,
+                        rp.warped, st);
+  rt::profile_mark(sc->ws, rt::ST_WARP, st);
+  // 3. the network over all frames, one launch per layer (a 3x3 window never
+  //    crosses from one frame into the next)
+  if (e == cudaSuccess && net) {
+    e = net_forward(net, rp.feat16, rp.act, rp.prob, W, H, st, n_frames);
+    rt::profile_mark(sc->ws, rt::ST_NET, st);
+  }
+  // 4. mask over every right pixel of every frame, compacted into one list
+  if (e == cudaSuccess)
+    e = rt::reproj_mask(rp.hole, net ? rp.prob : nullptr, (uint32_t)FP, threshold, rp.mask, rp.plist,
+                        rp.count, st);
+  rt::profile_mark(sc->ws, rt::ST_MASK, st);
+  // 5. the masked right pixels of all frames, one launch
+  if (e == cudaSuccess) {
+    rt::RenderArgs b = a;
+    b.eyes = 2u;
+    b.hit_L = nullptr; b.depth_L = nullptr; b.normal_L = nullptr;
+    b.plist = rp.plist;
+    b.plist_n = 0;
+    b.plist_n_dev = rp.count;
+    b.resolve = false;
+    b.trace_stage = rt::ST_RETRACE;
+    e = rt::render(b, sc->ws, st);
+  }
+  // 6. right images of all frames
+  if (e == cudaSuccess)
+    e = rt::reproj_compose(rp.mask, sc->ws.accum + 3 * FP, rp.warped, (uint32_t)FP,
+                           1.f / sc->color_scale, d_out_R, st);
+  rt::profile_mark(sc->ws, rt::ST_COMPOSE, st);
+  if (e == cudaSuccess && d_n_retraced)
+    e = cudaMemcpyAsync(d_n_retraced, rp.count, 4, cudaMemcpyDeviceToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(e, "multi-frame reprojection render");
   return RT_OK;
 }
 

@@ -147,6 +147,8 @@ int make_render_args(const rt_scene* scene, const rt_camera* cam, float eye_sep,
   a.cam.H = H;
   a.cam.tiles_x = (W + 7) / 8;
   a.cam.tiles_y = (H + 3) / 4;
+  a.cam.y0 = 0;
+  a.cam.rows = H;
   // binary renders walk the SAH tree unless the LBVH is asked for; the
   // 4-wide tree (and the work counts of a 4-wide scene) derive from the SAH
   // tree
@@ -330,6 +332,30 @@ int rt_render_stereo(const rt_scene* scene, const rt_camera* cam, float eye_sep,
                      void* cuda_stream) {
   return rt_render_stereo_aux(scene, cam, eye_sep, convergence, W, H, max_depth, out_L, out_R,
                               nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, cuda_stream);
+}
+
+int rt_render_stereo_rows(const rt_scene* scene, const rt_camera* cam, float eye_sep,
+                          float convergence, uint32_t W, uint32_t H, uint32_t max_depth,
+                          uint32_t row0, uint32_t n_rows, float* out_L, float* out_R,
+                          uint64_t* ray_counts, void* cuda_stream) {
+  rt::RenderArgs a;
+  int rc = make_render_args(scene, cam, eye_sep, convergence, W, H, max_depth, a);
+  if (rc) return rc;
+  if (n_rows < 1 || row0 >= H || n_rows > H - row0)
+    return fail(RT_ERR_INVALID_ARG, "rows row0 .. row0 + n_rows - 1 must lie inside 0 .. H - 1");
+  if (!out_L || !out_R) return fail(RT_ERR_INVALID_ARG, "output buffer is NULL");
+  rc = ensure_workspace(scene, W, n_rows);
+  if (rc) return rc;
+  a.cam.y0 = row0;
+  a.cam.rows = n_rows;
+  a.cam.tiles_y = (n_rows + 3) / 4;
+  a.out_L = out_L; a.out_R = out_R;
+  a.ray_counts = ray_counts;
+  rt::Workspace& ws = const_cast<rt_scene*>(scene)->ws;
+  rt::profile_begin(ws, static_cast<cudaStream_t>(cuda_stream));
+  cudaError_t e = rt::render(a, ws, static_cast<cudaStream_t>(cuda_stream));
+  if (e != cudaSuccess) return cuda_fail(e, "row-band render launch");
+  return RT_OK;
 }
 
 namespace {

@@ -52,8 +52,9 @@ struct DeviceScene {
 struct CameraParams {
   float eye[3], right[3], up[3], fwd[3];
   float tan_x, tan_y, zc, half_sep;
-  uint32_t W, H;
-  uint32_t tiles_x, tiles_y;  // 8x4-pixel tiles per eye
+  uint32_t W, H;              // the whole image (it fixes the rays)
+  uint32_t tiles_x, tiles_y;  // 8x4-pixel tiles per eye (of the traced rows)
+  uint32_t y0, rows;          // the rows traced: y0 .. y0 + rows - 1 (0 and H for a whole image)
 };
 
 // stages of one render, in launch order
@@ -160,7 +161,14 @@ struct RenderArgs {
   bool resolve;            // write out_L/out_R from the sums (false: caller composes)
   int trace_stage;         // stage the tracing kernel is timed as (ST_TRACE or ST_RETRACE)
   bool binary;             // traverse the binary tree instead of the 4-wide one
+  // several frames in one launch (0 or 1: just cam): n_frames cameras of the
+  // same image size in host memory (frames[0] is cam); pixel ids, sums,
+  // images and G-buffers then run over all frames, eye-major:
+  // eye * (n_frames P) + frame * P + pixel
+  uint32_t n_frames;
+  const CameraParams* frames;
 };
+constexpr int kMaxFrames = 8;
 
 // entry points implemented in the .cu files
 cudaError_t build_lbvh(const float4* d_sph_in, const float* d_tri_in, uint32_t ns, uint32_t nt,
@@ -206,9 +214,11 @@ size_t packed_fwd_elems(int l);
 size_t packed_bwd_elems(int l);
 cudaError_t pack_weights(const float* params, __nv_bfloat16* const wf[4], __nv_bfloat16* const wb[4],
                          cudaStream_t st);
+// forward / forward_fp8: n_img feature maps of W x H pixels each, stacked
+// image after image (one launch per layer for all of them)
 cudaError_t forward(const __nv_bfloat16* feat16, const float* params, __nv_bfloat16* const wf[4],
                     __nv_bfloat16* act1, __nv_bfloat16* act2, __nv_bfloat16* act3, float* prob,
-                    uint32_t W, uint32_t H, uint32_t* err, cudaStream_t st);
+                    uint32_t W, uint32_t H, uint32_t* err, cudaStream_t st, uint32_t n_img = 1);
 cudaError_t backward(const __nv_bfloat16* feat16, const float* label, __nv_bfloat16* const wb[4],
                      const __nv_bfloat16* act1, const __nv_bfloat16* act2,
                      const __nv_bfloat16* act3, const float* prob, __nv_bfloat16* g16, float* g32,
@@ -226,7 +236,7 @@ cudaError_t pack_weights_fp8(const float* params, const float* const scale[3], u
 cudaError_t forward_fp8(const __nv_bfloat16* feat16, const float* params, __nv_bfloat16* const wf[4],
                         uint8_t* const w8[3], const float* const inv[3], const float act_scale[3],
                         uint8_t* act8_1, uint8_t* act8_2, uint8_t* act8_3, float* prob, uint32_t W,
-                        uint32_t H, uint32_t* err, cudaStream_t st);
+                        uint32_t H, uint32_t* err, cudaStream_t st, uint32_t n_img = 1);
 cudaError_t activation_amax(const __nv_bfloat16* const act[3], uint64_t P, unsigned* amax3,
                             cudaStream_t st);
 }  // namespace nn

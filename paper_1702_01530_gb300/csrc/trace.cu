@@ -63,6 +63,9 @@ struct KParams {
   uint32_t n_tiles;    // primary tiles of 32 rays (pixel list: 32 entries each)
   bool share_partial;  // drain: hand over backlogs of less than a round too
   bool pair_eyes;      // primary tiles of 4x4 pixels of both eyes (else 8x4 of one eye)
+  uint32_t n_frames;   // frames traced by this launch (each its own camera, same image size)
+  uint32_t tiles_pf;   // primary tiles per frame
+  CameraParams cams[kMaxFrames];   // the camera of each frame (cams[0] = a.cam)
 };
 
 constexpr uint32_t kNullPix = 0xFFFFFFFFu;   // pool entry that carries no ray
@@ -176,7 +179,10 @@ k_render(KParams kp) {
     __syncthreads();
   }
   const CameraParams& cam = a.cam;
-  const uint32_t P = cam.W * cam.H;
+  const uint32_t P = cam.W * cam.rows;   // pixels per eye of the traced rows, one frame
+  // pixel ids: eye * FP + frame * P + row * W + column (eye-major: the left
+  // eyes of all frames first, so each eye's sums and images are contiguous)
+  const uint32_t FP = P * kp.n_frames;
   const uint32_t lane = lane_id();
   const uint32_t lt_mask = (1u << lane) - 1u;
   const size_t gwarp = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -295,7 +301,7 @@ k_render(KParams kp) {
         } else {
           s0 = e[0]; s1 = e[1]; s2 = e[2];
         }
-        if (__float_as_uint(s0.w) >= 2 * P) {     // an empty pool entry, or corrupt
+        if (__float_as_uint(s0.w) >= 2 * FP) {    // an empty pool entry, or corrupt
           if (__float_as_uint(s0.w) != kNullPix) atomicOr(a.err, ERR_INDEX);
           ok = false;
         }
@@ -313,32 +319,36 @@ k_render(KParams kp) {
     V3 o, d, w = v3(1.f, 1.f, 1.f);
     uint32_t pix = 0, depth = 0;
     if (mode == M_PRIMARY) {
-      uint32_t eye, px, py;
+      uint32_t eye, px, py, frame;
       if (a.plist) {                       // an explicit pixel list (masked retrace)
         const uint32_t i = tile * 32u + lane;
         active = i < plist_n;
         pix = active ? a.plist[i] : 0u;
-        if (pix >= 2 * P) { active = false; pix = 0u; }
-        eye = pix >= P;
-        const uint32_t pi = pix - eye * P;
+        if (pix >= 2 * FP) { active = false; pix = 0u; }
+        eye = pix >= FP;
+        const uint32_t r = pix - eye * FP;
+        frame = r / P;
+        const uint32_t pi = r - frame * P;
         py = pi / cam.W;
         px = pi - py * cam.W;
-      } else if (a.eyes == 3u && kp.pair_eyes) {   // 4x4 pixels of both eyes: lane 2q left, 2q+1 right
-        const uint32_t tx4 = (cam.W + 3u) / 4u, q = lane >> 1;
-        eye = lane & 1u;
-        px = (tile % tx4) * 4u + (q & 3u);
-        py = (tile / tx4) * 4u + (q >> 2);
-        active = px < cam.W && py < cam.H;
-        pix = eye * P + py * cam.W + px;
-      } else {                             // 8x4 tiles of one eye, eyes alternating when both are traced
-        const uint32_t tt = a.eyes == 3u ? tile >> 1 : tile;
-        eye = a.eyes == 3u ? (tile & 1u) : (a.eyes == 2u ? 1u : 0u);
-        px = (tt % cam.tiles_x) * 8u + (lane & 7u);
-        py = (tt / cam.tiles_x) * 4u + (lane >> 3);
-        active = px < cam.W && py < cam.H;
-        pix = eye * P + py * cam.W + px;
+      } else {
+        frame = tile / kp.tiles_pf;
+        const uint32_t ft = tile - frame * kp.tiles_pf;   // tile within its frame
+        if (a.eyes == 3u && kp.pair_eyes) {   // 4x4 pixels of both eyes: lane 2q left, 2q+1 right
+          const uint32_t tx4 = (cam.W + 3u) / 4u, q = lane >> 1;
+          eye = lane & 1u;
+          px = (ft % tx4) * 4u + (q & 3u);
+          py = (ft / tx4) * 4u + (q >> 2);
+        } else {                             // 8x4 tiles of one eye, eyes alternating when both are traced
+          const uint32_t tt = a.eyes == 3u ? ft >> 1 : ft;
+          eye = a.eyes == 3u ? (ft & 1u) : (a.eyes == 2u ? 1u : 0u);
+          px = (tt % cam.tiles_x) * 8u + (lane & 7u);
+          py = (tt / cam.tiles_x) * 4u + (lane >> 3);
+        }
+        active = px < cam.W && py < cam.rows;
+        pix = eye * FP + frame * P + py * cam.W + px;
       }
-      primary_ray(cam, px, py, eye, o, d);
+      primary_ray(kp.cams[frame < kp.n_frames ? frame : 0], px, cam.y0 + py, eye, o, d);
     } else {
       active = lane < take;
       if (active) {
@@ -356,7 +366,7 @@ k_render(KParams kp) {
         }
         o = xyz(q0);
         pix = __float_as_uint(q0.w);
-        if (pix >= 2 * P) {                         // an empty pool entry, or corrupt
+        if (pix >= 2 * FP) {                        // an empty pool entry, or corrupt
           if (pix != kNullPix) atomicOr(a.err, ERR_INDEX);
           active = false;
           pix = 0;
@@ -423,12 +433,15 @@ k_render(KParams kp) {
     nR += __popc(mr);
     made_r += __popc(mr);
     if (mode == M_PRIMARY && active) {
-      const uint32_t eye = pix >= P;
-      const uint32_t pi = pix - eye * P;
+      const uint32_t eye = pix >= FP;
+      const uint32_t pi = pix - eye * FP;  // frame * P + pixel
       uint32_t* hid = eye ? a.hit_R : a.hit_L;
       float* dep = eye ? a.depth_R : a.depth_L;
       if (hid) hid[pi] = id;
-      if (dep) dep[pi] = hit ? t * dot(d, v3(cam.fwd[0], cam.fwd[1], cam.fwd[2])) : INFINITY;
+      if (dep) {
+        const CameraParams& cf = kp.cams[pi / P];
+        dep[pi] = hit ? t * dot(d, v3(cf.fwd[0], cf.fwd[1], cf.fwd[2])) : INFINITY;
+      }
       float* nr = eye ? a.normal_R : a.normal_L;
       if (nr) {                            // zero normal on a miss
         nr[3 * (size_t)pi + 0] = hit ? nrm.x : 0.f;
@@ -496,18 +509,22 @@ int blocks_per_sm() {
 
 template <bool COUNT, bool WIDE>
 cudaError_t render_impl(const RenderArgs& a, Workspace& ws, cudaStream_t st) {
-  const uint64_t P = (uint64_t)a.cam.W * a.cam.H;
+  const uint32_t F = a.n_frames ? a.n_frames : 1u;
+  if (F > (uint32_t)kMaxFrames) return cudaErrorInvalidValue;
+  const uint64_t P = (uint64_t)a.cam.W * a.cam.rows * F;   // pixels per eye over all frames
   KParams kp;
   kp.a = a;
+  kp.n_frames = F;
+  for (uint32_t f = 0; f < F; ++f) kp.cams[f] = a.frames ? a.frames[f] : a.cam;
   kp.accum = ws.accum;
   kp.wq = ws.wq;
   kp.counters = ws.counters;
   kp.cap_s = ws.cap_s;
   kp.cap_r = ws.cap_r;
   kp.pair_eyes = a.eyes == 3u && a.sc.n_prims >= kPairEyesPrims;
-  kp.n_tiles = a.plist ? (a.plist_n + 31u) / 32u
-             : kp.pair_eyes ? ((a.cam.W + 3u) / 4u) * a.cam.tiles_y   // 4x4 pixels, both eyes
-                            : (a.eyes == 3u ? 2u : 1u) * a.cam.tiles_x * a.cam.tiles_y;   // 8x4, one eye
+  kp.tiles_pf = kp.pair_eyes ? ((a.cam.W + 3u) / 4u) * a.cam.tiles_y   // 4x4 pixels, both eyes
+                             : (a.eyes == 3u ? 2u : 1u) * a.cam.tiles_x * a.cam.tiles_y;   // 8x4, one eye
+  kp.n_tiles = a.plist ? (a.plist_n + 31u) / 32u : F * kp.tiles_pf;
   const int grid = render_grid();
   if ((uint64_t)grid * (kThreads / 32) > ws.n_warps) return cudaErrorInvalidValue;
   kp.share_partial = a.sc.n_prims >= kSharePartialPrims;
