@@ -371,23 +371,24 @@ int rt_build_lbvh_noalloc(const rt_sphere* d_spheres, uint32_t n_spheres,
  * pixels that a small network (or a disocclusion) marks. The full right-eye
  * trace stays the reference it is judged against.
  *
- * Network: 3x3 convolutions 9 -> 32 -> 32 -> 32 -> 1, zero padding 1,
+ * Network: 3x3 convolutions 10 -> 32 -> 32 -> 32 -> 1, zero padding 1,
  * ReLU, sigmoid; BF16 operands on the tensor cores, FP32 accumulation,
  * FP32 master weights. Parameters (RT_NET_PARAMS floats) in this order:
- * W1[32][9][3][3], b1[32], W2[32][32][3][3], b2[32], W3[32][32][3][3],
+ * W1[32][10][3][3], b1[32], W2[32][32][3][3], b2[32], W3[32][32][3][3],
  * b3[32], W4[1][32][3][3], b4[1].
- * Features of a right pixel (BF16, 16 channels per pixel, channels 9-15
+ * Features of a right pixel (BF16, 16 channels per pixel, channels 10-15
  * zero; all zero on a hole): min(z/100, 1), the normal (3), hash(hit id) =
- * (fmix32(id) >> 8) * 2^-24 (MurmurHash3 finaliser), the left RGB (3) and
- * the disparity / 16, taken from the left pixel that the forward warp puts
- * there: a left pixel (i, j) at view depth z lands on column
+ * (fmix32(id) >> 8) * 2^-24 (MurmurHash3 finaliser), the left RGB (3), the
+ * disparity / 16 and the reflectivity of the hit surface (mirror pixels
+ * change colour with the viewpoint, so a warp cannot carry them), taken
+ * from the left pixel that the forward warp puts there: a left pixel (i, j) at view depth z lands on column
  * floor(i - D + 0.5) of row j, D = f_px * eye_sep * (1/z - 1/convergence),
  * f_px = (H/2)/tan(vfov/2); the nearest z wins, equal z the lower index.
  * A left pixel whose ray missed is a source at infinity (z = +inf, zero
  * normal, background colour), so only disocclusions and the uncovered
  * border remain holes.
  */
-#define RT_NET_PARAMS 21409
+#define RT_NET_PARAMS 21697
 typedef struct rt_net rt_net;  /* opaque */
 
 /* Upload RT_NET_PARAMS host floats (finite) into a new network; synchronises.
@@ -479,6 +480,17 @@ int rt_net_forward(rt_net* net, const uint16_t* d_feat16, uint32_t W, uint32_t H
                    void* cuda_stream);
 
 /*
+ * rt_net_forward_images -- rt_net_forward of n_img feature maps of W x H
+ * pixels stored one after the other (d_feat16: n_img*W*H*16 BF16; d_prob:
+ * n_img*W*H floats), one launch per layer for all of them. Each image is
+ * convolved on its own (zero padding at its borders), so image i's output
+ * equals rt_net_forward on image i alone bit for bit. The paper has no
+ * network; this serves the multi-frame reprojection below.
+ */
+int rt_net_forward_images(rt_net* net, const uint16_t* d_feat16, uint32_t n_img, uint32_t W,
+                          uint32_t H, float* d_prob, void* cuda_stream);
+
+/*
  * rt_net_train_step -- one step on the mean binary cross-entropy of the
  * network's output against d_label (DEVICE, W*H floats in {0,1}): forward,
  * backward (data gradients on the tensor cores, weight gradients in FP32),
@@ -493,14 +505,19 @@ int rt_net_train_step(rt_net* net, const uint16_t* d_feat16, const float* d_labe
  * rt_reproj_warp -- forward warp of a left G-buffer to the right eye.
  *   inputs (DEVICE, W*H pixels each): d_depth_L view depth (+inf = the ray
  *   missed: a source at infinity; <= 0 or NaN: skipped),
- *   d_normal_L (3 floats), d_id_L (hit id), d_rgb_L (3 floats).
+ *   d_normal_L (3 floats), d_id_L (hit id), d_rgb_L (3 floats),
+ *   d_refl_L (reflectivity of the hit surface, 0 on a miss; may be NULL:
+ *   all 0).
  *   d_zbuf: DEVICE scratch of W*H uint64 (overwritten).
  *   outputs (DEVICE, any may be NULL): d_feat16 (W*H*16 BF16 bits),
- *   d_feat32 (W*H*9 floats, the same features before BF16 rounding),
- *   d_hole (W*H bytes, 1 where no left pixel lands), d_warped (W*H*3 floats).
+ *   d_feat32 (W*H*10 floats, the same features before BF16 rounding),
+ *   d_hole (W*H bytes: 1 where no left pixel lands, 2 where the left pixel
+ *   that lands there hit a reflective surface (reflectivity > 0), else 0),
+ *   d_warped (W*H*3 floats).
  */
 int rt_reproj_warp(const float* d_depth_L, const float* d_normal_L, const uint32_t* d_id_L,
-                   const float* d_rgb_L, uint32_t W, uint32_t H, float f_px, float eye_sep,
+                   const float* d_rgb_L, const float* d_refl_L, uint32_t W, uint32_t H, float f_px,
+                   float eye_sep,
                    float convergence, uint64_t* d_zbuf, uint16_t* d_feat16, float* d_feat32,
                    uint8_t* d_hole, float* d_warped, void* cuda_stream);
 
@@ -519,8 +536,10 @@ int rt_reproj_training_pair(const rt_scene* scene, const rt_camera* cam, float e
 /*
  * rt_render_stereo_reproj -- a stereo pair with the right eye reprojected:
  * traces the left eye (out_L exactly as rt_render_stereo), warps it to the
- * right grid, runs the network (net may be NULL: retrace holes only), traces
- * the right pixels with hole != 0 or p > threshold, and writes out_R = traced
+ * right grid, runs the network (net may be NULL: no network), traces the
+ * right pixels that are holes, that show a reflective surface (a mirror's
+ * colour depends on the viewpoint, so the warp cannot carry it) or whose
+ * retrace probability p exceeds threshold, and writes out_R = traced
  * colour there, warped colour elsewhere. d_n_retraced (DEVICE uint32, may be
  * NULL) receives the number of retraced right pixels. Asynchronous.
  */

@@ -10,9 +10,10 @@ definitions in numpy (and PyTorch CPU float64 for the network):
   target column are evaluated in float32 with the same operations as the
   kernel (one IEEE operation at a time), because they decide an integer.
 * features of a right pixel: min(z/100, 1), normal, hash(id) =
-  (fmix32(id) >> 8) 2^-24 (MurmurHash3 finaliser), left RGB, D/16; zeros on a
-  hole. Labels: hole or max_c |warped - full| > threshold.
-* network: 3x3 convolutions 9 -> 32 -> 32 -> 32 -> 1 with zero padding 1,
+  (fmix32(id) >> 8) 2^-24 (MurmurHash3 finaliser), left RGB, D/16, the
+  reflectivity of the left pixel's surface; zeros on a hole. Labels: hole
+  or max_c |warped - full| > threshold.
+* network: 3x3 convolutions 10 -> 32 -> 32 -> 32 -> 1 with zero padding 1,
   ReLU, sigmoid; mean binary cross-entropy; gradients by autograd in float64.
   `forward(..., bf16=True)` rounds inputs, weights and hidden activations to
   BF16 where the tensor-core kernels do, so the two can be compared closely.
@@ -31,7 +32,16 @@ import numpy as np
 
 Z_FAR = 100.0
 DISP_SCALE = 1.0 / 16.0
-LAYERS = ((9, 32), (32, 32), (32, 32), (32, 1))
+LAYERS = ((10, 32), (32, 32), (32, 32), (32, 1))
+IN_CH = LAYERS[0][0]              # feature channels the network reads
+# offsets of each layer's weights and biases in the parameter vector
+OFF_W, OFF_B = [], []
+_k = 0
+for _ci, _co in LAYERS:
+    OFF_W.append(_k)
+    OFF_B.append(_k + _co * _ci * 9)
+    _k += _co * _ci * 9 + _co
+N_PARAMS = _k
 
 
 def fmix32(h):
@@ -53,9 +63,10 @@ def disparity32(z, f_px, eye_sep, convergence):
         return fs * (f32(1.0) / np.asarray(z, np.float32) - inv_zc)
 
 
-def warp(depth, normal, ids, rgb, W, H, f_px, eye_sep, convergence):
-    """Returns features (P, 9) float64, hole (P,) bool, warped RGB (P, 3),
-    source index (P,) int64 (-1 on a hole)."""
+def warp(depth, normal, ids, rgb, W, H, f_px, eye_sep, convergence, refl=None):
+    """Returns features (P, 10) float64, hole (P,) bool, warped RGB (P, 3),
+    source index (P,) int64 (-1 on a hole). refl: reflectivity of each left
+    pixel's surface (None: zeros)."""
     P = W * H
     z = np.asarray(depth, np.float32).reshape(P)
     with np.errstate(invalid="ignore"):
@@ -76,7 +87,7 @@ def warp(depth, normal, ids, rgb, W, H, f_px, eye_sep, convergence):
     source[tgt_s[first]] = src_s[first]
     hole = source < 0
     q = np.where(hole, 0, source)
-    feat = np.zeros((P, 9), np.float64)
+    feat = np.zeros((P, IN_CH), np.float64)
     zq = z[q].astype(np.float64)
     with np.errstate(invalid="ignore"):
         feat[:, 0] = np.minimum(zq / Z_FAR, 1.0)
@@ -84,6 +95,8 @@ def warp(depth, normal, ids, rgb, W, H, f_px, eye_sep, convergence):
     feat[:, 4] = (fmix32(np.asarray(ids).reshape(P)[q]) >> np.uint32(8)).astype(np.float64) * 2.0 ** -24
     feat[:, 5:8] = np.asarray(rgb, np.float64).reshape(P, 3)[q]
     feat[:, 8] = D[q].astype(np.float64) * DISP_SCALE
+    if refl is not None:
+        feat[:, 9] = np.asarray(refl, np.float32).reshape(P)[q].astype(np.float64)
     feat[hole] = 0.0
     return feat, hole, feat[:, 5:8].copy(), source
 
@@ -113,10 +126,10 @@ def _bf16(t):
 
 
 def forward(params, feat, W, H, bf16=True):
-    """Retrace probability (H, W) of features (P, >=9), float64."""
+    """Retrace probability (H, W) of features (P, >= IN_CH), float64."""
     import torch
     import torch.nn.functional as F
-    x = torch.tensor(np.asarray(feat, np.float64)[:, :9].reshape(H, W, 9)).permute(2, 0, 1)[None]
+    x = torch.tensor(np.asarray(feat, np.float64)[:, :IN_CH].reshape(H, W, IN_CH)).permute(2, 0, 1)[None]
     if bf16:
         x = _bf16(x)
     layers = unpack(params)
@@ -169,7 +182,7 @@ def forward_fp8(params, feat, W, H, act_scales):
     act_scales: scales of the three hidden activations (layer 1-3 outputs)."""
     import torch
     import torch.nn.functional as F
-    x = torch.tensor(np.asarray(feat, np.float64)[:, :9].reshape(H, W, 9)).permute(2, 0, 1)[None]
+    x = torch.tensor(np.asarray(feat, np.float64)[:, :IN_CH].reshape(H, W, IN_CH)).permute(2, 0, 1)[None]
     x = _bf16(x)
     layers = unpack(params)
     wsc = weight_scales_fp8(params)
@@ -193,7 +206,7 @@ def loss_and_grads(params, feat, label, W, H):
     import torch
     import torch.nn.functional as F
     p = torch.tensor(np.asarray(params, np.float64).reshape(-1), requires_grad=True)
-    x = torch.tensor(np.asarray(feat, np.float64)[:, :9].reshape(H, W, 9)).permute(2, 0, 1)[None]
+    x = torch.tensor(np.asarray(feat, np.float64)[:, :IN_CH].reshape(H, W, IN_CH)).permute(2, 0, 1)[None]
     k = 0
     for li, (ci, co) in enumerate(LAYERS):
         w = p[k:k + co * ci * 9].reshape(co, ci, 3, 3)
@@ -222,7 +235,7 @@ def grads_emulated(params, feat, label, W, H, bf16=True):
     rb = _bf16 if bf16 else (lambda t: t)
     P = W * H
     layers = [(torch.tensor(w), torch.tensor(b)) for w, b in unpack(params)]
-    a = [rb(torch.tensor(np.asarray(feat, np.float64)[:, :9].reshape(H, W, 9)).permute(2, 0, 1)[None])]
+    a = [rb(torch.tensor(np.asarray(feat, np.float64)[:, :IN_CH].reshape(H, W, IN_CH)).permute(2, 0, 1)[None])]
     for li in range(3):
         w, b = layers[li]
         a.append(rb(torch.relu(F.conv2d(a[-1], rb(w), b, padding=1))))

@@ -71,13 +71,14 @@ _SIGS = {
     "rt_net_status": (ctypes.c_int, [_vp, _vp]),
     "rt_net_forward": (ctypes.c_int, [_vp, _vp, _u32, _u32, _vp, _vp]),
     "rt_net_set_fp8": (ctypes.c_int, [_vp, _vp]),
+    "rt_net_forward_images": (ctypes.c_int, [_vp, _vp, _u32, _u32, _u32, _vp, _vp]),
     "rt_net_activation_amax": (ctypes.c_int, [_vp, _vp, _u32, _u32, _vp, _vp]),
     "rt_net_calibrate_fp8": (ctypes.c_int, [_vp, _vp, _u32, _u32, _u32, _vp, _vp, _vp]),
     "rt_net_save": (ctypes.c_int, [_vp, ctypes.c_char_p]),
     "rt_net_load": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(_vp)]),
     "rt_net_train_step": (ctypes.c_int, [_vp, _vp, _vp, _u32, _u32, _f32, _vp, _vp, _vp]),
-    "rt_reproj_warp": (ctypes.c_int, [_vp, _vp, _vp, _vp, _u32, _u32, _f32, _f32, _f32, _vp, _vp,
-                                      _vp, _vp, _vp, _vp]),
+    "rt_reproj_warp": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _u32, _u32, _f32, _f32, _f32, _vp,
+                                      _vp, _vp, _vp, _vp, _vp]),
     "rt_reproj_training_pair": (ctypes.c_int, [_vp, _vp, _f32, _f32, _u32, _u32, _u32, _vp, _vp,
                                                _vp, _vp, _f32, _vp]),
     "rt_render_stereo_reproj": (ctypes.c_int, [_vp, _vp, _f32, _f32, _u32, _u32, _u32, _vp, _f32,
@@ -420,7 +421,7 @@ def rt_stereo_composite(L, R, W, H, mode, out, stream=None):
     _check(lib().rt_stereo_composite(_dptr(L), _dptr(R), W, H, mode, _dptr(out), _stream(stream)))
 
 
-RT_NET_PARAMS = 21409
+RT_NET_PARAMS = 21697
 
 
 def rt_net_create(params) -> int:
@@ -446,6 +447,10 @@ def rt_net_status(net, stream=None):
 
 def rt_net_forward(net, feat16, W, H, prob, stream=None):
     _check(lib().rt_net_forward(net, _dptr(feat16), W, H, _dptr(prob), _stream(stream)))
+
+
+def rt_net_forward_images(net, feat16, n_img, W, H, prob, stream=None):
+    _check(lib().rt_net_forward_images(net, _dptr(feat16), n_img, W, H, _dptr(prob), _stream(stream)))
 
 
 def rt_net_set_fp8(net, act_scales):
@@ -494,8 +499,9 @@ def rt_net_train_step(net, feat16, label, W, H, lr, want_loss=True, grads=None, 
 
 
 def rt_reproj_warp(depth_L, normal_L, id_L, rgb_L, W, H, f_px, eye_sep, convergence, zbuf,
-                   feat16=None, feat32=None, hole=None, warped=None, stream=None):
-    _check(lib().rt_reproj_warp(_dptr(depth_L), _dptr(normal_L), _dptr(id_L), _dptr(rgb_L), W, H,
+                   feat16=None, feat32=None, hole=None, warped=None, stream=None, refl_L=None):
+    _check(lib().rt_reproj_warp(_dptr(depth_L), _dptr(normal_L), _dptr(id_L), _dptr(rgb_L),
+                                _dptr(refl_L), W, H,
                                 f_px, eye_sep, convergence, _dptr(zbuf), _dptr(feat16),
                                 _dptr(feat32), _dptr(hole), _dptr(warped), _stream(stream)))
 

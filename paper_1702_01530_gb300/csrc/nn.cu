@@ -71,7 +71,16 @@ constexpr int kEpiWarps = 4 * RT_CONV_EPI_WG;
 constexpr int kConvTmaThreads = 32 * (kEpiWarps + 1);
 constexpr int kRows = RT_CONV_ROWS;
 constexpr int kTileM = 128;          // pixels per row tile (one MMA M block)
-constexpr int kHaloW = kTileM + 2;   // 130
+// RT_CONV_SKEW = pixels by which the halo of every odd 16-byte channel chunk
+// starts earlier than that of the even chunks: the two core matrices of one
+// MMA's K step (an even and an odd chunk of the same pixels) then sit
+// RT_CONV_SKEW * 16 bytes apart modulo 128 instead of on the same shared-
+// memory banks (the chunk planes are 128-byte aligned for TMA).
+#ifndef RT_CONV_SKEW
+#define RT_CONV_SKEW 0
+#endif
+constexpr int kSkew = RT_CONV_SKEW;
+constexpr int kHaloW = kTileM + 2 + kSkew;   // halo pixels per row (130 without skew)
 constexpr int kHaloRows = (kRows + 2) * kHaloW;  // halo pixels per tile
 constexpr uint32_t kWaitBound = 1u << 26;
 
@@ -239,7 +248,8 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
 template <int kChunks, int COUT, uint32_t kPlaneBytes, bool FP8>
 __device__ __forceinline__ void issue_tile_mmas(uint32_t hbase, uint32_t wbase, uint32_t dtmem,
                                                 uint32_t idesc) {
-  const uint32_t a_lo = desc_lo(hbase, kPlaneBytes), b_lo = desc_lo(wbase, COUT * 16);
+  // LBO = the distance from an even chunk's core matrix to the odd one's
+  const uint32_t a_lo = desc_lo(hbase, kPlaneBytes + 16u * kSkew), b_lo = desc_lo(wbase, COUT * 16);
   constexpr uint32_t hi = desc_hi(128u);
 #pragma unroll
   for (int ry = 0; ry < kRows; ++ry) {
@@ -375,11 +385,11 @@ __global__ void __launch_bounds__(kConvTmaThreads, 1)
 #pragma unroll
         for (int c = 0; c < Lt::kChunks; ++c)
           if (PLANAR_IN)   // tensor {16 B of channels, W, H, images, chunks}
-            tma_load_5d(halo0 + (size_t)b * Lt::kHalo + (size_t)c * Lt::kPlane, &tmap, 0, x0 - 1,
-                        y - 1, img, c, halo_full + b);
+            tma_load_5d(halo0 + (size_t)b * Lt::kHalo + (size_t)c * Lt::kPlane, &tmap, 0,
+                        x0 - 1 - ((c & 1) ? kSkew : 0), y - 1, img, c, halo_full + b);
           else             // tensor {16 B of channels, chunks, W, H, images}
-            tma_load_5d(halo0 + (size_t)b * Lt::kHalo + (size_t)c * Lt::kPlane, &tmap, 0, c, x0 - 1,
-                        y - 1, img, halo_full + b);
+            tma_load_5d(halo0 + (size_t)b * Lt::kHalo + (size_t)c * Lt::kPlane, &tmap, 0, c,
+                        x0 - 1 - ((c & 1) ? kSkew : 0), y - 1, img, halo_full + b);
         issued_halo[b] = true;
         halo_par[b] = (j / kStages) & 1u;
       };
@@ -834,10 +844,10 @@ cudaError_t launch_conv(const void* in, const void* wpk, const float* bias, cons
 void set_conv_smem_pad(int bytes) { g_conv_smem_pad = bytes; }
 
 // parameter offsets (canonical layout W[Cout][Cin][3][3], b[Cout] per layer)
-constexpr uint32_t kOffW[4] = {0, 2624, 11872, 21120};
-constexpr uint32_t kOffB[4] = {2592, 11840, 21088, 21408};
+constexpr uint32_t kOffW[4] = {0, 2912, 12160, 21408};
+constexpr uint32_t kOffB[4] = {2880, 12128, 21376, 21696};
 constexpr int kCout[4] = {32, 32, 32, 1};
-constexpr int kCin[4] = {9, 32, 32, 32};
+constexpr int kCin[4] = {10, 32, 32, 32};
 constexpr int kCinPad[4] = {16, 32, 32, 32};
 constexpr int kCoutPad[4] = {32, 32, 32, 16};
 
@@ -945,7 +955,7 @@ cudaError_t backward(const __nv_bfloat16* feat16, const float* label, __nv_bfloa
                                              W, H, err, st);
   if (e != cudaSuccess) return e;
   // layer 1 (no data gradient for the input features)
-  k_wgrad<16, 32><<<rows_grid, 256, 0, st>>>(feat16, 9, dz_a, nullptr, W, H, wpart);
+  k_wgrad<16, 32><<<rows_grid, 256, 0, st>>>(feat16, kCin[0], dz_a, nullptr, W, H, wpart);
   reduce(0);
   return cudaGetLastError();
 }

@@ -19,9 +19,12 @@
 // The disparity and the target column use explicitly rounded FP32
 // operations (no contraction) so the decision is reproducible bit for bit.
 //
-// Features of a right pixel (9 channels, zeros on a hole):
+// Features of a right pixel (10 channels, zeros on a hole):
 //   min(z/100, 1), normal (3), hash(id) = (fmix32(id) >> 8) * 2^-24 with
-//   MurmurHash3's 32-bit finaliser, left RGB (3), D/16.
+//   MurmurHash3's 32-bit finaliser, left RGB (3), D/16, and the reflectivity
+//   of the surface the left pixel hit: a mirror's colour depends on the
+//   viewpoint, so warped mirror pixels are wrong however exact the warp, and
+//   without this channel the network cannot see which pixels are mirrors.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -33,6 +36,7 @@ namespace {
 
 constexpr float kZFar = 100.f;
 constexpr float kDispScale = 1.f / 16.f;
+constexpr int kFeat = 10;          // feature channels (of the 16 stored per pixel)
 
 __device__ __forceinline__ uint32_t fmix32(uint32_t h) {
   h ^= h >> 16;
@@ -72,11 +76,12 @@ __global__ void k_warp_scatter(const float* __restrict__ depth_L, uint32_t W, ui
 __global__ void k_warp_gather(const unsigned long long* __restrict__ zbuf,
                               const float* __restrict__ depth_L, const float* __restrict__ normal_L,
                               const uint32_t* __restrict__ id_L, const float* __restrict__ rgb_L,
-                              uint32_t P, float fs, float inv_zc, __nv_bfloat16* feat16,
+                              const float* __restrict__ refl_L, uint32_t P, float fs, float inv_zc,
+                              __nv_bfloat16* feat16,
                               float* feat32, uint8_t* hole, float* warped) {
   for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
     const unsigned long long key = zbuf[p];
-    float f[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    float f[kFeat] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     const bool h = key == ~0ull;
     if (!h) {
       const uint32_t q = (uint32_t)(key & 0xFFFFFFFFull);
@@ -90,12 +95,13 @@ __global__ void k_warp_gather(const unsigned long long* __restrict__ zbuf,
       f[6] = rgb_L[3 * (size_t)q + 1];
       f[7] = rgb_L[3 * (size_t)q + 2];
       f[8] = disparity(z, fs, inv_zc) * kDispScale;
+      f[9] = refl_L ? refl_L[q] : 0.f;
     }
     if (feat16) {                          // 32 bytes per pixel as two 16-byte stores
       uint32_t w[8];
 #pragma unroll
       for (int c = 0; c < 8; ++c) {
-        const float lo = 2 * c < 9 ? f[2 * c] : 0.f, hi = 2 * c + 1 < 9 ? f[2 * c + 1] : 0.f;
+        const float lo = 2 * c < kFeat ? f[2 * c] : 0.f, hi = 2 * c + 1 < kFeat ? f[2 * c + 1] : 0.f;
         __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
         w[c] = *reinterpret_cast<uint32_t*>(&h);
       }
@@ -105,9 +111,12 @@ __global__ void k_warp_gather(const unsigned long long* __restrict__ zbuf,
     }
     if (feat32) {
 #pragma unroll
-      for (int c = 0; c < 9; ++c) feat32[9 * (size_t)p + c] = f[c];
+      for (int c = 0; c < kFeat; ++c) feat32[kFeat * (size_t)p + c] = f[c];
     }
-    if (hole) hole[p] = h ? 1 : 0;
+    // 1: a hole; 2: the source surface reflects (its colour depends on the
+    // viewpoint, so the warped colour is not the right eye's); the retrace
+    // mask takes both, the training labels only the holes
+    if (hole) hole[p] = h ? 1 : (f[9] > 0.f ? 2 : 0);
     if (warped) {
       warped[3 * (size_t)p + 0] = f[5];
       warped[3 * (size_t)p + 1] = f[6];
@@ -123,12 +132,13 @@ __global__ void k_labels(const uint8_t* __restrict__ hole, const float* __restri
     float e = 0.f;
 #pragma unroll
     for (int c = 0; c < 3; ++c) e = fmaxf(e, fabsf(warped[3 * (size_t)p + c] - full_R[3 * (size_t)p + c]));
-    label[p] = (hole[p] || e > thr) ? 1.f : 0.f;
+    label[p] = (hole[p] == 1 || e > thr) ? 1.f : 0.f;
   }
 }
 
-// mask = hole or prob > threshold; the masked right pixels (as global
-// indices P + p) are appended to plist with warp-aggregated atomics
+// mask = hole, reflective source, or prob > threshold; the masked right
+// pixels (as global indices P + p) are appended to plist with warp-aggregated
+// atomics
 __global__ void k_mask_compact(const uint8_t* __restrict__ hole, const float* __restrict__ prob,
                                uint32_t P, float threshold, uint8_t* mask, uint32_t* plist,
                                uint32_t* count) {
@@ -166,7 +176,7 @@ int grid_1d(uint64_t n, int threads) {
 }  // namespace
 
 cudaError_t reproj_warp(const float* depth_L, const float* normal_L, const uint32_t* id_L,
-                        const float* rgb_L, uint32_t W, uint32_t H, float f_px, float eye_sep,
+                        const float* rgb_L, const float* refl_L, uint32_t W, uint32_t H, float f_px, float eye_sep,
                         float convergence, unsigned long long* zbuf, __nv_bfloat16* feat16,
                         float* feat32, uint8_t* hole, float* warped, cudaStream_t st) {
   const uint32_t P = W * H;
@@ -174,7 +184,7 @@ cudaError_t reproj_warp(const float* depth_L, const float* normal_L, const uint3
   const float inv_zc = 1.f / convergence;
   k_warp_clear<<<grid_1d(P, 256), 256, 0, st>>>(zbuf, P);
   k_warp_scatter<<<grid_1d(P, 256), 256, 0, st>>>(depth_L, W, H, fs, inv_zc, zbuf);
-  k_warp_gather<<<grid_1d(P, 256), 256, 0, st>>>(zbuf, depth_L, normal_L, id_L, rgb_L, P, fs,
+  k_warp_gather<<<grid_1d(P, 256), 256, 0, st>>>(zbuf, depth_L, normal_L, id_L, rgb_L, refl_L, P, fs,
                                                   inv_zc, feat16, feat32, hole, warped);
   return cudaGetLastError();
 }

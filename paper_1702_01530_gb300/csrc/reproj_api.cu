@@ -91,7 +91,7 @@ int reproj_buffers(const rt_scene* sc_c, uint64_t P) {
   if (rp.base && rp.cap >= P) return RT_OK;
   const size_t b4 = a256(P * 4), b12 = a256(P * 12), b8 = a256(P * 8), b1 = a256(P),
                bf = a256(P * 16 * 2), bact = a256(P * 32 * 2);
-  const size_t total = b4 + b12 + b4 + b8 + bf + b1 + b12 + b1 + b4 + 256 + b4 + 3 * bact;
+  const size_t total = b4 + b12 + b4 + b4 + b8 + bf + b1 + b12 + b1 + b4 + 256 + b4 + 3 * bact;
   void* base = nullptr;
   cudaError_t e = cudaMalloc(&base, total);
   if (e != cudaSuccess) { cudaGetLastError(); return cuda_fail(e, "reprojection buffers"); }
@@ -101,6 +101,7 @@ int reproj_buffers(const rt_scene* sc_c, uint64_t P) {
   rp.cap = P;
   rp.depth_L = reinterpret_cast<float*>(p); p += b4;
   rp.normal_L = reinterpret_cast<float*>(p); p += b12;
+  rp.refl_L = reinterpret_cast<float*>(p); p += b4;
   rp.id_L = reinterpret_cast<uint32_t*>(p); p += b4;
   rp.zbuf = reinterpret_cast<unsigned long long*>(p); p += b8;
   rp.feat16 = reinterpret_cast<__nv_bfloat16*>(p); p += bf;
@@ -240,8 +241,8 @@ int rt_net_set_fp8(rt_net* net, const float* act_scales) {
   if (e != cudaSuccess) return cuda_fail(e, "rt_net_set_fp8: parameter download");
   // per output channel of layers 2-4: the largest power of two s with
   // max |w| * s <= 448 (1 for an all-zero channel); inverse scale 1/(a s)
-  static const uint32_t off_w[4] = {0, 2624, 11872, 21120};
-  static const int cout[4] = {32, 32, 32, 1}, cin[4] = {9, 32, 32, 32};
+  static const uint32_t off_w[4] = {0, 2912, 12160, 21408};
+  static const int cout[4] = {32, 32, 32, 1}, cin[4] = {10, 32, 32, 32};
   for (int l = 1; l < 4; ++l) {
     float sc[32], iv[32];
     for (int co = 0; co < 32; ++co) {
@@ -398,6 +399,18 @@ int rt_net_forward(rt_net* net, const uint16_t* d_feat16, uint32_t W, uint32_t H
   return RT_OK;
 }
 
+int rt_net_forward_images(rt_net* net, const uint16_t* d_feat16, uint32_t n_img, uint32_t W, uint32_t H,
+                          float* d_prob, void* cuda_stream) {
+  if (!net || !d_feat16 || !d_prob || n_img < 1 || W < 1 || H < 1) return fail(RT_ERR_INVALID_ARG, "bad argument");
+  if ((uint64_t)W * H * n_img > (1ull << 30)) return fail(RT_ERR_INVALID_ARG, "images too large");
+  int rc = net_buffers(net, (uint64_t)W * H * n_img);
+  if (rc) return rc;
+  cudaError_t e = net_forward(net, reinterpret_cast<const __nv_bfloat16*>(d_feat16), net->act, d_prob,
+                              W, H, static_cast<cudaStream_t>(cuda_stream), n_img);
+  if (e != cudaSuccess) return cuda_fail(e, "network forward (images)");
+  return RT_OK;
+}
+
 int rt_net_train_step(rt_net* net, const uint16_t* d_feat16, const float* d_label, uint32_t W,
                       uint32_t H, float lr, float* host_loss, float* d_grads, void* cuda_stream) {
   if (!net || !d_feat16 || !d_label || W < 1 || H < 1 || !(lr >= 0.f) || !std::isfinite(lr))
@@ -432,7 +445,7 @@ int rt_net_train_step(rt_net* net, const uint16_t* d_feat16, const float* d_labe
 }
 
 int rt_reproj_warp(const float* d_depth_L, const float* d_normal_L, const uint32_t* d_id_L,
-                   const float* d_rgb_L, uint32_t W, uint32_t H, float f_px, float eye_sep,
+                   const float* d_rgb_L, const float* d_refl_L, uint32_t W, uint32_t H, float f_px, float eye_sep,
                    float convergence, uint64_t* d_zbuf, uint16_t* d_feat16, float* d_feat32,
                    uint8_t* d_hole, float* d_warped, void* cuda_stream) {
   if (!d_depth_L || !d_normal_L || !d_id_L || !d_rgb_L || !d_zbuf || W < 1 || H < 1)
@@ -441,7 +454,7 @@ int rt_reproj_warp(const float* d_depth_L, const float* d_normal_L, const uint32
   if (!(f_px > 0.f) || !(eye_sep >= 0.f) || !(convergence > 0.f) || !std::isfinite(f_px) ||
       !std::isfinite(eye_sep) || !std::isfinite(convergence))
     return fail(RT_ERR_INVALID_ARG, "f_px, eye_sep, convergence out of range");
-  cudaError_t e = rt::reproj_warp(d_depth_L, d_normal_L, d_id_L, d_rgb_L, W, H, f_px, eye_sep,
+  cudaError_t e = rt::reproj_warp(d_depth_L, d_normal_L, d_id_L, d_rgb_L, d_refl_L, W, H, f_px, eye_sep,
                                   convergence, reinterpret_cast<unsigned long long*>(d_zbuf),
                                   reinterpret_cast<__nv_bfloat16*>(d_feat16), d_feat32, d_hole,
                                   d_warped, static_cast<cudaStream_t>(cuda_stream));
@@ -464,12 +477,12 @@ int rt_reproj_training_pair(const rt_scene* scene, const rt_camera* cam, float e
   if (rc) return rc;
   rt::ReprojBuffers& rp = const_cast<rt_scene*>(scene)->ws.rp;
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
-  a.out_L = d_out_L; a.out_R = d_out_R;
-  a.hit_L = rp.id_L; a.depth_L = rp.depth_L; a.normal_L = rp.normal_L;
+  a.out_L = d_out_L; a.out_R = d_out_R;   // both eyes in full: the labels compare with the right
+  a.hit_L = rp.id_L; a.depth_L = rp.depth_L; a.normal_L = rp.normal_L; a.refl_L = rp.refl_L;
   rt::profile_begin(const_cast<rt_scene*>(scene)->ws, st);
   cudaError_t e = rt::render(a, const_cast<rt_scene*>(scene)->ws, st);
   if (e == cudaSuccess)
-    e = rt::reproj_warp(rp.depth_L, rp.normal_L, rp.id_L, d_out_L, W, H, focal_px(cam, H), eye_sep,
+    e = rt::reproj_warp(rp.depth_L, rp.normal_L, rp.id_L, d_out_L, rp.refl_L, W, H, focal_px(cam, H), eye_sep,
                         convergence, rp.zbuf, reinterpret_cast<__nv_bfloat16*>(d_feat16), nullptr,
                         rp.hole, rp.warped, st);
   if (e == cudaSuccess) e = rt::reproj_labels(rp.hole, rp.warped, d_out_R, (uint32_t)P, label_threshold, d_label, st);
@@ -496,12 +509,12 @@ int rt_render_stereo_reproj(const rt_scene* scene, const rt_camera* cam, float e
   // 1. left eye with its G-buffer
   rt::profile_begin(sc->ws, st);
   a.eyes = 1u;
-  a.out_L = d_out_L; a.out_R = d_out_R;
-  a.hit_L = rp.id_L; a.depth_L = rp.depth_L; a.normal_L = rp.normal_L;
+  a.out_L = d_out_L; a.out_R = nullptr;   // the left pass resolves the left eye only
+  a.hit_L = rp.id_L; a.depth_L = rp.depth_L; a.normal_L = rp.normal_L; a.refl_L = rp.refl_L;
   cudaError_t e = rt::render(a, sc->ws, st);
   // 2. forward warp to the right grid, network features
   if (e == cudaSuccess)
-    e = rt::reproj_warp(rp.depth_L, rp.normal_L, rp.id_L, d_out_L, W, H, focal_px(cam, H), eye_sep,
+    e = rt::reproj_warp(rp.depth_L, rp.normal_L, rp.id_L, d_out_L, rp.refl_L, W, H, focal_px(cam, H), eye_sep,
                         convergence, rp.zbuf, net ? rp.feat16 : nullptr, nullptr, rp.hole,
                         rp.warped, st);
   rt::profile_mark(sc->ws, rt::ST_WARP, st);
@@ -510,7 +523,7 @@ int rt_render_stereo_reproj(const rt_scene* scene, const rt_camera* cam, float e
     e = net_forward(net, rp.feat16, rp.act, rp.prob, W, H, st);
     rt::profile_mark(sc->ws, rt::ST_NET, st);
   }
-  // 4. mask = hole or p > threshold, compacted
+  // 4. mask = hole, reflective source, or p > threshold, compacted
   if (e == cudaSuccess)
     e = rt::reproj_mask(rp.hole, net ? rp.prob : nullptr, (uint32_t)P, threshold, rp.mask, rp.plist,
                         rp.count, st);
@@ -519,7 +532,7 @@ int rt_render_stereo_reproj(const rt_scene* scene, const rt_camera* cam, float e
   if (e == cudaSuccess) {
     rt::RenderArgs b = a;
     b.eyes = 2u;
-    b.hit_L = nullptr; b.depth_L = nullptr; b.normal_L = nullptr;
+    b.hit_L = nullptr; b.depth_L = nullptr; b.normal_L = nullptr; b.refl_L = nullptr;
     b.plist = rp.plist;
     b.plist_n = 0;
     b.plist_n_dev = rp.count;
@@ -574,13 +587,13 @@ int rt_render_stereo_reproj_frames(const rt_scene* scene, const rt_camera* cams,
   // 1. left eyes of all frames, one launch, with their G-buffers
   rt::profile_begin(sc->ws, st);
   a.eyes = 1u;
-  a.out_L = d_out_L; a.out_R = d_out_R;
-  a.hit_L = rp.id_L; a.depth_L = rp.depth_L; a.normal_L = rp.normal_L;
+  a.out_L = d_out_L; a.out_R = nullptr;   // the left pass resolves the left eye only
+  a.hit_L = rp.id_L; a.depth_L = rp.depth_L; a.normal_L = rp.normal_L; a.refl_L = rp.refl_L;
   cudaError_t e = rt::render(a, sc->ws, st);
   // 2. forward warp: it moves pixels along their row only, so the frames,
   //    stacked as one image of n_frames * H rows, warp in one pass
   if (e == cudaSuccess)
-    e = rt::reproj_warp(rp.depth_L, rp.normal_L, rp.id_L, d_out_L, W, H * n_frames, focal_px(&cams[0], H),
+    e = rt::reproj_warp(rp.depth_L, rp.normal_L, rp.id_L, d_out_L, rp.refl_L, W, H * n_frames, focal_px(&cams[0], H),
                         eye_sep, convergence, rp.zbuf, net ? rp.feat16 : nullptr, nullptr, rp.hole,
                         rp.warped, st);
   rt::profile_mark(sc->ws, rt::ST_WARP, st);
@@ -599,7 +612,7 @@ int rt_render_stereo_reproj_frames(const rt_scene* scene, const rt_camera* cams,
   if (e == cudaSuccess) {
     rt::RenderArgs b = a;
     b.eyes = 2u;
-    b.hit_L = nullptr; b.depth_L = nullptr; b.normal_L = nullptr;
+    b.hit_L = nullptr; b.depth_L = nullptr; b.normal_L = nullptr; b.refl_L = nullptr;
     b.plist = rp.plist;
     b.plist_n = 0;
     b.plist_n_dev = rp.count;

@@ -141,6 +141,8 @@ int make_render_args(const rt_scene* scene, const rt_camera* cam, float eye_sep,
   }
   a.cam.tan_y = (float)ty;
   a.cam.tan_x = (float)(ty * (double)W / (double)H);
+  a.cam.sx = (float)(2.0 * ty / (double)H);      // 2 tan_x / W = 2 tan_y / H
+  a.cam.sy = (float)(2.0 * ty / (double)H);
   a.cam.zc = convergence;
   a.cam.half_sep = 0.5f * eye_sep;
   a.cam.W = W;
@@ -156,7 +158,7 @@ int make_render_args(const rt_scene* scene, const rt_camera* cam, float eye_sep,
   a.sc.nodes4 = scene->nodes4;
   a.sc.n4 = scene->n4;
   a.sc.n_top = scene->n_top;
-  a.binary = scene->tree != RT_TREE_WIDE;
+  a.tree = scene->tree == RT_TREE_WIDE ? rt::kTreeWide4 : rt::kTreeBinary;
   a.sc.prims = scene->prims;
   a.sc.mats = scene->mats;
   a.sc.lights = scene->lights;
@@ -320,6 +322,7 @@ int rt_render_stereo_aux(const rt_scene* scene, const rt_camera* cam, float eye_
   a.depth_L = depth_L; a.depth_R = depth_R;
   a.ray_counts = ray_counts;
   a.work = work;
+  if (work) a.tree = rt::kTreeBinary;   // the instrumented walk is binary
   rt::Workspace& ws = const_cast<rt_scene*>(scene)->ws;
   rt::profile_begin(ws, static_cast<cudaStream_t>(cuda_stream));
   cudaError_t e = rt::render(a, ws, static_cast<cudaStream_t>(cuda_stream));

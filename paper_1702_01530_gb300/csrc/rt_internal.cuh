@@ -33,6 +33,9 @@ enum : uint32_t {
   ERR_BUILD = 16u,     // BVH refit did not reach the root
 };
 
+// the tree a render walks
+constexpr int kTreeBinary = 0, kTreeWide4 = 1;
+
 constexpr int kStackSize = 64;   // >= the depth of the LBVH (64-bit keys) and of the SAH tree (60)
 constexpr int32_t kEmptyChild = 0x7FFFFFFF;  // unused slot of a 4-wide node
 constexpr float kAmbient = 0.1f;
@@ -52,6 +55,7 @@ struct DeviceScene {
 struct CameraParams {
   float eye[3], right[3], up[3], fwd[3];
   float tan_x, tan_y, zc, half_sep;
+  float sx, sy;                // 2 tan_x / W and 2 tan_y / H (pixel step in window units)
   uint32_t W, H;              // the whole image (it fixes the rays)
   uint32_t tiles_x, tiles_y;  // 8x4-pixel tiles per eye (of the traced rows)
   uint32_t y0, rows;          // the rows traced: y0 .. y0 + rows - 1 (0 and H for a whole image)
@@ -77,6 +81,7 @@ struct ReprojBuffers {
   uint64_t cap = 0;              // pixels per eye the buffers hold
   float* depth_L = nullptr;      // left G-buffer: view depth, normal (3), hit id
   float* normal_L = nullptr;
+  float* refl_L = nullptr;       // reflectivity of the left primary hit (0 on a miss)
   uint32_t* id_L = nullptr;
   unsigned long long* zbuf = nullptr;  // forward-warp z-test keys
   __nv_bfloat16* feat16 = nullptr;     // network input, 16 channels
@@ -150,6 +155,7 @@ struct RenderArgs {
   float* depth_L;
   float* depth_R;
   float* normal_L;         // G-buffer: primary-hit normal (facing the ray), 3 floats/pixel
+  float* refl_L;           // G-buffer: reflectivity of the left primary hit (0 on a miss)
   float* normal_R;
   uint64_t* ray_counts;
   uint64_t* work;          // non-null => instrumented traversal
@@ -160,7 +166,7 @@ struct RenderArgs {
   const uint32_t* plist_n_dev;  // its length in device memory (read by the kernel)
   bool resolve;            // write out_L/out_R from the sums (false: caller composes)
   int trace_stage;         // stage the tracing kernel is timed as (ST_TRACE or ST_RETRACE)
-  bool binary;             // traverse the binary tree instead of the 4-wide one
+  int tree;                // kTreeBinary (sc.nodes) or kTreeWide4 (sc.nodes4)
   // several frames in one launch (0 or 1: just cam): n_frames cameras of the
   // same image size in host memory (frames[0] is cam); pixel ids, sums,
   // images and G-buffers then run over all frames, eye-major:
@@ -196,7 +202,7 @@ int treelet_depth();    // 4-wide levels numbered first for shared-memory stagin
 
 // reprojection (reproj.cu)
 cudaError_t reproj_warp(const float* depth_L, const float* normal_L, const uint32_t* id_L,
-                        const float* rgb_L, uint32_t W, uint32_t H, float f_px, float eye_sep,
+                        const float* rgb_L, const float* refl_L, uint32_t W, uint32_t H, float f_px, float eye_sep,
                         float convergence, unsigned long long* zbuf, __nv_bfloat16* feat16,
                         float* feat32, uint8_t* hole, float* warped, cudaStream_t st);
 cudaError_t reproj_labels(const uint8_t* hole, const float* warped, const float* full_R, uint32_t P,
@@ -208,7 +214,7 @@ cudaError_t reproj_compose(const uint8_t* mask, const uint32_t* accum_R, const f
 
 // retrace network (nn.cu)
 namespace nn {
-constexpr uint32_t kParams = 21409;
+constexpr uint32_t kParams = 21697;
 void set_conv_smem_pad(int bytes);
 size_t packed_fwd_elems(int l);
 size_t packed_bwd_elems(int l);

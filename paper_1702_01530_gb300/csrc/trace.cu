@@ -163,7 +163,7 @@ enum Mode : int { M_SHADOW = 0, M_PRIMARY = 1, M_MIRROR = 2 };
 
 // Shadow queue entry: (origin | pixel) (direction | t_max) (contribution | 0)
 // Mirror queue entry: (origin | pixel) (direction | depth) (weight | 0)
-template <bool COUNT, bool WIDE>
+template <bool COUNT, int TREE>
 __global__ void
 #if RT_MIN_BLOCKS > 0
 __launch_bounds__(kThreads, RT_MIN_BLOCKS)
@@ -174,7 +174,7 @@ k_render(KParams kp) {
   const RenderArgs& a = kp.a;
   // the top of the 4-wide tree, staged in shared memory once per block
   extern __shared__ float4 top[];
-  if (WIDE && !COUNT) {
+  if (TREE == kTreeWide4 && !COUNT) {
     for (uint32_t i = threadIdx.x; i < 7u * a.sc.n_top; i += blockDim.x) top[i] = a.sc.nodes4[i];
     __syncthreads();
   }
@@ -307,7 +307,7 @@ k_render(KParams kp) {
         }
         float tb = 0.f;
         uint32_t id = 0, k = 0;
-        if (ok && !trace_ray<true, COUNT, WIDE>(a.sc, top, xyz(s0), xyz(s1), s1.w, tb, id, k, wc_s, a.err))
+        if (ok && !trace_ray<true, COUNT, TREE>(a.sc, top, xyz(s0), xyz(s1), s1.w, tb, id, k, wc_s, a.err))
           accumulate(kp.accum, __float_as_uint(s0.w), s2.x, s2.y, s2.z, a.color_scale);
       }
       __syncwarp();
@@ -381,7 +381,7 @@ k_render(KParams kp) {
     uint32_t id = RT_MISS_ID, k = 0;
     bool hit = false;
     if (active)
-      hit = trace_ray<false, COUNT, WIDE>(a.sc, top, o, d, INFINITY, t, id, k,
+      hit = trace_ray<false, COUNT, TREE>(a.sc, top, o, d, INFINITY, t, id, k,
                                    mode == M_PRIMARY ? wc_p : wc_r, a.err);
     __syncwarp();
 
@@ -442,6 +442,7 @@ k_render(KParams kp) {
         const CameraParams& cf = kp.cams[pi / P];
         dep[pi] = hit ? t * dot(d, v3(cf.fwd[0], cf.fwd[1], cf.fwd[2])) : INFINITY;
       }
+      if (!eye && a.refl_L) a.refl_L[pi] = hit ? mat.w : 0.f;
       float* nr = eye ? a.normal_R : a.normal_L;
       if (nr) {                            // zero normal on a miss
         nr[3 * (size_t)pi + 0] = hit ? nrm.x : 0.f;
@@ -468,7 +469,8 @@ k_render(KParams kp) {
 
 __global__ void k_resolve(const uint32_t* __restrict__ acc, float* __restrict__ out_L,
                           float* __restrict__ out_R, uint32_t n3, float inv_scale) {
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < 2 * n3; i += gridDim.x * blockDim.x) {
+  const uint32_t total = out_R ? 2 * n3 : n3;      // no right image: the left eye only
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
     const float v = fminf(1.f, (float)acc[i] * inv_scale);
     if (i < n3) out_L[i] = v; else out_R[i - n3] = v;
   }
@@ -480,7 +482,8 @@ __global__ void k_resolve(const uint32_t* __restrict__ acc, float* __restrict__ 
 // wide stores make fuller transfers over the CPU-GPU link.
 __global__ void k_resolve4(const uint4* __restrict__ acc, float4* __restrict__ out_L,
                            float4* __restrict__ out_R, uint32_t n3_4, float inv_scale) {
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < 2 * n3_4; i += gridDim.x * blockDim.x) {
+  const uint32_t total = out_R ? 2 * n3_4 : n3_4;  // no right image: the left eye only
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
     const uint4 a = acc[i];
     const float4 v = make_float4(fminf(1.f, (float)a.x * inv_scale), fminf(1.f, (float)a.y * inv_scale),
                                  fminf(1.f, (float)a.z * inv_scale), fminf(1.f, (float)a.w * inv_scale));
@@ -495,19 +498,19 @@ __global__ void k_counts(const uint32_t* counters, uint64_t primary, uint64_t* o
   out[2] = counters[C_REFL];
 }
 
-template <bool COUNT, bool WIDE>
+template <bool COUNT, int TREE>
 int blocks_per_sm() {
   static int cached = 0;
   if (!cached) {
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render<COUNT, WIDE>, kThreads,
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render<COUNT, TREE>, kThreads,
                                                   kMaxTopBytes);
     cached = per_sm > 0 ? per_sm : 1;
   }
   return cached;
 }
 
-template <bool COUNT, bool WIDE>
+template <bool COUNT, int TREE>
 cudaError_t render_impl(const RenderArgs& a, Workspace& ws, cudaStream_t st) {
   const uint32_t F = a.n_frames ? a.n_frames : 1u;
   if (F > (uint32_t)kMaxFrames) return cudaErrorInvalidValue;
@@ -544,8 +547,8 @@ cudaError_t render_impl(const RenderArgs& a, Workspace& ws, cudaStream_t st) {
   else cudaMemsetAsync(ws.accum + 3 * P, 0, P * 3 * sizeof(uint32_t), st);
   if (a.work) cudaMemsetAsync(a.work, 0, 9 * sizeof(uint64_t), st);
   profile_mark(ws, ST_CLEAR, st);
-  const size_t top_bytes = (WIDE && !COUNT) ? 7 * sizeof(float4) * a.sc.n_top : 0;
-  k_render<COUNT, WIDE><<<grid, kThreads, top_bytes, st>>>(kp);
+  const size_t top_bytes = (TREE == kTreeWide4 && !COUNT) ? 7 * sizeof(float4) * a.sc.n_top : 0;
+  k_render<COUNT, TREE><<<grid, kThreads, top_bytes, st>>>(kp);
   profile_mark(ws, a.trace_stage, st);
   const uint32_t n3 = (uint32_t)(P * 3);
   if (a.resolve) {
@@ -579,9 +582,9 @@ int num_sms() {
 
 int render_grid() {
   // the variants may fit different numbers of blocks; size for the largest grid
-  int b = blocks_per_sm<false, true>();
-  if (blocks_per_sm<false, false>() > b) b = blocks_per_sm<false, false>();
-  if (blocks_per_sm<true, false>() > b) b = blocks_per_sm<true, false>();
+  int b = blocks_per_sm<false, kTreeWide4>();
+  if (blocks_per_sm<false, kTreeBinary>() > b) b = blocks_per_sm<false, kTreeBinary>();
+  if (blocks_per_sm<true, kTreeBinary>() > b) b = blocks_per_sm<true, kTreeBinary>();
   return num_sms() * b;
 }
 
@@ -604,9 +607,9 @@ void profile_mark(Workspace& ws, int stage, cudaStream_t st) {
 
 cudaError_t render(const RenderArgs& a, Workspace& ws, cudaStream_t st) {
   if (a.sc.n_top * 7 * sizeof(float4) > (size_t)kMaxTopBytes) return cudaErrorInvalidValue;
-  if (a.work) return render_impl<true, false>(a, ws, st);
-  return a.binary || a.sc.n4 == 0 ? render_impl<false, false>(a, ws, st)
-                                   : render_impl<false, true>(a, ws, st);
+  if (a.work) return render_impl<true, kTreeBinary>(a, ws, st);
+  if (a.tree == kTreeWide4 && a.sc.n4 > 0) return render_impl<false, kTreeWide4>(a, ws, st);
+  return render_impl<false, kTreeBinary>(a, ws, st);
 }
 
 }  // namespace rt

@@ -529,8 +529,10 @@ def gbuffer_synthetic(seed: int, W: int, H: int, miss_frac: float = 0.2,
 
     Draw order per pixel (row-major): miss coin, depth u (log-uniform in
     [z_lo, z_hi)), normal x, y, z (uniform in [-1,1], then normalised), id u
-    (ids 0..999), r, g, b. Misses get depth +inf and id 0xFFFFFFFF. Returns
-    float32 depth (P), normal (P,3), rgb (P,3) and uint32 ids (P).
+    (ids 0..999), r, g, b. Misses get depth +inf and id 0xFFFFFFFF. The
+    hit surface's reflectivity is (0, 0.5, 0.7)[id % 3] (0 on a miss).
+    Returns float32 depth (P), normal (P,3), rgb (P,3), uint32 ids (P) and
+    float32 reflectivity (P).
     """
     u = SplitMix64(seed).uniform(W * H * 9).reshape(W * H, 9)
     miss = u[:, 0] < miss_frac
@@ -540,10 +542,12 @@ def gbuffer_synthetic(seed: int, W: int, H: int, miss_frac: float = 0.2,
     n /= np.maximum(np.linalg.norm(n, axis=1, keepdims=True), 1e-12)
     ids = np.minimum((u[:, 5] * 1000).astype(np.uint32), 999).astype(np.uint32)
     ids[miss] = 0xFFFFFFFF
-    return depth, n.astype(np.float32), ids, u[:, 6:9].astype(np.float32)
+    refl = np.array([0.0, 0.5, 0.7], np.float32)[ids % 3]
+    refl[miss] = 0.0
+    return depth, n.astype(np.float32), ids, u[:, 6:9].astype(np.float32), refl
 
 
-NET_LAYERS = ((9, 32), (32, 32), (32, 32), (32, 1))
+NET_LAYERS = ((10, 32), (32, 32), (32, 32), (32, 1))
 NET_PARAMS = sum(co * ci * 9 + co for ci, co in NET_LAYERS)
 
 
@@ -563,9 +567,10 @@ def net_params_he(seed: int) -> np.ndarray:
 
 def bf16_features_synthetic(seed: int, W: int, H: int) -> np.ndarray:
     """Random network inputs already representable in BF16: (P, 16) float32,
-    channels 0-8 uniform in [-1, 1) rounded to 8 significant bits, 9-15 zero."""
-    u = SplitMix64(seed).uniform(W * H * 9).reshape(W * H, 9) * 2.0 - 1.0
+    channels 0-9 uniform in [-1, 1) rounded to 8 significant bits, 10-15 zero."""
+    c = NET_LAYERS[0][0]
+    u = SplitMix64(seed).uniform(W * H * c).reshape(W * H, c) * 2.0 - 1.0
     f = np.zeros((W * H, 16), np.float32)
     m, e = np.frexp(u)
-    f[:, :9] = np.ldexp(np.round(m * 256.0) / 256.0, e)
+    f[:, :c] = np.ldexp(np.round(m * 256.0) / 256.0, e)
     return f

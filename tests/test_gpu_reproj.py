@@ -39,23 +39,28 @@ def _t(a, dtype=None):
 @pytest.mark.parametrize("W,H,seed", [(97, 41, 1), (256, 3, 2), (1, 5, 3), (333, 20, 4)])
 def test_warp_matches_oracle(W, H, seed):
     import torch
-    depth, normal, ids, rgb = sg.gbuffer_synthetic(seed, W, H)
+    depth, normal, ids, rgb, refl = sg.gbuffer_synthetic(seed, W, H)
     f_px, s, zc = 731.25, 0.065 * 3, 9.0
     P = W * H
     zbuf = torch.empty(P, dtype=torch.int64, device="cuda")
     f16 = torch.empty((P, 16), dtype=torch.bfloat16, device="cuda")
-    f32 = torch.empty((P, 9), dtype=torch.float32, device="cuda")
+    f32 = torch.empty((P, orp.IN_CH), dtype=torch.float32, device="cuda")
     hole = torch.empty(P, dtype=torch.uint8, device="cuda")
     warped = torch.empty((P, 3), dtype=torch.float32, device="cuda")
     capi.rt_reproj_warp(_t(depth), _t(normal), _t(ids.view(np.int32)), _t(rgb), W, H, f_px, s, zc,
-                        zbuf, f16, f32, hole, warped)
+                        zbuf, f16, f32, hole, warped, refl_L=_t(refl))
     torch.cuda.synchronize()
-    feat, ohole, owarp, src = orp.warp(depth, normal, ids, rgb, W, H, f_px, s, zc)
-    assert np.array_equal(hole.cpu().numpy().astype(bool), ohole)
+    feat, ohole, owarp, src = orp.warp(depth, normal, ids, rgb, W, H, f_px, s, zc, refl)
+    hc = hole.cpu().numpy()
+    assert np.array_equal(hc == 1, ohole)
+    # 2 marks a right pixel whose source surface reflects (always retraced)
+    assert np.array_equal(hc == 2, ~ohole & (feat[:, 9] > 0))
     g = f32.cpu().numpy()
     assert np.abs(g - feat).max() <= 1e-6
     assert np.abs(warped.cpu().numpy() - owarp).max() <= 1e-7
-    assert torch.equal(f16[:, :9].float(), f32.to(torch.bfloat16).float()) and (f16[:, 9:] == 0).all()
+    c = orp.IN_CH
+    assert torch.equal(f16[:, :c].float(), f32.to(torch.bfloat16).float()) and (f16[:, c:] == 0).all()
+    assert (feat[~ohole, 9] > 0).any() or (~ohole).sum() < 10  # the reflectivity channel is carried
     assert 0 < ohole.mean() < 1 or P < 10
 
 
@@ -64,8 +69,8 @@ def test_network_forward_matches_oracle(W, H):
     import torch
     params = sg.net_params_he(11)
     rng = np.random.default_rng(5)
-    params[2592:2624] = rng.normal(0, 0.1, 32)             # non-zero biases
-    params[21408] = -0.5
+    params[orp.OFF_B[0]:orp.OFF_B[0] + 32] = rng.normal(0, 0.1, 32)             # non-zero biases
+    params[orp.OFF_B[3]] = -0.5
     feat = sg.bf16_features_synthetic(12, W, H)
     net = capi.Net(params)
     try:
@@ -85,7 +90,7 @@ def test_gradients_match_float64_autograd():
     import torch
     W, H = 200, 9
     params = sg.net_params_he(21)
-    params[21408] = 0.2
+    params[orp.OFF_B[3]] = 0.2
     feat = sg.bf16_features_synthetic(22, W, H)
     label = (np.random.default_rng(6).random(W * H) < 0.3).astype(np.float32)
     net = capi.Net(params)
@@ -209,8 +214,8 @@ def test_fp8_forward_matches_fp8_oracle(W, H):
     import torch
     params = sg.net_params_he(11)
     rng = np.random.default_rng(5)
-    params[2592:2624] = rng.normal(0, 0.1, 32)
-    params[21408] = -0.5
+    params[orp.OFF_B[0]:orp.OFF_B[0] + 32] = rng.normal(0, 0.1, 32)
+    params[orp.OFF_B[3]] = -0.5
     feat = sg.bf16_features_synthetic(12, W, H)
     net = capi.Net(params)
     try:
@@ -258,7 +263,7 @@ def test_activation_amax_matches_bf16_oracle_activations():
         net.close()
     # the oracle's BF16-emulated hidden activations, layer by layer
     import torch.nn.functional as F
-    x = torch.tensor(np.asarray(feat, np.float64)[:, :9].reshape(H, W, 9)).permute(2, 0, 1)[None]
+    x = torch.tensor(np.asarray(feat, np.float64)[:, :orp.IN_CH].reshape(H, W, orp.IN_CH)).permute(2, 0, 1)[None]
     x = orp._bf16(x)
     want = []
     for w, b in orp.unpack(params)[:3]:
@@ -385,8 +390,8 @@ def test_network_forward_multi_tile_per_cta(W, H):
     assert _tiles_per_cta(W, H, 2) >= 4
     params = sg.net_params_he(41)
     rng = np.random.default_rng(42)
-    params[2592:2624] = rng.normal(0, 0.1, 32)
-    params[21408] = -0.5
+    params[orp.OFF_B[0]:orp.OFF_B[0] + 32] = rng.normal(0, 0.1, 32)
+    params[orp.OFF_B[3]] = -0.5
     feat = sg.bf16_features_synthetic(43, W, H)
     net = capi.Net(params)
     try:
@@ -416,7 +421,7 @@ def test_gradients_multi_tile_per_cta(W, H):
     import torch
     assert _tiles_per_cta(W, H, 2) >= 4
     params = sg.net_params_he(51)
-    params[21408] = 0.2
+    params[orp.OFF_B[3]] = 0.2
     feat = sg.bf16_features_synthetic(52, W, H)
     label = (np.random.default_rng(53).random(W * H) < 0.3).astype(np.float32)
     net = capi.Net(params)
@@ -441,10 +446,11 @@ def test_gradients_multi_tile_per_cta(W, H):
 # ---------------------------------------------- mixed retrace mask (A9)
 def test_reprojection_mixed_mask_matches_oracle():
     """Trained weights at threshold 0.1 on a 320x240 small scene: the right
-    pixels retraced are the holes and the pixels whose oracle probability
-    (on the GPU's own features) exceeds the threshold; retraced pixels equal
-    the full trace, the others the oracle's warped left colour. Pixels whose
-    probability lies within 5e-3 of the threshold may go either way."""
+    pixels retraced are the holes, the pixels showing a reflective surface
+    and the pixels whose oracle probability (on the GPU's own features)
+    exceeds the threshold; retraced pixels equal the full trace, the others
+    the oracle's warped left colour. Pixels whose probability lies within
+    5e-3 of the threshold may go either way."""
     import torch
     from paper_1702_01530_gb300 import train_reproj as tr
     s = sg.config_small(7, W=320, H=240)
@@ -456,6 +462,7 @@ def test_reprojection_mixed_mask_matches_oracle():
     try:
         full = g.render(aux=True)
         depth_L = full["depth"][0].cpu().numpy()
+        hit_L = full["hit_id"][0].cpu().numpy().view(np.uint32).reshape(P)
         fL, fR = full["rgb"][0], full["rgb"][1]
         L = torch.empty((H, W, 3), dtype=torch.float32, device="cuda")
         R = torch.empty_like(L)
@@ -475,11 +482,17 @@ def test_reprojection_mixed_mask_matches_oracle():
         net.close()
         g.close()
     f_px = capi.focal_px(s.camera, H)
-    _, hole, warped, _ = orp.warp(depth_L, np.zeros((P, 3)), np.zeros(P, np.uint32), Lh, W, H,
-                                  f_px, s.eye_sep, s.convergence)
+    # reflectivity of each left pixel's surface (ids: spheres first, then triangles)
+    refl_of_id = np.concatenate([s.materials["reflectivity"][s.spheres["material"]],
+                                 s.materials["reflectivity"][s.triangles["material"]]])
+    refl_L = np.where(hit_L == capi.RT_MISS_ID, 0.0, refl_of_id[np.minimum(hit_L, len(refl_of_id) - 1)])
+    ofeat, hole, warped, _ = orp.warp(depth_L, np.zeros((P, 3)), np.zeros(P, np.uint32), Lh, W, H,
+                                      f_px, s.eye_sep, s.convergence, refl_L.astype(np.float32))
+    mirror = ~hole & (ofeat[:, 9] > 0)
+    assert np.array_equal(ofeat[:, 9] > 0, feat[:, 9] > 0)             # the GPU's feature agrees
     p = orp.forward(params, feat, W, H, bf16=True).reshape(P)
     near = np.abs(p - thr) < 5e-3
-    want = hole | (p > thr)
+    want = hole | mirror | (p > thr)
     R2, F2, Wp = Rh.reshape(P, 3), fRh.reshape(P, 3), warped.reshape(P, 3).astype(np.float32)
     sel = want & ~near
     assert np.array_equal(R2[sel], F2[sel])                       # retraced = full trace
@@ -487,4 +500,4 @@ def test_reprojection_mixed_mask_matches_oracle():
     assert np.array_equal(R2[keep], Wp[keep])                     # others = warped colour
     assert abs(int(n.item()) - int(want.sum())) <= int(near.sum())
     # a mixed mask: some pixels retraced for p > thr beyond the holes, most kept
-    assert (want & ~hole).sum() > 0 and 0 < want.mean() < 0.5, (want.sum(), hole.sum())
+    assert (want & ~hole & ~mirror).sum() > 0 and 0 < want.mean() < 0.5, (want.sum(), hole.sum())

@@ -66,8 +66,8 @@ REPROJ_MUTANTS = [
     ("forward: input unrounded", "        x = _bf16(x)\n    layers = unpack(params)",
      "        pass\n    layers = unpack(params)", "forward"),
     ("backward: input unrounded",
-     "a = [rb(torch.tensor(np.asarray(feat, np.float64)[:, :9].reshape(H, W, 9)).permute(2, 0, 1)[None])]",
-     "a = [torch.tensor(np.asarray(feat, np.float64)[:, :9].reshape(H, W, 9)).permute(2, 0, 1)[None]]",
+     "a = [rb(torch.tensor(np.asarray(feat, np.float64)[:, :IN_CH].reshape(H, W, IN_CH)).permute(2, 0, 1)[None])]",
+     "a = [torch.tensor(np.asarray(feat, np.float64)[:, :IN_CH].reshape(H, W, IN_CH)).permute(2, 0, 1)[None]]",
      "grads"),
     ("backward: hidden activations unrounded",
      "a.append(rb(torch.relu(F.conv2d(a[-1], rb(w), b, padding=1))))",

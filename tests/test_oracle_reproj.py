@@ -45,7 +45,7 @@ def test_warp_of_fronto_parallel_plane_is_a_uniform_shift():
     src = src.reshape(H, W)
     jj, ii = np.mgrid[0:H, 0:W - 3]
     assert np.array_equal(src[:, :W - 3], jj * W + ii + 3)         # x_R = x_L - 3
-    f = feat.reshape(H, W, 9)
+    f = feat.reshape(H, W, orp.IN_CH)
     assert np.allclose(f[:, :W - 3, 8], 3.0 / 16) and np.allclose(f[:, :W - 3, 0], 0.025)
     assert np.allclose(f[:, :W - 3, 1:4], [0, 0, 1]) and (f[:, W - 3:] == 0).all()
     # misses are sources at infinity: D = -f s / zc = -1 -> they fill column 0.. from the left
@@ -58,6 +58,16 @@ def test_warp_of_fronto_parallel_plane_is_a_uniform_shift():
     _, hole2, _, src2 = orp.warp(depth2, normal, ids, rgb, W, H, 100.0, 0.1, 10.0)
     assert hole2.reshape(H, W)[:, 0].all() and not hole2.reshape(H, W)[:, 1:].any()
     assert src2.reshape(H, W)[0, 5] == 4                           # floor(4 + 0.75 + 0.5) = 5
+
+
+def test_warp_carries_reflectivity_of_the_source_pixel():
+    W, H = 40, 6
+    depth, normal, ids, rgb = _plane(W, H, 2.5)
+    refl = (np.arange(W * H) % 7 / 10.0).astype(np.float32)
+    feat, hole, _, src = orp.warp(depth, normal, ids, rgb, W, H, 100.0, 0.1, 10.0, refl)
+    ok = ~hole
+    assert np.array_equal(feat[ok, 9], refl[src[ok]].astype(np.float64)) and (feat[hole] == 0).all()
+    assert (orp.warp(depth, normal, ids, rgb, W, H, 100.0, 0.1, 10.0)[0][:, 9] == 0).all()
 
 
 def test_warp_z_test_keeps_nearest_then_lowest_index():
@@ -106,7 +116,7 @@ def test_network_forward_matches_explicit_loops():
     params = sg.net_params_he(3).astype(np.float64)
     params[params.size - 1] = 0.3
     feat = sg.bf16_features_synthetic(4, W, H)
-    x = feat[:, :9].reshape(H, W, 9).transpose(2, 0, 1).astype(np.float64)
+    x = feat[:, :orp.IN_CH].reshape(H, W, orp.IN_CH).transpose(2, 0, 1).astype(np.float64)
     for li, (w, b) in enumerate(orp.unpack(params)):
         x = _conv_loops(x, w, b)
         if li < 3:
@@ -137,7 +147,9 @@ def test_network_gradient_matches_central_differences():
     y = (np.random.default_rng(2).random(W * H) < 0.3).astype(np.float64)
     _, g = orp.loss_and_grads(params, feat, y, W, H)
     rng = np.random.default_rng(3)
-    idx = np.concatenate([rng.choice(2592, 6, replace=False), [2600, 2624 + 5, 21087, 21120 + 7, 21408]])
+    B, Wo = orp.OFF_B, orp.OFF_W
+    idx = np.concatenate([rng.choice(B[0], 6, replace=False),
+                          [B[0] + 8, Wo[1] + 5, B[2] - 1, Wo[3] + 7, B[3]]])
     h = 1e-6
     for i in idx:
         pp, pm = params.copy(), params.copy()
@@ -150,7 +162,7 @@ def test_network_gradient_matches_central_differences():
 def test_emulated_backward_equals_autograd_without_rounding():
     W, H = 6, 5
     params = sg.net_params_he(9).astype(np.float64)
-    params[2592:2624] = 0.05
+    params[orp.OFF_B[0]:orp.OFF_B[0] + 32] = 0.05
     feat = sg.bf16_features_synthetic(10, W, H)
     y = (np.random.default_rng(4).random(W * H) < 0.4).astype(np.float64)
     _, g = orp.loss_and_grads(params, feat, y, W, H)
@@ -162,7 +174,9 @@ def test_emulated_backward_equals_autograd_without_rounding():
 
 
 def test_generators_for_reprojection():
-    d, n, ids, rgb = sg.gbuffer_synthetic(1, 30, 20)
+    d, n, ids, rgb, refl = sg.gbuffer_synthetic(1, 30, 20)
+    assert set(np.unique(refl[~np.isinf(d)]).tolist()) <= set(np.float32([0.0, 0.5, 0.7]).tolist())
+    assert (refl[np.isinf(d)] == 0).all()
     assert np.isinf(d).mean() == pytest.approx(0.2, abs=0.06)
     assert np.allclose(np.linalg.norm(n, axis=1), 1.0, atol=1e-6)
     assert (ids[np.isinf(d)] == 0xFFFFFFFF).all() and (ids[~np.isinf(d)] < 1000).all()
@@ -171,7 +185,7 @@ def test_generators_for_reprojection():
     t = torch.tensor(f)
     assert torch.equal(t.to(torch.bfloat16).to(torch.float32), t)
     p = sg.net_params_he(0)
-    assert p.size == sg.NET_PARAMS == 21409 and p[2592:2624].max() == 0
+    assert p.size == sg.NET_PARAMS == orp.N_PARAMS == 21697 and p[orp.OFF_B[0]:orp.OFF_B[0] + 32].max() == 0
 
 
 def test_composite_oracle_definitions():
@@ -255,7 +269,7 @@ def test_fp8_forward_identity_network_closed_form():
     rng = np.random.default_rng(5)
     feat = np.zeros((W * H, 16), np.float32)
     feat[:, 0] = rng.integers(0, 16, W * H) / 8.0
-    feat[:, 1:9] = rng.uniform(-1, 1, (W * H, 8))
+    feat[:, 1:orp.IN_CH] = rng.uniform(-1, 1, (W * H, orp.IN_CH - 1))
     for scales in ((16.0, 16.0, 16.0), (1.0, 64.0, 0.5)):
         p = orp.forward_fp8(params, feat, W, H, scales)
         want = 1.0 / (1.0 + np.exp(-(feat[:, 0].astype(np.float64).reshape(H, W) - 0.75)))
@@ -322,7 +336,7 @@ def _conv_dgrad(dz, w, H, W):
 def _net_loops_bf16(params, feat, label, W, H):
     """Probability map and mean-BCE gradient with BF16 rounding points."""
     layers = orp.unpack(np.asarray(params, np.float64))
-    a = [_rne_bf16(np.asarray(feat, np.float64)[:, :9].reshape(H, W, 9).transpose(2, 0, 1))]
+    a = [_rne_bf16(np.asarray(feat, np.float64)[:, :orp.IN_CH].reshape(H, W, orp.IN_CH).transpose(2, 0, 1))]
     for li in range(3):
         w, b = layers[li]
         a.append(_rne_bf16(np.maximum(_conv_loops(a[-1], _rne_bf16(w), b), 0.0)))
