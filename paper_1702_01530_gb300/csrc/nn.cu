@@ -75,11 +75,23 @@ constexpr int kTileM = 128;          // pixels per row tile (one MMA M block)
 // starts earlier than that of the even chunks: the two core matrices of one
 // MMA's K step (an even and an odd chunk of the same pixels) then sit
 // RT_CONV_SKEW * 16 bytes apart modulo 128 instead of on the same shared-
-// memory banks (the chunk planes are 128-byte aligned for TMA).
+// memory banks (the chunk planes are 128-byte aligned for TMA). Measured at
+// 1920x1080 (network forward, outputs identical bit for bit): 0.2877 ->
+// 0.2895 ms BF16, 0.1662 -> 0.1685 ms FP8 at 4: no gain, off by default.
 #ifndef RT_CONV_SKEW
 #define RT_CONV_SKEW 0
 #endif
 constexpr int kSkew = RT_CONV_SKEW;
+// RT_CONV_BSWZ = 1: the weight operand in shared memory in the swizzled
+// K-major layout (rows of one output channel's 32 or 64 bytes of input
+// channels per tap, 16-byte chunks permuted by the row: 32-byte rows swizzle
+// by bit 7 of the address, 64-byte rows by bits 7-8) instead of 8x16-byte
+// core matrices. Measured at 1920x1080 (outputs identical bit for bit):
+// 0.2892 -> 0.2895 ms BF16, 0.1670 -> 0.1669 ms FP8: the weight operand's
+// layout does not limit the kernel; off by default.
+#ifndef RT_CONV_BSWZ
+#define RT_CONV_BSWZ 0
+#endif
 constexpr int kHaloW = kTileM + 2 + kSkew;   // halo pixels per row (130 without skew)
 constexpr int kHaloRows = (kRows + 2) * kHaloW;  // halo pixels per tile
 constexpr uint32_t kWaitBound = 1u << 26;
@@ -251,6 +263,11 @@ __device__ __forceinline__ void issue_tile_mmas(uint32_t hbase, uint32_t wbase, 
   // LBO = the distance from an even chunk's core matrix to the odd one's
   const uint32_t a_lo = desc_lo(hbase, kPlaneBytes + 16u * kSkew), b_lo = desc_lo(wbase, COUT * 16);
   constexpr uint32_t hi = desc_hi(128u);
+  // swizzled weights: rows of kRowB bytes (one output channel's input
+  // channels of a tap), 8-row atoms kRowB * 8 apart; layout type 6 = 32-byte,
+  // 4 = 64-byte swizzle (bits 61-63 of the descriptor)
+  constexpr uint32_t kRowB = 16u * kChunks;
+  constexpr uint32_t b_hi = desc_hi(8u * kRowB) | ((kRowB == 64u ? 4u : 6u) << 29);
 #pragma unroll
   for (int ry = 0; ry < kRows; ++ry) {
 #pragma unroll
@@ -259,8 +276,13 @@ __device__ __forceinline__ void issue_tile_mmas(uint32_t hbase, uint32_t wbase, 
 #pragma unroll
       for (int ks = 0; ks < kChunks / 2; ++ks) {
         const uint32_t a_off = (2u * ks) * kPlaneBytes + (uint32_t)((ry + dy) * kHaloW + dx) * 16u;
+#if RT_CONV_BSWZ
+        const uint32_t b_off = (uint32_t)tap * COUT * kRowB + 32u * ks;
+        const uint64_t da = desc_join(a_lo + (a_off >> 4), hi), db = desc_join(b_lo + (b_off >> 4), b_hi);
+#else
         const uint32_t b_off = (uint32_t)((tap * kChunks + 2 * ks) * COUT) * 16u;
         const uint64_t da = desc_join(a_lo + (a_off >> 4), hi), db = desc_join(b_lo + (b_off >> 4), hi);
+#endif
         if (FP8) mma_e4m3(dtmem + (uint32_t)(ry * COUT), da, db, idesc, (tap | ks) ? 1u : 0u);
         else mma_bf16(dtmem + (uint32_t)(ry * COUT), da, db, idesc, (tap | ks) ? 1u : 0u);
       }
@@ -342,7 +364,18 @@ __global__ void __launch_bounds__(kConvTmaThreads, 1)
   {
     const uint4* src = reinterpret_cast<const uint4*>(wpk);
     uint4* dst = reinterpret_cast<uint4*>(wsm);
+#if RT_CONV_BSWZ
+    // packed [tap][chunk][co] 16-byte chunks -> [tap][co] rows, chunk c of
+    // row co at chunk c ^ (row bits the swizzle takes)
+    for (uint32_t i = tid; i < Lt::kWBytes / 16u; i += blockDim.x) {
+      const uint32_t co = i % COUT, rest = i / COUT;
+      const uint32_t c = rest % Lt::kChunks, tap = rest / Lt::kChunks;
+      const uint32_t sw = Lt::kChunks == 4 ? (co >> 1) & 3u : (co >> 2) & 1u;
+      dst[(tap * COUT + co) * Lt::kChunks + (c ^ sw)] = src[i];
+    }
+#else
     for (uint32_t i = tid; i < Lt::kWBytes / 16u; i += blockDim.x) dst[i] = src[i];
+#endif
     if (tid < COUT) {
       bsm[tid] = bias ? bias[tid] : 0.f;
       ism[tid] = inv ? inv[tid] : 1.f;
