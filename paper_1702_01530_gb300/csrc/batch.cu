@@ -234,7 +234,8 @@ __global__ void __launch_bounds__(kThreads, RT_BATCH_MIN_BLOCKS) k_render_batch(
         lights = rq->sc.lights;
         max_depth = rq->max_depth;
       }
-      accumulate(kp.accum, pix, ar, ag, ab, scale);
+      if (RT_PRIMARY_STORE && mode == 1) store_first(kp.accum, pix, ar, ag, ab, scale);
+      else accumulate(kp.accum, pix, ar, ag, ab, scale);
     }
     const bool lit = active && hit;
     const V3 o2 = p + nrm * eps;
@@ -428,7 +429,7 @@ int apply_config(rt_batch* b, const rt_batch_config& c) {
   cudaMemcpyAsync(b->d_table, b->h_table, sizeof(rt::BatchReq) * b->n, cudaMemcpyHostToDevice, st);
   cudaMemsetAsync(b->counters, 0, rt::C_TOTAL * sizeof(uint32_t), st);
   cudaMemsetAsync(b->err, 0, sizeof(uint32_t), st);
-  cudaMemsetAsync(b->accum, 0, b->total_pixels * 3 * sizeof(uint32_t), st);
+  if (!RT_PRIMARY_STORE) cudaMemsetAsync(b->accum, 0, b->total_pixels * 3 * sizeof(uint32_t), st);
   if (c.track_latency) {
     cudaMemsetAsync(b->done_ns, 0, (size_t)b->n * sizeof(unsigned long long), st);
     rt::k_stamp<<<1, 32, 0, st>>>(b->done_ns + b->n);

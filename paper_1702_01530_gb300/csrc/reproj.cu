@@ -137,23 +137,51 @@ __global__ void k_labels(const uint8_t* __restrict__ hole, const float* __restri
 }
 
 // mask = hole, reflective source, or prob > threshold; the masked right
-// pixels (as global indices P + p) are appended to plist with warp-aggregated
-// atomics
+// pixels (as global indices P + p) are appended to plist, in pixel order
+// within each warp's 128 pixels, with one atomic per warp. A thread takes 4
+// consecutive pixels (one 4-byte and one 16-byte load when the buffers allow
+// it); the pixels past the last whole group of 4 are read one by one.
 __global__ void k_mask_compact(const uint8_t* __restrict__ hole, const float* __restrict__ prob,
-                               uint32_t P, float threshold, uint8_t* mask, uint32_t* plist,
-                               uint32_t* count) {
+                               uint32_t P, float threshold, bool wide, uint8_t* mask,
+                               uint32_t* plist, uint32_t* count) {
   const uint32_t lane = threadIdx.x & 31u;
-  for (uint32_t base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u; base < P;
+  const uint32_t groups = (P + 3u) / 4u;
+  for (uint32_t base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u; base < groups;
        base += gridDim.x * blockDim.x) {
-    const uint32_t p = base + lane;
-    bool m = false;
-    if (p < P) m = hole[p] || (prob && prob[p] > threshold);
-    const uint32_t bal = __ballot_sync(0xFFFFFFFFu, m);
+    const uint32_t g = base + lane, p0 = 4u * g;
+    uint32_t bits = 0;                    // bit j: pixel p0 + j is masked
+    if (g < groups) {
+      if (wide && p0 + 4u <= P) {
+        const uchar4 h = *reinterpret_cast<const uchar4*>(hole + p0);
+        float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (prob) q = *reinterpret_cast<const float4*>(prob + p0);
+        bits = (h.x || (prob && q.x > threshold) ? 1u : 0u) | (h.y || (prob && q.y > threshold) ? 2u : 0u) |
+               (h.z || (prob && q.z > threshold) ? 4u : 0u) | (h.w || (prob && q.w > threshold) ? 8u : 0u);
+        if (mask)
+          *reinterpret_cast<uchar4*>(mask + p0) =
+              make_uchar4(bits & 1u, (bits >> 1) & 1u, (bits >> 2) & 1u, (bits >> 3) & 1u);
+      } else {
+        for (uint32_t j = 0; j < 4u && p0 + j < P; ++j) {
+          const bool m = hole[p0 + j] || (prob && prob[p0 + j] > threshold);
+          bits |= (m ? 1u : 0u) << j;
+          if (mask) mask[p0 + j] = m ? 1 : 0;
+        }
+      }
+    }
+    // exclusive prefix sum of the lanes' counts
+    const uint32_t n = __popc(bits);
+    uint32_t incl = n;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t v = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+      if (lane >= (uint32_t)d) incl += v;
+    }
+    const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
     uint32_t off = 0;
-    if (lane == 0 && bal) off = atomicAdd(count, (uint32_t)__popc(bal));
-    off = __shfl_sync(0xFFFFFFFFu, off, 0);
-    if (m) plist[off + __popc(bal & ((1u << lane) - 1u))] = P + p;
-    if (p < P && mask) mask[p] = m ? 1 : 0;
+    if (lane == 31 && total) off = atomicAdd(count, total);
+    off = __shfl_sync(0xFFFFFFFFu, off, 31) + incl - n;
+    for (uint32_t j = 0; j < 4u; ++j)
+      if (bits >> j & 1u) plist[off++] = P + p0 + j;
   }
 }
 
@@ -164,6 +192,32 @@ __global__ void k_compose(const uint8_t* __restrict__ mask, const uint32_t* __re
   for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < 3 * P; k += gridDim.x * blockDim.x) {
     const uint32_t p = k / 3;
     out_R[k] = mask[p] ? fminf(1.f, (float)accum_R[k] * inv_scale) : warped[k];
+  }
+}
+
+// the same, 4 pixels (12 floats) per thread as 16-byte loads and stores;
+// the sums are read only for groups with a masked pixel
+__global__ void k_compose4(const uchar4* __restrict__ mask, const uint4* __restrict__ accum_R,
+                           const float4* __restrict__ warped, uint32_t groups, float inv_scale,
+                           float4* out_R) {
+  for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < groups; g += gridDim.x * blockDim.x) {
+    const uchar4 m = mask[g];
+    float4 v[3] = {warped[3 * (size_t)g], warped[3 * (size_t)g + 1], warped[3 * (size_t)g + 2]};
+    if (m.x | m.y | m.z | m.w) {
+      const uint4 a[3] = {accum_R[3 * (size_t)g], accum_R[3 * (size_t)g + 1], accum_R[3 * (size_t)g + 2]};
+      const uint32_t* ai = reinterpret_cast<const uint32_t*>(a);
+      float* vf = reinterpret_cast<float*>(v);
+      const uint8_t mm[4] = {m.x, m.y, m.z, m.w};
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (mm[j]) {
+#pragma unroll
+          for (int c = 0; c < 3; ++c) vf[3 * j + c] = fminf(1.f, (float)ai[3 * j + c] * inv_scale);
+        }
+    }
+    out_R[3 * (size_t)g] = v[0];
+    out_R[3 * (size_t)g + 1] = v[1];
+    out_R[3 * (size_t)g + 2] = v[2];
   }
 }
 
@@ -198,13 +252,23 @@ cudaError_t reproj_labels(const uint8_t* hole, const float* warped, const float*
 cudaError_t reproj_mask(const uint8_t* hole, const float* prob, uint32_t P, float threshold,
                         uint8_t* mask, uint32_t* plist, uint32_t* count, cudaStream_t st) {
   cudaMemsetAsync(count, 0, sizeof(uint32_t), st);
-  k_mask_compact<<<grid_1d(P, 256), 256, 0, st>>>(hole, prob, P, threshold, mask, plist, count);
+  const bool wide = ((uintptr_t)hole % 4) == 0 && ((uintptr_t)prob % 16) == 0 && ((uintptr_t)mask % 4) == 0;
+  k_mask_compact<<<grid_1d((P + 3) / 4, 256), 256, 0, st>>>(hole, prob, P, threshold, wide, mask, plist,
+                                                            count);
   return cudaGetLastError();
 }
 
 cudaError_t reproj_compose(const uint8_t* mask, const uint32_t* accum_R, const float* warped,
                            uint32_t P, float inv_scale, float* out_R, cudaStream_t st) {
-  k_compose<<<grid_1d(3ull * P, 256), 256, 0, st>>>(mask, accum_R, warped, P, inv_scale, out_R);
+  const bool wide = P % 4 == 0 && ((uintptr_t)mask % 4) == 0 && ((uintptr_t)accum_R % 16) == 0 &&
+                    ((uintptr_t)warped % 16) == 0 && ((uintptr_t)out_R % 16) == 0;
+  if (wide)
+    k_compose4<<<grid_1d(P / 4, 256), 256, 0, st>>>(reinterpret_cast<const uchar4*>(mask),
+                                                    reinterpret_cast<const uint4*>(accum_R),
+                                                    reinterpret_cast<const float4*>(warped), P / 4,
+                                                    inv_scale, reinterpret_cast<float4*>(out_R));
+  else
+    k_compose<<<grid_1d(3ull * P, 256), 256, 0, st>>>(mask, accum_R, warped, P, inv_scale, out_R);
   return cudaGetLastError();
 }
 

@@ -29,10 +29,11 @@
 //              instead of one per bounce depth.
 //   k_resolve  fixed-point sums -> float RGB, clamp to [0,1]
 //
-// Colour sums are fixed-point uint32 per channel (atomic adds of
-// round(value * 2^k)): integer addition is associative, so the image does
-// not depend on the order in which shadow rays finish, and both eyes of a
-// zero-separation pair are bitwise identical.
+// Colour sums are fixed-point uint32 per channel (round(value * 2^k); the
+// primary ray stores its term, every later ray adds its own atomically):
+// integer addition is associative, so the image does not depend on the order
+// in which shadow rays finish, and both eyes of a zero-separation pair are
+// bitwise identical.
 //
 // Traversal (Table 1 of the paper: BVH trees): BVH2 nodes of 64 B with both
 // child boxes, read as four 16-byte vector loads through the read-only path;
@@ -398,7 +399,8 @@ k_render(KParams kp) {
         const float kd = (1.f - mat.w) * kAmbient;
         ar = w.x * kd * mat.x; ag = w.y * kd * mat.y; ab = w.z * kd * mat.z;
       }
-      accumulate(kp.accum, pix, ar, ag, ab, a.color_scale);
+      if (RT_PRIMARY_STORE && mode == M_PRIMARY) store_first(kp.accum, pix, ar, ag, ab, a.color_scale);
+      else accumulate(kp.accum, pix, ar, ag, ab, a.color_scale);
     }
     const bool lit = active && hit;
     const V3 o2 = p + nrm * eps;
@@ -540,11 +542,14 @@ cudaError_t render_impl(const RenderArgs& a, Workspace& ws, cudaStream_t st) {
   }
   kp.epoch = ws.epoch;
   cudaMemsetAsync(ws.counters, 0, C_TOTAL * sizeof(uint32_t), st);
-  // clear the colour sums of the eyes this render traces
-  const bool left = !a.plist && (a.eyes & 1u), right = a.plist || (a.eyes & 2u);
-  if (left && right) cudaMemsetAsync(ws.accum, 0, 2 * P * 3 * sizeof(uint32_t), st);
-  else if (left) cudaMemsetAsync(ws.accum, 0, P * 3 * sizeof(uint32_t), st);
-  else cudaMemsetAsync(ws.accum + 3 * P, 0, P * 3 * sizeof(uint32_t), st);
+  // the colour sums of the traced pixels start at their primary ray's store;
+  // with atomic adds only, clear the sums of the eyes this render traces
+  if (!RT_PRIMARY_STORE) {
+    const bool left = !a.plist && (a.eyes & 1u), right = a.plist || (a.eyes & 2u);
+    if (left && right) cudaMemsetAsync(ws.accum, 0, 2 * P * 3 * sizeof(uint32_t), st);
+    else if (left) cudaMemsetAsync(ws.accum, 0, P * 3 * sizeof(uint32_t), st);
+    else cudaMemsetAsync(ws.accum + 3 * P, 0, P * 3 * sizeof(uint32_t), st);
+  }
   if (a.work) cudaMemsetAsync(a.work, 0, 9 * sizeof(uint64_t), st);
   profile_mark(ws, ST_CLEAR, st);
   const size_t top_bytes = (TREE == kTreeWide4 && !COUNT) ? 7 * sizeof(float4) * a.sc.n_top : 0;

@@ -79,6 +79,13 @@ constexpr int kMaxTopBytes = 85 * 7 * 16;
 // match, and pixel positions by multiplication with host-computed scales
 // instead of two divisions per primary ray: 1.050 -> 1.020 ms per 1080p blob
 // pair, 0.222 -> 0.214 ms for the 10-primitive scene; on by default
+// RT_PRIMARY_STORE = 1: a pixel's primary ray stores its contribution
+// (store_first) and the colour sums are not cleared before a render; 0: every
+// contribution is an atomic add onto sums cleared by a memset.
+#ifndef RT_PRIMARY_STORE
+#define RT_PRIMARY_STORE 1
+#endif
+
 #ifndef RT_FAST_RCP
 #define RT_FAST_RCP 1
 #endif
@@ -670,6 +677,19 @@ __device__ __forceinline__ void accumulate(uint32_t* acc, uint32_t pix, float r,
   atomicAdd(p + 0, __float2uint_rn(r * scale));
   atomicAdd(p + 1, __float2uint_rn(g * scale));
   atomicAdd(p + 2, __float2uint_rn(b * scale));
+}
+
+// The first contribution to a pixel: its primary ray's, stored rather than
+// added, so the sums need no clearing before the launch. Every later
+// contribution (shadow and mirror rays, all spawned by this ray after this
+// store, on this lane or handed on through a release store) is an atomic add
+// that the hand-over orders after it.
+__device__ __forceinline__ void store_first(uint32_t* acc, uint32_t pix, float r, float g, float b,
+                                            float scale) {
+  uint32_t* p = acc + 3 * (size_t)pix;
+  p[0] = __float2uint_rn(r * scale);
+  p[1] = __float2uint_rn(g * scale);
+  p[2] = __float2uint_rn(b * scale);
 }
 
 }  // namespace
