@@ -3,15 +3,29 @@
 // and FP32 accumulation on the 5th-generation tensor cores (sm_103a).
 //
 // Convolution as implicit GEMM on tcgen05 (k_conv_tma):
-//   a persistent CTA computes tiles of R rows x 128 consecutive pixels: per
-//   row, D[128 pixels, Cout] = sum over the 9 taps (dy, dx) of
-//   A_tap[128, Cin] x B_tap[Cin, Cout]. The input halo (R+2 rows x 130 pixels x
-//   Cin channels, BF16) sits in shared memory as 16-byte (8-channel) chunks
-//   ordered [chunk][halo pixel], so A_tap for every tap is the same matrix
-//   shifted by (row+dy)*130 + dx rows: the K-major, non-swizzled operand layout
-//   with 8-row core matrices 128 B apart (SBO) and 8-channel chunk planes
-//   (R+2)*130*16 B (rounded up to 128 B) apart (LBO). Weights are pre-packed in
-//   the same core-matrix layout.
+//   a persistent CTA computes tiles of R rows x 128 consecutive pixels:
+//   output row ry is D_ry[128 pixels, Cout] = sum over the 9 taps (dy, dx) of
+//   A(ry+dy, dx)[128, Cin] x B(dy, dx)[Cin, Cout], where A(h, dx) is halo row h
+//   shifted by dx pixels. The input halo (R+2 rows x 130 pixels x Cin
+//   channels) sits in shared memory as 16-byte channel chunks ordered
+//   [chunk][halo pixel], so every A(h, dx) is the same matrix shifted by
+//   h*130 + dx rows: the K-major, non-swizzled operand layout with 8-row core
+//   matrices 128 B apart (SBO) and chunk planes (R+2)*130*16 B (rounded up to
+//   128 B) apart (LBO).
+//   Stacked taps: an MMA of N = Cout costs the tensor core as much as one of
+//   N = 64 (about 45 cycles on GB300, measured; N = 96 about 56, N = 256 about
+//   128, the full rate), so the three vertical taps of a kernel column are
+//   multiplied in one MMA of N = 3 Cout: B(dx) = [B(2, dx) | B(1, dx) |
+//   B(0, dx)], and A(h, dx) x B(dx) lands in TMEM at column h*Cout of the
+//   tile's accumulators, where output row ry keeps its sum at column
+//   (ry+2)*Cout: block j of the product (tap dy = 2 - j) adds into row h - dy.
+//   Consecutive MMAs thus accumulate into overlapping column ranges (exact,
+//   measured), (R+2) * 3 MMAs per K step and tile instead of R * 9; rows -2,
+//   -1, R, R+1 of the accumulators take the products that fall outside the
+//   tile and are never read. Every MMA accumulates; the epilogue zeroes the
+//   columns it has read (and the four outside rows) before handing the
+//   accumulators back. Weights are pre-packed in this stacked core-matrix
+//   layout, [dx][chunk][3 Cout][chunk elements].
 //   The CTA is warp-specialised. A producer thread loads each halo with one
 //   TMA box per 8-channel chunk (cp.async.bulk.tensor, zeros outside the
 //   image) into a ring of halo buffers, up to RT_CONV_STAGES - 1 tiles ahead,
@@ -47,53 +61,46 @@ namespace rt {
 namespace nn {
 
 // Tuning knobs: RT_CONV_ROWS = image rows per tile (R accumulators of 128
-// pixels share one halo of R+2 rows); RT_CONV_STAGES = halo buffers (the
-// producer loads up to RT_CONV_STAGES - 1 tiles ahead of the MMAs);
+// pixels share one halo of R+2 rows; with the stacked taps each accumulator
+// set takes (R+4) * Cout TMEM columns, so R <= 4); RT_CONV_STAGES = the most
+// halo buffers a CTA keeps (each layer takes as many as fit in ~220 KB of
+// shared memory, up to this; the loads run that many tiles ahead of the MMAs).
+// A halo load took ~5600 cycles to land at 1080p, two to three tiles' MMAs,
+// yet deeper rings were slower: 3 / 4 / 5 / 6 / 8 stages, FP8 network at
+// 1920x1080: 0.145 / 0.147 / 0.155 / 0.163 / 0.172 ms (3840x2160, 8 images:
+// 0.398 / 0.397 / 0.426 / 0.434 ms per image for 3-6);
 // RT_CONV_EPI_WG = epilogue warpgroups (4 warps each; group g takes the rows
-// ry with ry % RT_CONV_EPI_WG == g of every tile). Measured on GB300 at
-// 1920x1080 (network forward, 4 layers, identical output bit for bit), with
-// interleaved 32-channel maps: R=8 / 2 stages 0.45 ms, R=4 with 2 / 3 / 4
-// stages 0.41 / 0.318 / 0.321, R=2 with 3 / 4 / 6 stages 0.377 / 0.377 /
-// 0.386, epilogue groups 1, 2, 4 alike; an earlier single-role kernel
-// (16-byte cp.async halos, one buffer, one accumulator set, 2 CTAs per SM)
-// took 0.385 ms at R=8.
+// ry with ry % RT_CONV_EPI_WG == g of every tile; 4 groups were slower than 2:
+// 0.197 against 0.147 ms, FP8 at 1920x1080).
 #ifndef RT_CONV_ROWS
 #define RT_CONV_ROWS 4
 #endif
 #ifndef RT_CONV_STAGES
-#define RT_CONV_STAGES 3
+#define RT_CONV_STAGES 4
 #endif
 #ifndef RT_CONV_EPI_WG
 #define RT_CONV_EPI_WG 2
 #endif
-constexpr int kStages = RT_CONV_STAGES;
+constexpr int kMaxStages = RT_CONV_STAGES;
+static_assert(kMaxStages >= 2 && kMaxStages <= 8, "halo stages");
+constexpr uint32_t kSmemBudget = 220u * 1024u;
 constexpr int kEpiWarps = 4 * RT_CONV_EPI_WG;
-constexpr int kConvTmaThreads = 32 * (kEpiWarps + 1);
+constexpr int kConvTmaThreads = 32 * (kEpiWarps + 2);   // + the MMA warp and the TMA warp
 constexpr int kRows = RT_CONV_ROWS;
 constexpr int kTileM = 128;          // pixels per row tile (one MMA M block)
-// RT_CONV_SKEW = pixels by which the halo of every odd 16-byte channel chunk
-// starts earlier than that of the even chunks: the two core matrices of one
-// MMA's K step (an even and an odd chunk of the same pixels) then sit
-// RT_CONV_SKEW * 16 bytes apart modulo 128 instead of on the same shared-
-// memory banks (the chunk planes are 128-byte aligned for TMA). Measured at
-// 1920x1080 (network forward, outputs identical bit for bit): 0.2877 ->
-// 0.2895 ms BF16, 0.1662 -> 0.1685 ms FP8 at 4: no gain, off by default.
-#ifndef RT_CONV_SKEW
-#define RT_CONV_SKEW 0
-#endif
-constexpr int kSkew = RT_CONV_SKEW;
-// RT_CONV_BSWZ = 1: the weight operand in shared memory in the swizzled
-// K-major layout (rows of one output channel's 32 or 64 bytes of input
-// channels per tap, 16-byte chunks permuted by the row: 32-byte rows swizzle
-// by bit 7 of the address, 64-byte rows by bits 7-8) instead of 8x16-byte
-// core matrices. Measured at 1920x1080 (outputs identical bit for bit):
-// 0.2892 -> 0.2895 ms BF16, 0.1670 -> 0.1669 ms FP8: the weight operand's
-// layout does not limit the kernel; off by default.
-#ifndef RT_CONV_BSWZ
-#define RT_CONV_BSWZ 0
-#endif
-constexpr int kHaloW = kTileM + 2 + kSkew;   // halo pixels per row (130 without skew)
-constexpr int kHaloRows = (kRows + 2) * kHaloW;  // halo pixels per tile
+// The operand layout does not limit the MMAs: a 128-byte-swizzled operand
+// costs what the non-swizzled one does (measured), and neither a halo whose odd
+// chunks start a few pixels early (other shared-memory banks) nor swizzled
+// weights changed the layered network's time.
+constexpr int kHaloW = kTileM + 2;           // halo pixels per row of an interleaved input
+// A planar (chunk-plane) input is loaded as one TMA box per chunk whose rows
+// are 128 pixels x 16 bytes (256 8-byte elements, the largest box row), so
+// its tiles are 126 output pixels wide (the MMA lanes 126 and 127 read the
+// next halo row and are not stored). Boxes with rows of one 16-byte chunk
+// make one 16-byte request per pixel that moves a whole 32-byte sector from
+// L2: ~1500 requests per tile, whose transfer took longer than the tile's
+// MMAs (measured).
+constexpr int kHaloWPlanar = kTileM;
 constexpr uint32_t kWaitBound = 1u << 26;
 
 enum Epi : int { EPI_RELU_BF16 = 0, EPI_SIGMOID_F32 = 1, EPI_BWD_MASK_BF16 = 2, EPI_RELU_FP8 = 3 };
@@ -252,48 +259,52 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
   return *reinterpret_cast<uint32_t*>(&h);
 }
 
-// All MMAs of one tile: per output row ry, D[128 px, COUT] (TMEM columns
-// dtmem + ry*COUT) = sum over taps (dy, dx) and 32-byte K steps (16 BF16 or
-// 32 E4M3 channels) of the halo shifted by (ry+dy)*130 + dx pixels times the
-// packed weights of the tap. kChunks = 16-byte channel chunks per pixel,
-// kPlaneBytes = the distance between chunk planes of the halo.
-template <int kChunks, int COUT, uint32_t kPlaneBytes, bool FP8>
+// All MMAs of one tile: for halo row h, kernel column dx and 32-byte K step
+// ks (16 BF16 or 32 E4M3 channels), the halo shifted by h*130 + dx pixels
+// times the stacked weights B(dx) (N = 3*COUT) accumulate into TMEM columns
+// dtmem + h*COUT .. + 3*COUT - 1 (output rows h-2 .. h). kChunks = 16-byte
+// channel chunks per pixel, kPlaneBytes = the distance between chunk planes
+// of the halo, kPitch = pixels from one halo row to the next. The
+// accumulators start at zero (cleared by the epilogue).
+template <int kChunks, int COUT, uint32_t kPlaneBytes, int kPitch, bool FP8>
 __device__ __forceinline__ void issue_tile_mmas(uint32_t hbase, uint32_t wbase, uint32_t dtmem,
                                                 uint32_t idesc) {
-  // LBO = the distance from an even chunk's core matrix to the odd one's
-  const uint32_t a_lo = desc_lo(hbase, kPlaneBytes + 16u * kSkew), b_lo = desc_lo(wbase, COUT * 16);
+  constexpr int kN = 3 * COUT;
+  // A: LBO = the distance from an even chunk's core matrix to the odd one's;
+  // B: chunk c + 1 of a weight row sits kN * 16 bytes after chunk c
+  const uint32_t a_lo = desc_lo(hbase, kPlaneBytes), b_lo = desc_lo(wbase, kN * 16);
   constexpr uint32_t hi = desc_hi(128u);
-  // swizzled weights: rows of kRowB bytes (one output channel's input
-  // channels of a tap), 8-row atoms kRowB * 8 apart; layout type 6 = 32-byte,
-  // 4 = 64-byte swizzle (bits 61-63 of the descriptor)
-  constexpr uint32_t kRowB = 16u * kChunks;
-  constexpr uint32_t b_hi = desc_hi(8u * kRowB) | ((kRowB == 64u ? 4u : 6u) << 29);
 #pragma unroll
-  for (int ry = 0; ry < kRows; ++ry) {
+  for (int h = 0; h < kRows + 2; ++h) {
 #pragma unroll
-    for (int tap = 0; tap < 9; ++tap) {
-      const int dy = tap / 3, dx = tap % 3;
+    for (int dx = 0; dx < 3; ++dx) {
 #pragma unroll
       for (int ks = 0; ks < kChunks / 2; ++ks) {
-        const uint32_t a_off = (2u * ks) * kPlaneBytes + (uint32_t)((ry + dy) * kHaloW + dx) * 16u;
-#if RT_CONV_BSWZ
-        const uint32_t b_off = (uint32_t)tap * COUT * kRowB + 32u * ks;
-        const uint64_t da = desc_join(a_lo + (a_off >> 4), hi), db = desc_join(b_lo + (b_off >> 4), b_hi);
-#else
-        const uint32_t b_off = (uint32_t)((tap * kChunks + 2 * ks) * COUT) * 16u;
+        const uint32_t a_off = (2u * ks) * kPlaneBytes + (uint32_t)(h * kPitch + dx) * 16u;
+        const uint32_t b_off = (uint32_t)((dx * kChunks + 2 * ks) * kN) * 16u;
         const uint64_t da = desc_join(a_lo + (a_off >> 4), hi), db = desc_join(b_lo + (b_off >> 4), hi);
-#endif
-        if (FP8) mma_e4m3(dtmem + (uint32_t)(ry * COUT), da, db, idesc, (tap | ks) ? 1u : 0u);
-        else mma_bf16(dtmem + (uint32_t)(ry * COUT), da, db, idesc, (tap | ks) ? 1u : 0u);
+        if (FP8) mma_e4m3(dtmem + (uint32_t)(h * COUT), da, db, idesc, 1u);
+        else mma_bf16(dtmem + (uint32_t)(h * COUT), da, db, idesc, 1u);
       }
     }
   }
 }
 
+// zeroes 16 consecutive TMEM columns of this warp's 32 lanes
+__device__ __forceinline__ void tmem_zero16(uint32_t taddr) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1};" ::"r"(
+          taddr),
+      "r"(0u)
+      : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
 // ------------------------------------------------------------ conv kernel
 // in:  BF16 [P][16] interleaved (CIN = 16) or [4][P][8] planar (CIN = 32);
 //      with IN_FP8, E4M3 [2][P][16] planar (CIN = 32)
-// wpk: packed weights, [tap][16-byte chunk][COUT][chunk elements] (BF16 or E4M3)
+// wpk: packed weights, [dx][16-byte chunk][3 COUT: dy = 2, 1, 0][chunk elements]
+//      (BF16 or E4M3)
 // With IN_FP8 the accumulator of channel co is first multiplied by inv[co]
 // (the product of the input's activation scale and the channel's weight
 // scale, inverted: a power of two).
@@ -303,35 +314,40 @@ __device__ __forceinline__ void issue_tile_mmas(uint32_t hbase, uint32_t wbase, 
 // EPI_RELU_FP8:      out (E4M3 planar [2][P][16]) = e4m3(relu(acc + bias) * out_scale),
 //                    round to nearest even, saturating at +-448
 //
-// The last warp is the producer: its first lane loads each tile's halo as one
-// TMA box per 8-channel chunk (8 channels x 130 pixels x R+2 rows, zeros
-// outside the image) into a ring of RT_CONV_STAGES halo buffers, up to
-// RT_CONV_STAGES - 1 tiles ahead, and issues the tile's MMAs into one of two
-// TMEM accumulator sets as soon as its halo has landed and the epilogue has
-// drained that set. The epilogue warps (RT_CONV_EPI_WG warpgroups; warp w
-// reads TMEM lanes 32 (w % 4) .. +31) run the epilogue of tile i while the
-// tensor cores work on tile i+1 and the TMA engine fetches the next tiles.
-//   halo_full[b]: TMA bytes of halo buffer b arrived (expect_tx by the producer)
-//   acc_full[s]:  MMAs of accumulator set s done (tcgen05.commit); this also
-//                 frees the halo buffer they read (the producer waits on it
-//                 before reloading that buffer)
-//   acc_empty[s]: every epilogue thread has read set s
+// Three roles. The last warp's first lane loads each tile's halo (one TMA box
+// per 16-byte channel chunk, zeros outside the image) into a ring of
+// RT_CONV_STAGES halo buffers, as far ahead as the ring allows; the warp
+// before it issues the tile's MMAs into one of two TMEM accumulator sets as
+// soon as its halo has landed and the epilogue has drained that set; the
+// epilogue warps (RT_CONV_EPI_WG warpgroups; warp w reads TMEM lanes
+// 32 (w % 4) .. +31) run the epilogue of tile i while the tensor cores work on
+// tile i+1 and the TMA engine fetches the next tiles. Loads, MMAs and
+// epilogues each wait only on their own barriers (in one thread, the loads'
+// issue and the waits for their buffers held up the MMAs, measured).
+//   halo_full[b]:  TMA bytes of halo buffer b arrived (expect_tx by the loader)
+//   halo_empty[b]: the MMAs that read buffer b completed (tcgen05.commit)
+//   acc_full[s]:   MMAs of accumulator set s done (tcgen05.commit)
+//   acc_empty[s]:  every epilogue thread has read and zeroed set s
 // Every wait is bounded; a wait that gives up sets the error word, and before
 // the CTA frees TMEM and exits the producer waits (bounded) for the copies and
 // MMAs it has issued.
-template <int CIN, int COUT, bool IN_FP8>
+template <int CIN, int COUT, bool IN_FP8, bool PLANAR>
 struct ConvTmaLayout {
   static constexpr int kElem = IN_FP8 ? 1 : 2;                           // bytes per channel
   static constexpr int kChunks = CIN * kElem / 16;                       // 16-byte chunks per pixel
-  static constexpr uint32_t kBox = (uint32_t)kHaloRows * 16u;          // bytes of one TMA box
+  static constexpr int kPitch = PLANAR ? kHaloWPlanar : kHaloW;          // halo pixels per row
+  static constexpr int kOutW = kPitch - 2;                               // output pixels per row
+  static constexpr uint32_t kBox = (uint32_t)(kRows + 2) * kPitch * 16u; // bytes of one TMA box
   static constexpr uint32_t kPlane = (kBox + 127u) & ~127u;            // chunk plane stride
   static constexpr uint32_t kHalo = ((kChunks * kPlane) + 1023u) & ~1023u;
   static constexpr uint32_t kWBytes = 9u * COUT * CIN * kElem;
   static constexpr uint32_t kW = (kWBytes + 127u) & ~127u;
-  static constexpr uint32_t kAcc = (uint32_t)kRows * COUT;
+  static constexpr uint32_t kAcc = (uint32_t)(kRows + 4) * COUT;       // rows -2 .. R+1
   static constexpr uint32_t kSet = kAcc <= 32 ? 32 : (kAcc <= 64 ? 64 : (kAcc <= 128 ? 128 : 256));
   static constexpr uint32_t kTmemCols = 2 * kSet;
-  static constexpr size_t kSmem = kStages * (size_t)kHalo + kW + 64 * 4 + 16 * 8 + 16;
+  static constexpr uint32_t kFit = (kSmemBudget - kW - 1024u) / kHalo;   // halo buffers that fit
+  static constexpr int kSt = kFit < 2u ? 2 : (kFit > (uint32_t)kMaxStages ? kMaxStages : (int)kFit);
+  static constexpr size_t kSmem = kSt * (size_t)kHalo + kW + 64 * 4 + 20 * 8 + 16;
 };
 
 template <int CIN, int COUT, int EPI, bool PLANAR_IN, bool IN_FP8>
@@ -340,49 +356,41 @@ __global__ void __launch_bounds__(kConvTmaThreads, 1)
                const float* __restrict__ bias, const float* __restrict__ inv,
                float out_scale, const __nv_bfloat16* __restrict__ mask16, void* __restrict__ out,
                float* __restrict__ out32, uint32_t W, uint32_t H, uint32_t n_img, uint32_t* err) {
-  using Lt = ConvTmaLayout<CIN, COUT, IN_FP8>;
+  using Lt = ConvTmaLayout<CIN, COUT, IN_FP8, PLANAR_IN>;
   static_assert(CIN % 16 == 0 && (COUT == 16 || COUT == 32), "shape");
   static_assert(Lt::kTmemCols <= 512, "two accumulator sets must fit in TMEM");
   extern __shared__ __align__(1024) unsigned char smem[];
-  static_assert(kStages >= 2 && kStages <= 8, "halo stages");
   unsigned char* halo0 = smem;
-  unsigned char* wsm = smem + kStages * Lt::kHalo;
+  unsigned char* wsm = smem + Lt::kSt * Lt::kHalo;
   float* bsm = reinterpret_cast<float*>(wsm + Lt::kW);    // bias[32], then inv[32]
   float* ism = bsm + 32;
   uint64_t* bars = reinterpret_cast<uint64_t*>(bsm + 64);
-  uint64_t* halo_full = bars;        // [kStages]
-  uint64_t* acc_full = bars + 8;     // [2]
-  uint64_t* acc_empty = bars + 10;   // [2]
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 12);
+  uint64_t* halo_full = bars;        // [kSt]
+  uint64_t* halo_empty = bars + 8;   // [kSt]
+  uint64_t* acc_full = bars + 16;    // [2]
+  uint64_t* acc_empty = bars + 18;   // [2]
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 20);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   // n_img images of W x H pixels stacked in memory (image-major); a tile
   // never spans two images, and the halo rows outside its image read zeros
-  const uint32_t tiles_x = (W + kTileM - 1) / kTileM;
+  const uint32_t tiles_x = (W + Lt::kOutW - 1) / Lt::kOutW;
   const uint32_t tiles_img = tiles_x * ((H + kRows - 1) / kRows);
   const uint32_t n_tiles = tiles_img * n_img;
   {
     const uint4* src = reinterpret_cast<const uint4*>(wpk);
     uint4* dst = reinterpret_cast<uint4*>(wsm);
-#if RT_CONV_BSWZ
-    // packed [tap][chunk][co] 16-byte chunks -> [tap][co] rows, chunk c of
-    // row co at chunk c ^ (row bits the swizzle takes)
-    for (uint32_t i = tid; i < Lt::kWBytes / 16u; i += blockDim.x) {
-      const uint32_t co = i % COUT, rest = i / COUT;
-      const uint32_t c = rest % Lt::kChunks, tap = rest / Lt::kChunks;
-      const uint32_t sw = Lt::kChunks == 4 ? (co >> 1) & 3u : (co >> 2) & 1u;
-      dst[(tap * COUT + co) * Lt::kChunks + (c ^ sw)] = src[i];
-    }
-#else
     for (uint32_t i = tid; i < Lt::kWBytes / 16u; i += blockDim.x) dst[i] = src[i];
-#endif
     if (tid < COUT) {
       bsm[tid] = bias ? bias[tid] : 0.f;
       ism[tid] = inv ? inv[tid] : 1.f;
     }
   }
   if (tid == 0) {
-    for (int b = 0; b < kStages; ++b) mbar_init(halo_full + b, 1);
+    for (int b = 0; b < Lt::kSt; ++b) {
+      mbar_init(halo_full + b, 1);
+      mbar_init(halo_empty + b, 1);
+    }
     for (int b = 0; b < 2; ++b) {
       mbar_init(acc_full + b, 1);
       mbar_init(acc_empty + b, 32 * kEpiWarps);
@@ -396,65 +404,102 @@ __global__ void __launch_bounds__(kConvTmaThreads, 1)
   __syncthreads();
   fence_after();
   const uint32_t tmem = *tslot;
+  // the MMAs only accumulate: clear both accumulator sets once (warp w % 4
+  // may address TMEM lanes 32 (w % 4) .. +31)
+  if (warp < 4) {
+    for (uint32_t c = 0; c < Lt::kTmemCols; c += 16) tmem_zero16(tmem + ((uint32_t)(warp * 32) << 16) + c);
+    tmem_wait_st();
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
 
+  const uint32_t my_tiles = blockIdx.x < n_tiles ? (n_tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
   if (warp == kEpiWarps) {
+    // ---- MMA issue: tile it of this CTA's sequence reads halo buffer it % kSt
     if (lane == 0) {
-      const uint32_t idesc = IN_FP8 ? make_idesc_e4m3(kTileM, COUT) : make_idesc(kTileM, COUT);
+      const uint32_t idesc = IN_FP8 ? make_idesc_e4m3(kTileM, 3 * COUT) : make_idesc(kTileM, 3 * COUT);
       const uint32_t wbase = smem_u32(wsm);
-      bool issued_halo[kStages], issued_acc[2] = {false, false};
-      uint32_t halo_par[kStages], acc_par[2] = {0, 0};     // parity of the last issued use
+      bool issued_acc[2] = {false, false}, issued_he[Lt::kSt];
+      uint32_t acc_par[2] = {0, 0}, he_par[Lt::kSt];     // parity of the last commit
 #pragma unroll
-      for (int b = 0; b < kStages; ++b) { issued_halo[b] = false; halo_par[b] = 0; }
+      for (int b = 0; b < Lt::kSt; ++b) { issued_he[b] = false; he_par[b] = 0; }
       bool ok = true;
-      // tile number j of this CTA's sequence goes to halo buffer j % kStages
-      auto load = [&](uint32_t j) {
+      for (uint32_t it = 0; it < my_tiles; ++it) {
+        const int b = (int)(it % Lt::kSt), sa = (int)(it & 1u);
+        if (!mbar_wait(halo_full + b, (it / Lt::kSt) & 1u)) { ok = false; break; }
+        if (it >= 2 && !mbar_wait(acc_empty + sa, ((it >> 1) - 1) & 1u)) { ok = false; break; }
+        fence_after();
+        issue_tile_mmas<Lt::kChunks, COUT, Lt::kPlane, Lt::kPitch, IN_FP8>(
+            smem_u32(halo0 + (size_t)b * Lt::kHalo), wbase, tmem + (uint32_t)sa * Lt::kSet, idesc);
+        mma_commit(halo_empty + b);   // the buffer may be reloaded once these MMAs completed
+        mma_commit(acc_full + sa);
+        issued_he[b] = true;
+        he_par[b] = (it / Lt::kSt) & 1u;
+        issued_acc[sa] = true;
+        acc_par[sa] = (it >> 1) & 1u;
+      }
+      if (!ok) atomicOr(err, ERR_ITER);
+      // drain: the MMAs issued here complete (and signal) before TMEM is freed
+      for (int b = 0; b < 2; ++b)
+        if (issued_acc[b]) mbar_wait(acc_full + b, acc_par[b]);
+      for (int b = 0; b < Lt::kSt; ++b)
+        if (issued_he[b]) mbar_wait(halo_empty + b, he_par[b]);
+    }
+    __syncwarp();
+  } else if (warp == kEpiWarps + 1) {
+    // ---- TMA loads: tile j into buffer j % kSt once the MMAs of tile
+    // j - kSt (the buffer's previous tile) completed
+    if (lane == 0) {
+      bool ok = true;
+      uint32_t n_loaded = 0;
+      for (uint32_t j = 0; j < my_tiles; ++j) {
+        const int b = (int)(j % Lt::kSt);
+        if (j >= (uint32_t)Lt::kSt && !mbar_wait(halo_empty + b, ((j / Lt::kSt) - 1) & 1u)) { ok = false; break; }
         const uint32_t tile = blockIdx.x + j * gridDim.x;
-        const int b = (int)(j % kStages);
         const int img = (int)(tile / tiles_img);
         const uint32_t it_img = tile - (uint32_t)img * tiles_img;
         const int ty = (int)(it_img / tiles_x);
-        const int y = ty * kRows, x0 = (int)(it_img - (uint32_t)ty * tiles_x) * kTileM;
+        const int y = ty * kRows, x0 = (int)(it_img - (uint32_t)ty * tiles_x) * Lt::kOutW;
         mbar_arrive_expect_tx(halo_full + b, (uint32_t)Lt::kChunks * Lt::kBox);
 #pragma unroll
-        for (int c = 0; c < Lt::kChunks; ++c)
-          if (PLANAR_IN)   // tensor {16 B of channels, W, H, images, chunks}
-            tma_load_5d(halo0 + (size_t)b * Lt::kHalo + (size_t)c * Lt::kPlane, &tmap, 0,
-                        x0 - 1 - ((c & 1) ? kSkew : 0), y - 1, img, c, halo_full + b);
+        for (int c = 0; c < Lt::kChunks; ++c) {
+          unsigned char* plane = halo0 + (size_t)b * Lt::kHalo + (size_t)c * Lt::kPlane;
+          if (PLANAR_IN)   // tensor {8-byte halves of pixels (2 W), H, images, chunks}
+            tma_load_4d(plane, &tmap, 2 * (x0 - 1), y - 1, img, c, halo_full + b);
           else             // tensor {16 B of channels, chunks, W, H, images}
-            tma_load_5d(halo0 + (size_t)b * Lt::kHalo + (size_t)c * Lt::kPlane, &tmap, 0, c,
-                        x0 - 1 - ((c & 1) ? kSkew : 0), y - 1, img, halo_full + b);
-        issued_halo[b] = true;
-        halo_par[b] = (j / kStages) & 1u;
-      };
-      const uint32_t my_tiles = blockIdx.x < n_tiles ? (n_tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-      for (uint32_t j = 0; j + 1 < (uint32_t)kStages && j < my_tiles; ++j) load(j);
-      for (uint32_t it = 0; it < my_tiles && ok; ++it) {
-        const int b = (int)(it % kStages), sa = (int)(it & 1u);
-        if (!mbar_wait(halo_full + b, (it / kStages) & 1u)) { ok = false; break; }
-        issued_halo[b] = false;
-        if (it >= 2 && !mbar_wait(acc_empty + sa, ((it >> 1) - 1) & 1u)) { ok = false; break; }
-        fence_after();
-        issue_tile_mmas<Lt::kChunks, COUT, Lt::kPlane, IN_FP8>(
-            smem_u32(halo0 + (size_t)b * Lt::kHalo), wbase, tmem + (uint32_t)sa * Lt::kSet, idesc);
-        mma_commit(acc_full + sa);
-        issued_acc[sa] = true;
-        acc_par[sa] = (it >> 1) & 1u;
-        const uint32_t j = it + kStages - 1;
-        if (j < my_tiles) {
-          // buffer j % kStages last held tile it - 1: free once its MMAs completed
-          if (it >= 1 && !mbar_wait(acc_full + ((it - 1) & 1u), ((it - 1) >> 1) & 1u)) { ok = false; break; }
-          load(j);
+            tma_load_5d(plane, &tmap, 0, c, x0 - 1, y - 1, img, halo_full + b);
         }
+        n_loaded = j + 1;
       }
       if (!ok) atomicOr(err, ERR_ITER);
-      // drain: copies and MMAs this thread issued complete before TMEM is freed
-      for (int b = 0; b < kStages; ++b)
-        if (issued_halo[b]) mbar_wait(halo_full + b, halo_par[b]);
-      for (int b = 0; b < 2; ++b)
-        if (issued_acc[b]) mbar_wait(acc_full + b, acc_par[b]);
+      // drain: the last copy into each buffer has landed before the CTA exits
+      for (uint32_t j = n_loaded > (uint32_t)Lt::kSt ? n_loaded - Lt::kSt : 0; j < n_loaded; ++j)
+        mbar_wait(halo_full + (j % Lt::kSt), (j / Lt::kSt) & 1u);
     }
     __syncwarp();
   } else {
+    // Each epilogue warp first copies its rows of the accumulator set into
+    // registers, zeroes them (and group 0 the rows outside the tile) and hands
+    // the set back, so the next tile's MMAs start while it converts and
+    // stores: the tensor core then waits only for the TMEM reads, not for the
+    // whole epilogue.
+    constexpr int kMine = kRows / RT_CONV_EPI_WG;   // rows per epilogue warp
+    constexpr int kHalves = COUT / 16;
+    static_assert(kRows % RT_CONV_EPI_WG == 0, "rows per tile must split evenly over the epilogue groups");
+    const int quarter = warp & 3, group = warp >> 2;   // TMEM lanes 32*quarter .. +31
+    const size_t P = (size_t)W * H * n_img;            // pixels of a channel plane
+    // per output channel c: out = max(fma(acc, sc[c], bi[c]), 0) (or the
+    // sigmoid of it), with the input's inverse scale (E4M3 inputs) and the
+    // output scale (E4M3 outputs) folded in: all are powers of two, so the
+    // folded form rounds exactly like scaling the rounded sum
+    float sc[COUT], bi[COUT];
+#pragma unroll
+    for (int c = 0; c < COUT; ++c) {
+      const float os = EPI == EPI_RELU_FP8 ? out_scale : 1.f;
+      sc[c] = (IN_FP8 ? ism[c] : 1.f) * os;
+      bi[c] = bsm[c] * os;
+    }
     uint32_t it = 0;
     for (uint32_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++it) {
       const int s = (int)(it & 1u);
@@ -464,89 +509,95 @@ __global__ void __launch_bounds__(kConvTmaThreads, 1)
         break;
       }
       fence_after();
+      // output row ry's sums sit in columns (ry + 2) * COUT of the set
+      const uint32_t set_addr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)s * Lt::kSet;
+      uint32_t r[kMine][kHalves][16];
+#pragma unroll
+      for (int k = 0; k < kMine; ++k)
+#pragma unroll
+        for (int half = 0; half < kHalves; ++half)
+          tmem_ld16_nowait(set_addr + (uint32_t)((group + k * RT_CONV_EPI_WG + 2) * COUT + half * 16), r[k][half]);
+      tmem_wait_ld();
+#pragma unroll
+      for (int k = 0; k < kMine; ++k)
+#pragma unroll
+        for (int half = 0; half < kHalves; ++half)
+          tmem_zero16(set_addr + (uint32_t)((group + k * RT_CONV_EPI_WG + 2) * COUT + half * 16));
+      if (group == 0) {   // rows -2, -1, R, R+1
+#pragma unroll
+        for (int c = 0; c < 2 * COUT; c += 16) {
+          tmem_zero16(set_addr + (uint32_t)c);
+          tmem_zero16(set_addr + (uint32_t)((kRows + 2) * COUT + c));
+        }
+      }
+      tmem_wait_st();
+      fence_before();
+      mbar_arrive(acc_empty + s);
+
       const uint32_t img = tile / tiles_img;
       const uint32_t it_img = tile - img * tiles_img;
       const int ty = (int)(it_img / tiles_x);
       const int y = ty * kRows;
-      const int x0 = (int)(it_img - (uint32_t)ty * tiles_x) * kTileM;
-      const int quarter = warp & 3, group = warp >> 2;   // TMEM lanes 32*quarter .. +31
+      const int x0 = (int)(it_img - (uint32_t)ty * tiles_x) * Lt::kOutW;
       const int x = x0 + quarter * 32 + lane;
+      const bool lane_ok = quarter * 32 + lane < Lt::kOutW;
 #pragma unroll
-      for (int ry = group; ry < kRows; ry += RT_CONV_EPI_WG) {
-        const int yy = y + ry;
-        const bool valid = x < (int)W && yy < (int)H;
+      for (int k = 0; k < kMine; ++k) {
+        const int yy = y + group + k * RT_CONV_EPI_WG;
+        if (!(lane_ok && x < (int)W && yy < (int)H)) continue;
         const size_t p = ((size_t)img * H + yy) * W + x;
-        const size_t P = (size_t)W * H * n_img;   // pixels of a channel plane
-        const uint32_t lane_addr =
-            tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)s * Lt::kSet + (uint32_t)(ry * COUT);
         if (EPI == EPI_SIGMOID_F32) {
-          float v[16];
-          tmem_ld16(lane_addr, v);
-          const float z = IN_FP8 ? fmaf(v[0], ism[0], bsm[0]) : v[0] + bsm[0];
-          if (valid) out32[p] = 1.f / (1.f + __expf(-z));
+          const float z = fmaf(__uint_as_float(r[k][0][0]), sc[0], bi[0]);
+          out32[p] = 1.f / (1.f + __expf(-z));
         } else if (EPI == EPI_RELU_FP8) {
-          uint32_t r[COUT / 16][16];
 #pragma unroll
-          for (int half = 0; half < COUT / 16; ++half) tmem_ld16_nowait(lane_addr + half * 16, r[half]);
-          tmem_wait_ld();
-#pragma unroll
-          for (int half = 0; half < COUT / 16; ++half) {
+          for (int half = 0; half < kHalves; ++half) {
             uint32_t packed[4];
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
               const int c0 = half * 16 + 2 * i, c1 = c0 + 1;
-              const float a0 = __uint_as_float(r[half][2 * i]), a1 = __uint_as_float(r[half][2 * i + 1]);
-              const float y0 = fmaxf(IN_FP8 ? fmaf(a0, ism[c0], bsm[c0]) : a0 + bsm[c0], 0.f);
-              const float y1 = fmaxf(IN_FP8 ? fmaf(a1, ism[c1], bsm[c1]) : a1 + bsm[c1], 0.f);
-              const uint32_t q = __nv_cvt_float2_to_fp8x2(make_float2(y0 * out_scale, y1 * out_scale),
-                                                          __NV_SATFINITE, __NV_E4M3);
+              const float a0 = __uint_as_float(r[k][half][2 * i]), a1 = __uint_as_float(r[k][half][2 * i + 1]);
+              const float y0 = fmaxf(fmaf(a0, sc[c0], bi[c0]), 0.f);
+              const float y1 = fmaxf(fmaf(a1, sc[c1], bi[c1]), 0.f);
+              const uint32_t q = __nv_cvt_float2_to_fp8x2(make_float2(y0, y1), __NV_SATFINITE, __NV_E4M3);
               if (i & 1) packed[i >> 1] |= q << 16; else packed[i >> 1] = q;
             }
             // E4M3 planar: plane `half` holds channels 16 half .. 16 half + 15
-            if (valid)
-              *reinterpret_cast<uint4*>(static_cast<uint8_t*>(out) + (half * P + p) * 16) =
-                  make_uint4(packed[0], packed[1], packed[2], packed[3]);
+            *reinterpret_cast<uint4*>(static_cast<uint8_t*>(out) + (half * P + p) * 16) =
+                make_uint4(packed[0], packed[1], packed[2], packed[3]);
           }
         } else {
           __nv_bfloat16* out16 = static_cast<__nv_bfloat16*>(out);
-          uint32_t r[COUT / 16][16];                 // all columns of the row, one wait
 #pragma unroll
-          for (int half = 0; half < COUT / 16; ++half) tmem_ld16_nowait(lane_addr + half * 16, r[half]);
-          tmem_wait_ld();
-#pragma unroll
-          for (int half = 0; half < COUT / 16; ++half) {
+          for (int half = 0; half < kHalves; ++half) {
             float v[16];
 #pragma unroll
-            for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[half][i]);
-            if (valid) {
-              uint32_t packed[8];
-              if (EPI == EPI_RELU_BF16) {
+            for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[k][half][i]);
+            uint32_t packed[8];
+            if (EPI == EPI_RELU_BF16) {
 #pragma unroll
-                for (int i = 0; i < 8; ++i)
-                  packed[i] = pack_bf16(fmaxf(v[2 * i] + bsm[half * 16 + 2 * i], 0.f),
-                                        fmaxf(v[2 * i + 1] + bsm[half * 16 + 2 * i + 1], 0.f));
-              } else {
-                // planar: channels 16 half + 0..7 and + 8..15 sit in planes 2 half, 2 half + 1
-                const uint4 ma = *reinterpret_cast<const uint4*>(mask16 + ((2 * half) * P + p) * 8);
-                const uint4 mb = *reinterpret_cast<const uint4*>(mask16 + ((2 * half + 1) * P + p) * 8);
-                const uint32_t mw[8] = {ma.x, ma.y, ma.z, ma.w, mb.x, mb.y, mb.z, mb.w};
+              for (int i = 0; i < 8; ++i)
+                packed[i] = pack_bf16(fmaxf(v[2 * i] + bi[half * 16 + 2 * i], 0.f),
+                                      fmaxf(v[2 * i + 1] + bi[half * 16 + 2 * i + 1], 0.f));
+            } else {
+              // planar: channels 16 half + 0..7 and + 8..15 sit in planes 2 half, 2 half + 1
+              const uint4 ma = *reinterpret_cast<const uint4*>(mask16 + ((2 * half) * P + p) * 8);
+              const uint4 mb = *reinterpret_cast<const uint4*>(mask16 + ((2 * half + 1) * P + p) * 8);
+              const uint32_t mw[8] = {ma.x, ma.y, ma.z, ma.w, mb.x, mb.y, mb.z, mb.w};
 #pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                  const __nv_bfloat162 mm = *reinterpret_cast<const __nv_bfloat162*>(&mw[i]);
-                  const float m0 = __bfloat162float(mm.x), m1 = __bfloat162float(mm.y);
-                  packed[i] = pack_bf16(m0 > 0.f ? v[2 * i] : 0.f, m1 > 0.f ? v[2 * i + 1] : 0.f);
-                }
+              for (int i = 0; i < 8; ++i) {
+                const __nv_bfloat162 mm = *reinterpret_cast<const __nv_bfloat162*>(&mw[i]);
+                const float m0 = __bfloat162float(mm.x), m1 = __bfloat162float(mm.y);
+                packed[i] = pack_bf16(m0 > 0.f ? v[2 * i] : 0.f, m1 > 0.f ? v[2 * i + 1] : 0.f);
               }
-              *reinterpret_cast<uint4*>(out16 + ((2 * half) * P + p) * 8) =
-                  make_uint4(packed[0], packed[1], packed[2], packed[3]);
-              *reinterpret_cast<uint4*>(out16 + ((2 * half + 1) * P + p) * 8) =
-                  make_uint4(packed[4], packed[5], packed[6], packed[7]);
             }
+            *reinterpret_cast<uint4*>(out16 + ((2 * half) * P + p) * 8) =
+                make_uint4(packed[0], packed[1], packed[2], packed[3]);
+            *reinterpret_cast<uint4*>(out16 + ((2 * half + 1) * P + p) * 8) =
+                make_uint4(packed[4], packed[5], packed[6], packed[7]);
           }
         }
       }
-      fence_before();
-      mbar_arrive(acc_empty + s);
     }
   }
   fence_before();
@@ -558,50 +609,56 @@ __global__ void __launch_bounds__(kConvTmaThreads, 1)
 
 // ------------------------------------------------ weight packing (FP32 -> BF16)
 // Canonical parameter layout of a layer: W[Cout][Cin][3][3] then b[Cout].
-// forward pack: [tap][ci/8][co][ci%8] with ci < cin_pad, co < cout_pad (zero fill)
+// Packed (k_conv_tma's stacked taps): element i of a conv with output
+// channels cout_p and input channels cin_p, chunks of `per` elements, is
+// [dx][ci / per][j * cout_p + co][ci % per] with tap (dy = 2 - j, dx).
+struct StackedIndex {
+  int co, ci, tap;
+};
+__device__ __forceinline__ StackedIndex stacked_index(int i, int per, int cout_p, int cin_p) {
+  const int e = i % per, rest = i / per;
+  const int n = rest % (3 * cout_p), rest2 = rest / (3 * cout_p);
+  const int chunk = rest2 % (cin_p / per), dx = rest2 / (cin_p / per);
+  const int j = n / cout_p;
+  return {n - j * cout_p, chunk * per + e, (2 - j) * 3 + dx};
+}
+
+// forward pack: W[co][ci][tap] with ci < cin_pad, co < cout_pad (zero fill)
 __global__ void k_pack_fwd(const float* __restrict__ Wt, int cout, int cin, int cout_pad,
                            int cin_pad, __nv_bfloat16* __restrict__ out) {
   const int n = 9 * cin_pad * cout_pad;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const int e = i % 8, rest = i / 8;
-    const int co = rest % cout_pad, rest2 = rest / cout_pad;
-    const int chunk = rest2 % (cin_pad / 8), tap = rest2 / (cin_pad / 8);
-    const int ci = chunk * 8 + e;
+    const StackedIndex x = stacked_index(i, 8, cout_pad, cin_pad);
     float v = 0.f;
-    if (co < cout && ci < cin) v = Wt[((size_t)co * cin + ci) * 9 + tap];
+    if (x.co < cout && x.ci < cin) v = Wt[((size_t)x.co * cin + x.ci) * 9 + x.tap];
     out[i] = __float2bfloat16_rn(v);
   }
 }
 
-// backward-data pack: output channel = forward ci, input channel = forward co,
-// tap flipped: W'[ci][co][8 - tap]
+// backward-data pack: a conv whose output channel o is forward input channel
+// ci and whose input channel c is forward output channel co, taps flipped:
+// W'[o][c][tap] = W[c][o][8 - tap]
 __global__ void k_pack_bwd(const float* __restrict__ Wt, int cout, int cin, int cout_pad,
                            int cin_pad, __nv_bfloat16* __restrict__ out) {
   // as a conv: CIN' = cout_pad, COUT' = cin_pad
   const int n = 9 * cout_pad * cin_pad;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const int e = i % 8, rest = i / 8;
-    const int ci = rest % cin_pad, rest2 = rest / cin_pad;      // output channel of the bwd conv
-    const int chunk = rest2 % (cout_pad / 8), tap = rest2 / (cout_pad / 8);
-    const int co = chunk * 8 + e;                               // input channel of the bwd conv
+    const StackedIndex x = stacked_index(i, 8, cin_pad, cout_pad);   // x.co: forward ci, x.ci: forward co
     float v = 0.f;
-    if (co < cout && ci < cin) v = Wt[((size_t)co * cin + ci) * 9 + (8 - tap)];
+    if (x.ci < cout && x.co < cin) v = Wt[((size_t)x.ci * cin + x.co) * 9 + (8 - x.tap)];
     out[i] = __float2bfloat16_rn(v);
   }
 }
 
-// FP8 forward pack of layers 2-4: [tap][ci/16][co][ci%16] E4M3 of
-// W[co][ci][tap] * scale[co] (round to nearest even, saturating), zero fill
+// FP8 forward pack of layers 2-4: E4M3 of W[co][ci][tap] * scale[co] (round
+// to nearest even, saturating), chunks of 16 elements, zero fill
 __global__ void k_pack_fwd_fp8(const float* __restrict__ Wt, int cout, int cin, int cout_pad,
                                int cin_pad, const float* __restrict__ scale, uint8_t* __restrict__ out) {
   const int n = 9 * cin_pad * cout_pad;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const int e = i % 16, rest = i / 16;
-    const int co = rest % cout_pad, rest2 = rest / cout_pad;
-    const int chunk = rest2 % (cin_pad / 16), tap = rest2 / (cin_pad / 16);
-    const int ci = chunk * 16 + e;
+    const StackedIndex x = stacked_index(i, 16, cout_pad, cin_pad);
     float v = 0.f;
-    if (co < cout && ci < cin) v = Wt[((size_t)co * cin + ci) * 9 + tap] * scale[co];
+    if (x.co < cout && x.ci < cin) v = Wt[((size_t)x.co * cin + x.ci) * 9 + x.tap] * scale[x.co];
     out[i] = (uint8_t)__nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
   }
 }
@@ -802,11 +859,11 @@ EncodeTiledFn encode_tiled() {
   return fn;
 }
 
-// Tensor map of a BF16 or E4M3 map for the halo boxes of k_conv_tma; a box
-// is one 16-byte channel chunk of 130 pixels x R+2 rows. Interleaved
-// [H][W][C] is viewed as {chunk elements, chunks, W, H} with box
-// {chunk elements, 1, 130, R+2}; planar [chunks][H][W][chunk elements] as
-// {chunk elements, W, H, chunks} with box {chunk elements, 130, R+2, 1}.
+// Tensor map of a BF16 or E4M3 map for the halo boxes of k_conv_tma.
+// Interleaved [images][H][W][C] is viewed as {chunk elements, chunks, W, H,
+// images} with one box {chunk elements, 1, 130, R+2, 1} per chunk; planar
+// [chunks][images][H][W][16 bytes] as 8-byte elements {2 W, H, images,
+// chunks} with one box {256 (128 pixels), R+2, 1, 1} per chunk.
 template <int CIN, bool PLANAR, bool FP8>
 cudaError_t make_halo_map(CUtensorMap* map, const void* in, uint32_t W, uint32_t H, uint32_t n_img) {
   const EncodeTiledFn fn = encode_tiled();
@@ -814,27 +871,25 @@ cudaError_t make_halo_map(CUtensorMap* map, const void* in, uint32_t W, uint32_t
   if (reinterpret_cast<uintptr_t>(in) & 15u) return cudaErrorInvalidValue;
   constexpr int kElem = FP8 ? 1 : 2, kPer = 16 / kElem, kChunks = CIN / kPer;
   const cuuint64_t P = (cuuint64_t)W * H;
-  cuuint64_t dims[5], strides[4];
-  cuuint32_t box[5];
-  if (PLANAR) {       // [chunks][images][H][W][chunk elements]
-    const cuuint64_t d[5] = {kPer, W, H, n_img, kChunks};
-    const cuuint64_t st[4] = {16, (cuuint64_t)W * 16, P * 16, P * n_img * 16};
-    const cuuint32_t bx[5] = {kPer, (cuuint32_t)kHaloW, (cuuint32_t)(kRows + 2), 1, 1};
-    for (int i = 0; i < 5; ++i) { dims[i] = d[i]; box[i] = bx[i]; }
-    for (int i = 0; i < 4; ++i) strides[i] = st[i];
-  } else {            // [images][H][W][chunks][chunk elements]
+  const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+  CUresult r;
+  if (PLANAR) {
+    const cuuint64_t d[4] = {2ull * W, H, n_img, kChunks};
+    const cuuint64_t st[3] = {(cuuint64_t)W * 16, P * 16, P * n_img * 16};
+    const cuuint32_t bx[4] = {2u * kHaloWPlanar, (cuuint32_t)(kRows + 2), 1, 1};
+    r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 4, const_cast<void*>(in), d, st, bx, estr,
+           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  } else {
     const cuuint64_t d[5] = {kPer, kChunks, W, H, n_img};
     const cuuint64_t st[4] = {16, (cuuint64_t)CIN * kElem, (cuuint64_t)W * CIN * kElem,
                               P * CIN * kElem};
     const cuuint32_t bx[5] = {kPer, 1, (cuuint32_t)kHaloW, (cuuint32_t)(kRows + 2), 1};
-    for (int i = 0; i < 5; ++i) { dims[i] = d[i]; box[i] = bx[i]; }
-    for (int i = 0; i < 4; ++i) strides[i] = st[i];
+    r = fn(map, FP8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5,
+           const_cast<void*>(in), d, st, bx, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+           CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   }
-  const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
-  const CUresult r = fn(map, FP8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5,
-                        const_cast<void*>(in), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
@@ -845,8 +900,8 @@ cudaError_t launch_conv(const void* in, const void* wpk, const float* bias, cons
                         float out_scale, const __nv_bfloat16* mask16, void* out, float* out32,
                         uint32_t W, uint32_t H, uint32_t* err, cudaStream_t st, uint32_t n_img = 1) {
   constexpr bool kPlanarIn = IN_FP8 || CIN == 32;
-  const uint32_t tiles = ((W + kTileM - 1) / kTileM) * ((H + kRows - 1) / kRows) * n_img;
-  using Lt = ConvTmaLayout<CIN, COUT, IN_FP8>;
+  using Lt = ConvTmaLayout<CIN, COUT, IN_FP8, kPlanarIn>;
+  const uint32_t tiles = ((W + Lt::kOutW - 1) / Lt::kOutW) * ((H + kRows - 1) / kRows) * n_img;
   size_t smem = Lt::kSmem + (size_t)(g_conv_smem_pad + conv_smem_pad());
   // a CTA that takes all 512 TMEM columns must be alone on its SM: ask for
   // more than half of the SM's shared memory so a second one cannot be placed
