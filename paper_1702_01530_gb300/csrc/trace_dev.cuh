@@ -79,15 +79,16 @@ constexpr int kMaxTopBytes = 85 * 7 * 16;
 // match, and pixel positions by multiplication with host-computed scales
 // instead of two divisions per primary ray: 1.050 -> 1.020 ms per 1080p blob
 // pair, 0.222 -> 0.214 ms for the 10-primitive scene; on by default
-// RT_PRIMARY_STORE = 1: a pixel's primary ray stores its contribution
-// (store_first) and the colour sums are not cleared before a render; 0: every
-// contribution is an atomic add onto sums cleared by a memset.
-#ifndef RT_PRIMARY_STORE
-#define RT_PRIMARY_STORE 1
-#endif
-
 #ifndef RT_FAST_RCP
 #define RT_FAST_RCP 1
+#endif
+// RT_PRIMARY_STORE = 1: a pixel's primary ray stores its contribution
+// (store_first) and the colour sums are not cleared before a render; 0: every
+// contribution is an atomic add onto sums cleared by a memset. Same images;
+// 1.018 -> 1.012 ms per 1080p blob pair, 0.212 -> 0.182 ms for the
+// 10-primitive scene at 1080p.
+#ifndef RT_PRIMARY_STORE
+#define RT_PRIMARY_STORE 1
 #endif
 constexpr int kThreads = 128;
 // conservative slab exit (Ize 2013): 1 + 2 gamma_3 with correctly rounded
