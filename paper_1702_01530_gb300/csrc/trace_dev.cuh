@@ -17,15 +17,18 @@ namespace {
 // GB300, SAH tree, both eyes of a 4x4-pixel tile per warp: 1.042 ms by
 // default, 0.221 ms for a 10-primitive scene):
 // RT_MIN_BLOCKS = minimum resident blocks per SM requested from the register
-// allocator (0 = no request; 8 measured best: 64 registers, 32 warps per SM;
-// 6 blocks: 1.051 / 0.216 ms; 10 blocks (48 registers, spills in the shading
-// code): 1.047 / 0.242 ms); RT_WHILE_WHILE = 1 postpones the first leaf a ray
+// allocator (0 = no request; 9 measured best: the default walk fits 56
+// registers without spills, 36 warps per SM; against 8 blocks (64 registers,
+// 32 warps) 1.005 against 1.014 ms per 1080p blob pair and 13.94 against
+// 14.05 ms per 4K terrain frame; 6 blocks: 1.051 / 0.216 ms; 7 blocks: 1.048
+// ms; 10 blocks (48 registers, spills in the shading code): 1.047 / 0.242 ms
+// in earlier builds); RT_WHILE_WHILE = 1 postpones the first leaf a ray
 // meets and keeps descending until every active lane of the warp holds a
 // leaf, so the leaf tests of a warp run together instead of interleaving
 // with node visits (the "while-while" loop of Aila & Laine, HPG 2009) --
 // 1.247 ms with one primitive per leaf, hence off by default.
 #ifndef RT_MIN_BLOCKS
-#define RT_MIN_BLOCKS 8
+#define RT_MIN_BLOCKS 9
 #endif
 #ifndef RT_WHILE_WHILE
 #define RT_WHILE_WHILE 0
