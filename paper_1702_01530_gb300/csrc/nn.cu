@@ -1,17 +1,21 @@
 // Retrace-probability network: 4 layers of 3x3 convolutions
-// (9 -> 32 -> 32 -> 32 -> 1, zero padding 1, ReLU, sigmoid), BF16 operands
-// and FP32 accumulation on the 5th-generation tensor cores (sm_103a).
+// (10 -> 32 -> 32 -> 32 -> 1, zero padding 1, ReLU, sigmoid), BF16 operands
+// (E4M3 for layers 2-4 in FP8 inference) and FP32 accumulation on the
+// 5th-generation tensor cores (sm_103a).
 //
 // Convolution as implicit GEMM on tcgen05 (k_conv_tma):
-//   a persistent CTA computes tiles of R rows x 128 consecutive pixels:
+//   a persistent CTA computes tiles of R rows x W_t consecutive pixels:
 //   output row ry is D_ry[128 pixels, Cout] = sum over the 9 taps (dy, dx) of
 //   A(ry+dy, dx)[128, Cin] x B(dy, dx)[Cin, Cout], where A(h, dx) is halo row h
-//   shifted by dx pixels. The input halo (R+2 rows x 130 pixels x Cin
-//   channels) sits in shared memory as 16-byte channel chunks ordered
-//   [chunk][halo pixel], so every A(h, dx) is the same matrix shifted by
-//   h*130 + dx rows: the K-major, non-swizzled operand layout with 8-row core
-//   matrices 128 B apart (SBO) and chunk planes (R+2)*130*16 B (rounded up to
-//   128 B) apart (LBO).
+//   shifted by dx pixels. The input halo (R+2 rows of Cin channels) sits in
+//   shared memory as 16-byte channel chunks ordered [chunk][halo pixel], so
+//   every A(h, dx) is the same matrix shifted by h*pitch + dx rows: the
+//   K-major, non-swizzled operand layout with 8-row core matrices 128 B apart
+//   (SBO) and chunk planes (R+2)*pitch*16 B (rounded up to 128 B) apart (LBO).
+//   Interleaved inputs (the 16-channel features) have 130-pixel halo rows and
+//   W_t = 128; chunk-planar inputs (activations) are loaded as 2 KB box rows
+//   of 128 pixels, W_t = 126 (the MMA lanes 126 and 127 read the next row and
+//   are not stored).
 //   Stacked taps: an MMA of N = Cout costs the tensor core as much as one of
 //   N = 64 (about 45 cycles on GB300, measured; N = 96 about 56, N = 256 about
 //   128, the full rate), so the three vertical taps of a kernel column are
@@ -26,22 +30,23 @@
 //   columns it has read (and the four outside rows) before handing the
 //   accumulators back. Weights are pre-packed in this stacked core-matrix
 //   layout, [dx][chunk][3 Cout][chunk elements].
-//   The CTA is warp-specialised. A producer thread loads each halo with one
-//   TMA box per 8-channel chunk (cp.async.bulk.tensor, zeros outside the
-//   image) into a ring of halo buffers, up to RT_CONV_STAGES - 1 tiles ahead,
-//   and issues the tile's 9 * Cin/16 tcgen05.mma per row (M=128, N=Cout, K=16,
-//   kind::f16 with BF16 inputs) into one of two TMEM accumulator sets; the
-//   epilogue warps read their TMEM lanes (tcgen05.ld 32x32b) for the fused
-//   epilogue (bias + ReLU -> BF16, bias + sigmoid -> FP32, or the backward
-//   ReLU mask), so loads, MMAs and epilogues of consecutive tiles overlap.
+//   The CTA is warp-specialised: a TMA warp loads each tile's halo
+//   (cp.async.bulk.tensor, zeros outside the image) into a ring of halo
+//   buffers; an MMA warp issues the tile's MMAs (kind::f16 with BF16 inputs,
+//   kind::f8f6f4 with E4M3) into one of two TMEM accumulator sets; the
+//   epilogue warps read their TMEM lanes (tcgen05.ld 32x32b), hand the set
+//   back and apply the fused epilogue (bias + ReLU -> BF16 or E4M3, bias +
+//   sigmoid -> FP32, or the backward ReLU mask), so loads, MMAs and
+//   epilogues of consecutive tiles overlap.
 //   Every mbarrier wait has an iteration bound; on expiry the kernel sets the
 //   error word, waits (bounded) for what it has in flight and frees its TMEM.
 //
 // Layouts in HBM: the 16-channel maps (network input features, the BCE
 // gradient) are interleaved [P][16]; the 32-channel activations and data
-// gradients are chunk-planar [4][P][8] (plane k holds channels 8k..8k+7 of
-// every pixel), so each TMA box row is one contiguous run of 130 x 16 bytes
-// and each warp's epilogue store is a contiguous 512-byte run per plane.
+// gradients are chunk-planar [4][P][8] BF16 or [2][P][16] E4M3 (plane k
+// holds one 16-byte chunk of channels of every pixel), so a halo row of one
+// chunk is one contiguous run and each warp's epilogue store a contiguous
+// 512-byte run per plane.
 //
 // Backward pass: data gradients are convolutions with the 3x3 taps flipped
 // and Cin/Cout swapped (same tensor-core kernel); weight gradients are an
@@ -329,8 +334,8 @@ __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.
 //   acc_full[s]:   MMAs of accumulator set s done (tcgen05.commit)
 //   acc_empty[s]:  every epilogue thread has read and zeroed set s
 // Every wait is bounded; a wait that gives up sets the error word, and before
-// the CTA frees TMEM and exits the producer waits (bounded) for the copies and
-// MMAs it has issued.
+// the CTA frees TMEM and exits, the TMA warp waits (bounded) for the last copy
+// into each buffer and the MMA warp for the MMAs it has issued.
 template <int CIN, int COUT, bool IN_FP8, bool PLANAR>
 struct ConvTmaLayout {
   static constexpr int kElem = IN_FP8 ? 1 : 2;                           // bytes per channel
