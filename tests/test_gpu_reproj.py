@@ -501,3 +501,68 @@ def test_reprojection_mixed_mask_matches_oracle():
     assert abs(int(n.item()) - int(want.sum())) <= int(near.sum())
     # a mixed mask: some pixels retraced for p > thr beyond the holes, most kept
     assert (want & ~hole & ~mirror).sum() > 0 and 0 < want.mean() < 0.5, (want.sum(), hole.sum())
+
+
+def _bf16_bits(x):
+    """float32 -> BF16 bit patterns, round to nearest even (finite inputs)."""
+    u = np.ascontiguousarray(x, np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) >> 16
+    return u.astype(np.uint16)
+
+
+def test_network_full_size_sampled_matches_oracle():
+    """The launch the terrain reprojection times: 8 images of 3840x2160 per
+    call, BF16 and FP8. Each output depends on the 9x9 window of inputs
+    around it (four 3x3 layers), so the oracle computes sampled pixels from
+    crops: tile edges (126-pixel tiles of the chunk-planar layers, 128 of the
+    first layer, rows in fours), image borders and random pixels. Features:
+    image i tiles a seeded 1024x1024 block with an offset of its own."""
+    import torch
+    W, H, N, B = 3840, 2160, 8, 1024
+    params = sg.net_params_he(51)
+    rng = np.random.default_rng(52)
+    params[orp.OFF_B[0]:orp.OFF_B[0] + 32] = rng.normal(0, 0.1, 32)
+    params[orp.OFF_B[3]] = -0.5
+    block = np.zeros((B, B, 16), np.uint16)
+    block[..., :orp.IN_CH] = _bf16_bits(np.clip(rng.normal(0, 0.8, (B, B, orp.IN_CH)), -2, 2))
+    block_f = (block.astype(np.uint32) << 16).view(np.float32)
+    offs = [(int(rng.integers(B)), int(rng.integers(B))) for _ in range(N)]
+    yy, xx = np.arange(H)[:, None], np.arange(W)[None, :]
+    feat = torch.empty((N, H, W, 16), dtype=torch.bfloat16, device="cuda")
+    for i, (oy, ox) in enumerate(offs):
+        img = block[(yy + oy) % B, (xx + ox) % B]
+        feat[i].copy_(torch.from_numpy(img).view(torch.bfloat16))
+    samples = [(0, 0, 0), (1, H - 1, W - 1), (2, 0, W - 1), (3, H - 1, 0)]
+    for i in range(N):
+        for y in (1, 3, 4, 7, 8, H - 2):
+            for x in (1, 125, 126, 127, 128, 251, 252, 253, W - 2):
+                if rng.random() < 0.35:
+                    samples.append((i, y, x))
+    samples += [(int(rng.integers(N)), int(rng.integers(H)), int(rng.integers(W))) for _ in range(40)]
+    net = capi.Net(params)
+    try:
+        prob = torch.empty((N, H, W), dtype=torch.float32, device="cuda")
+        capi.rt_net_forward_images(net.handle, feat, N, W, H, prob)
+        got16 = prob.cpu().numpy()
+        capi.rt_net_set_fp8(net.handle, FP8_SCALES)
+        capi.rt_net_forward_images(net.handle, feat, N, W, H, prob)
+        got8 = prob.cpu().numpy()
+        capi.rt_net_status(net.handle)
+    finally:
+        net.close()
+    e16, e8 = [], []
+    for i, y, x in samples:
+        y0, y1, x0, x1 = max(0, y - 4), min(H, y + 5), max(0, x - 4), min(W, x + 5)
+        oy, ox = offs[i]
+        crop = block_f[(np.arange(y0, y1)[:, None] + oy) % B, (np.arange(x0, x1)[None, :] + ox) % B]
+        h, w = y1 - y0, x1 - x0
+        flat = crop.reshape(h * w, 16).astype(np.float64)
+        r16 = orp.forward(params, flat, w, h, bf16=True)[y - y0, x - x0]
+        r8 = orp.forward_fp8(params, flat, w, h, FP8_SCALES)[y - y0, x - x0]
+        e16.append(abs(got16[i, y, x] - r16))
+        e8.append(abs(got8[i, y, x] - r8))
+    e16, e8 = np.array(e16), np.array(e8)
+    assert len(samples) > 150
+    assert e16.max() <= 5e-3 and e16.mean() <= 5e-4, (e16.max(), e16.mean())
+    assert e8.max() <= 3e-2 and e8.mean() <= 2e-3, (e8.max(), e8.mean())
+    assert np.isfinite(got16).all() and np.isfinite(got8).all() and got16.std() > 1e-3
