@@ -491,6 +491,64 @@ def reprojection_frames(g, s, cams, net, stream, per_launch, plain_ms, batched_m
 
 
 # ------------------------------------------------------ row-band split
+def row_bands_measure(g, s, rank, world, dev, steps, warmup):
+    """Time the row-band split of one pair over the `world` ranks: rank r
+    renders rows row_bands(H, N)[r] of both eyes (rt_render_stereo_rows) over
+    its own copy of the scene, then the bands are all-gathered so rank 0 holds
+    both images. Returns (slowest rank's step ms, slowest rank's render ms,
+    rays of the pair, clocks); every rank must call it."""
+    import torch
+    import torch.distributed as dist
+
+    from paper_1702_01530_gb300 import bands, capi
+    stream = torch.cuda.current_stream()
+    r0, k = bands.row_bands(s.H, world)[rank]
+    bl = torch.empty((max(k, 1), s.W, 3), dtype=torch.float32, device=dev)
+    br = torch.empty_like(bl)
+    rays = torch.zeros(3, dtype=torch.int64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def band(count=False):
+        if k > 0:
+            capi.rt_render_stereo_rows(g.handle, s.camera, s.eye_sep, s.convergence, s.W, s.H,
+                                       s.max_depth, r0, k, bl, br, rays if count else None, stream)
+
+    band(count=True)
+    capi.rt_sync_status(g.handle)
+    band_rays = rays.clone()
+    if world > 1:
+        dist.all_reduce(band_rays)
+    total_rays = int(band_rays.sum().item())
+    clk = ClockSampler(dev.index).__enter__()
+    for _ in range(warmup):
+        band()
+        if world > 1:
+            bands.gather_bands(bl, br, s.H, rank, world)
+    render_ms, step_ms = [], []
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for _ in range(steps):
+        flush.fill_(1.0)
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        band()
+        e1.record(stream)
+        if world > 1:
+            bands.gather_bands(bl, br, s.H, rank, world)
+        e2.record(stream)
+        e2.synchronize()
+        render_ms.append(e0.elapsed_time(e1))
+        step_ms.append(e0.elapsed_time(e2))
+    torch.cuda.synchronize()
+    clk.__exit__()
+    if world > 1:
+        dist.barrier()
+    capi.rt_sync_status(g.handle)
+    ms, ms_render = max_over_ranks([float(np.mean(step_ms)), float(np.mean(render_ms))], world, dev)
+    return ms, ms_render, total_rays, clk.summary()
+
+
 def run_split_rows(args, rank, world, local):
     """Strong scaling over N GPUs (paper Figure 1): rank r renders rows
     row_bands(H, N)[r] of both eyes (rt_render_stereo_rows) over its own copy
@@ -509,52 +567,8 @@ def run_split_rows(args, rank, world, local):
     if world > 1:
         dist.init_process_group("nccl", device_id=dev)
     s = workload(args)
-    stream = torch.cuda.current_stream()
     g = capi.GpuScene(s)
-    r0, k = bands.row_bands(s.H, world)[rank]
-    bl = torch.empty((max(k, 1), s.W, 3), dtype=torch.float32, device=dev)
-    br = torch.empty_like(bl)
-    rays = torch.zeros(3, dtype=torch.int64, device=dev)
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-
-    def band(count=False):
-        if k > 0:
-            capi.rt_render_stereo_rows(g.handle, s.camera, s.eye_sep, s.convergence, s.W, s.H,
-                                       s.max_depth, r0, k, bl, br, rays if count else None, stream)
-
-    band(count=True)
-    capi.rt_sync_status(g.handle)
-    band_rays = rays.clone()
-    if world > 1:
-        dist.all_reduce(band_rays)
-    total_rays = int(band_rays.sum().item())
-    clk = ClockSampler(local).__enter__()
-    for _ in range(args.warmup):
-        band()
-        if world > 1:
-            bands.gather_bands(bl, br, s.H, rank, world)
-    render_ms, step_ms = [], []
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    for _ in range(args.steps):
-        flush.fill_(1.0)
-        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
-        e0.record(stream)
-        band()
-        e1.record(stream)
-        if world > 1:
-            bands.gather_bands(bl, br, s.H, rank, world)
-        e2.record(stream)
-        e2.synchronize()
-        render_ms.append(e0.elapsed_time(e1))
-        step_ms.append(e0.elapsed_time(e2))
-    torch.cuda.synchronize()
-    clk.__exit__()
-    if world > 1:
-        dist.barrier()
-    capi.rt_sync_status(g.handle)
-    ms, ms_render = max_over_ranks([float(np.mean(step_ms)), float(np.mean(render_ms))], world, dev)
+    ms, ms_render, total_rays, clocks = row_bands_measure(g, s, rank, world, dev, args.steps, args.warmup)
     if rank == 0:
         line = {"metric": METRIC, "value": round(total_rays / (ms * 1e-3) / 1e6, 2), "unit": UNIT,
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -568,7 +582,7 @@ def run_split_rows(args, rank, world, local):
                 "stereo_pairs_per_s": round(1.0 / (ms * 1e-3), 2),
                 "render_ms_slowest_rank": round(ms_render, 4),
                 "gather_ms": round(ms - ms_render, 4),
-                "gpu_launches": int(args.steps * 2), "clocks": clk.summary()}
+                "gpu_launches": int(args.steps * 2), "clocks": clocks}
         print(json.dumps(line))
     g.close()
     if world > 1:
@@ -771,6 +785,19 @@ def run_ours(args, rank, world, local):
     if clocks and clocks.get("sm_mhz"):
         line["roofline"]["frac_at_sampled_clock"] = round(
             achieved / alu_peak_tops(n_sms, clocks["sm_mhz"]), 4)
+    if world > 1:
+        # the paper's Figure 1 split of one pair over the N GPUs (strong
+        # scaling; every rank takes part) beside the replicas' weak scaling of
+        # the headline value; the same measurement as --split rows
+        from paper_1702_01530_gb300 import bands
+        rb_steps, rb_warm = min(args.steps, 100), max(3, min(args.warmup, 10))
+        rb_ms, rb_render, rb_rays, _ = row_bands_measure(g, s, rank, world, dev, rb_steps, rb_warm)
+        line["row_bands"] = {"scaling": "strong", "parallelism": f"rowbands{world}",
+                             "bands": bands.row_bands(s.H, world), "steps": rb_steps, "warmup": rb_warm,
+                             "value": round(rb_rays / (rb_ms * 1e-3) / 1e6, 2), "unit": UNIT,
+                             "ms_per_pair": round(rb_ms, 4), "stereo_pairs_per_s": round(1e3 / rb_ms, 2),
+                             "render_ms_slowest_rank": round(rb_render, 4),
+                             "gather_ms": round(rb_ms - rb_render, 4)}
     if rank == 0 and not args.no_reproj:
         line["reproj"] = reproj_leg(s)
     if rank == 0 and not args.no_batch:
