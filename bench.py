@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--ncu-terrain", action="store_true",
                     help="profiling mode: build the 4K terrain scene and render frame 0 of its "
                          "flight twice with rt_render_stereo, exit")
+    ap.add_argument("--ncu-reproj", action="store_true",
+                    help="two 8-frame learned reprojection calls of the 4K terrain (for ncu)")
     ap.add_argument("--ncu-net", action="store_true",
                     help="profiling mode: run the retrace network on 1080p features twice, exit")
     ap.add_argument("--fp8", action="store_true",
@@ -905,6 +907,33 @@ def run_ncu_terrain():
     g.close()
 
 
+def run_ncu_reproj():
+    """Two calls of the terrain sequence's 8-frame learned reprojection
+    (frames 0-7, 3840x2160 per eye, FP8 network at threshold 0.9): left eyes,
+    warp, network, mask, retrace and compose of 8 frames per launch each."""
+    import torch
+
+    from paper_1702_01530_gb300 import build as rtbuild
+    from paper_1702_01530_gb300 import capi, scenegen as sg, train_reproj as tr
+    rtbuild.build()
+    s = sg.config_terrain()
+    cams = sg.terrain_cameras(5, 8)
+    g = capi.GpuScene(s)
+    params, _ = tr.load_weights()
+    net = capi.Net(params)
+    tr.fp8_calibrate(net.handle)              # switches the network to FP8
+    L = torch.empty((8, s.H, s.W, 3), dtype=torch.float32, device="cuda")
+    R = torch.empty_like(L)
+    n = torch.zeros(1, dtype=torch.int32, device="cuda")
+    for _ in range(2):
+        capi.rt_render_stereo_reproj_frames(g.handle, cams, s.eye_sep, s.convergence, s.W, s.H,
+                                            s.max_depth, net.handle, 0.9, L, R, n)
+    capi.rt_sync_status(g.handle)
+    capi.rt_net_status(net.handle)
+    net.close()
+    g.close()
+
+
 # ------------------------------------------------------------------ study
 def _event_ms(fn, stream, reps=20, warm=3, flush=None):
     """Median CUDA-event time of fn() on ``stream``."""
@@ -1090,6 +1119,9 @@ def main():
         return
     if args.ncu_terrain:
         run_ncu_terrain()
+        return
+    if args.ncu_reproj:
+        run_ncu_reproj()
         return
     if args.study:
         if rank == 0:
